@@ -1,0 +1,469 @@
+"""Plain FP64 CPU implementation of APDB / rAPDB for box-constrained convex QCQPs.
+
+Test infrastructure: only tests/, __graft_entry__.smoke() and bench.py's CPU
+arms use it.  It is deliberately slow and literal: every quantity the paper
+defines is evaluated from its definition (Phi, grad_x Phi, g, the test function
+E_k) with full float64 matrix-vector products; no algebraic shortcut, fusion or
+reordering beyond what the paper's formulas state.
+
+Sources (arXiv 2605.29291):
+  * Problem, coupling Phi and its gradients: Sec. 2.1, eq. (QCQP) and the
+    QCQP coupling function; Euclidean Bregman distances D = 0.5||.||^2
+    (Sec. 2.2, remark after Def. of Bregman distances).
+  * APDB-xy: Algorithm 1 with the test function of eq. (backtracking).
+  * APDB-yx: Sec. 3.2, the modified parameter/update rules (eq. apdb-yx-y)
+    and its test function E_k.  The dual ball B is not imposed (Sec. 5).
+  * Step rule (monotone / non-monotone): Algorithm 1's tau update and
+    Remark (non-monotone step sizes), eq. (nonmonotone-tau).
+  * rAPDB fixed-frequency restart: Algorithm 2; restart from the last
+    iterate as in the experiments (Sec. 5.1, implementation details), or from
+    the weighted average as Algorithm 2 states.
+  * Adaptive restart: eq. (ada_restart) with the schedule of Sec. 5.1/5.2
+    (first evaluation at k=50 (yx) / k=100 (xy), then every gap_every).
+  * Smoothed duality gap G_xi: Def. (smoothed duality gap) and the remark on
+    computing it (y-part is a projection, x-part a strongly convex box QP).
+  * KKT residual: the residual r(x, v, lambda) of Thm. (metric
+    subregularity sufficient conditions) with the map G(z) of its proof; the
+    normalisation into a relative residual is a reading (the paper is silent).
+
+Parity pins (see tests/test_oracle_pins.py): closed forms (ball constraint,
+interior PD QP, one-step iterate), weak-duality certificates from an exact box
+QP by exhaustive active-set enumeration, the ergodic bounds (Lemmas with eqs.
+4.16apd / 3.3apd) at random points, step-size invariants (monotone identity of
+the trial count, the golden-ratio bound of the non-monotone rule), the algebraic
+identity of E_k for quadratics, G_xi(z*) = 0 and G_xi >= 0, and the
+x-subproblem against brute-force active-set enumeration.
+Parity unpinned: absolute iteration counts of the paper's tables (different
+instances and data).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Parameters (Sec. 5: eta = 0.7; yx c_alpha = 0.4, delta = 0.5; xy c_alpha = 0.25,
+# c_beta = 0.3, delta = 0.4; xi = 0.04, q = 1/2).
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Params:
+    variant: str = "yx"              # "yx" (Sec. 3.2) or "xy" (Algorithm 1)
+    c_nm: int = 1                    # 0 monotone, 1 non-monotone (eq. nonmonotone-tau)
+    backtracking: bool = True        # False: fixed step tau_bar, every trial accepted
+    mu: float = 0.0
+    c_alpha: float = 0.4
+    c_beta: float = 0.0
+    delta: float = 0.5
+    eta: float = 0.7
+    tau_bar: float = 1.0
+    gamma0: float = 1.0
+    restart: str = "fixed"           # "none" | "fixed" (Algorithm 2) | "gap" (eq. ada_restart)
+    restart_period: int = 200
+    restart_from_average: bool = False
+    xi: float = 0.04
+    q: float = 0.5
+    gap_first: int = 50
+    gap_every: int = 500
+    max_iter: int = 50000
+    max_trials: int = 60
+    kkt_every: int = 1
+    tol: float = 1e-6
+
+
+def default_params(variant: str = "yx", **kw) -> Params:
+    """The paper's experiment settings (Sec. 5.1) for the chosen variant."""
+    if variant == "yx":
+        p = Params(variant="yx", c_alpha=0.4, c_beta=0.0, delta=0.5, gap_first=50)
+    elif variant == "xy":
+        p = Params(variant="xy", c_alpha=0.25, c_beta=0.3, delta=0.4, gap_first=100)
+    else:
+        raise ValueError(variant)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class BacktrackError(RuntimeError):
+    pass
+
+
+# ---------------------------------------------------------------------------
+# Problem: f(x) = 0.5 x'Q_0 x + q_0'x,  g_i(x) = 0.5 x'Q_i x + q_i'x + r_i,
+# Phi(x, lam) = f(x) + lam'g(x)   (Sec. 2.1, QCQP coupling, p = 0).
+# ---------------------------------------------------------------------------
+
+
+class Problem:
+    """Float64 copy of the canonical float32 data.  Q[0] is Q_0."""
+
+    def __init__(self, Q, c, d, lb, ub):
+        self.Q = np.asarray(Q, dtype=np.float64)
+        self.c = np.asarray(c, dtype=np.float64)
+        self.r = np.asarray(d, dtype=np.float64)
+        self.lb = np.asarray(lb, dtype=np.float64)
+        self.ub = np.asarray(ub, dtype=np.float64)
+        self.n = self.Q.shape[1]
+        self.m = self.Q.shape[0] - 1
+        assert self.c.shape == (self.m + 1, self.n) and self.r.shape == (self.m,)
+
+    @classmethod
+    def from_data(cls, data) -> "Problem":
+        h = data.numpy()
+        return cls(data.dense_q(), h.c, h.d, h.lb, h.ub)
+
+    # objective and constraints --------------------------------------------
+    def f(self, x):
+        return 0.5 * x @ (self.Q[0] @ x) + self.c[0] @ x
+
+    def g(self, x):
+        if self.m == 0:
+            return np.zeros(0)
+        return np.array([0.5 * x @ (self.Q[i] @ x) + self.c[i] @ x + self.r[i - 1]
+                         for i in range(1, self.m + 1)])
+
+    def phi(self, x, lam):
+        """Phi(x, y) = f(x) + <lam, g(x)>."""
+        return self.f(x) + lam @ self.g(x)
+
+    def grad_x(self, x, lam):
+        """grad_x Phi(x, y) = Q_0 x + q_0 + sum_i lam_i (Q_i x + q_i)."""
+        gr = self.Q[0] @ x + self.c[0]
+        for i in range(1, self.m + 1):
+            gr = gr + lam[i - 1] * (self.Q[i] @ x + self.c[i])
+        return gr
+
+    def grad_y(self, x, lam):
+        """grad_y Phi(x, y) = g(x) (independent of y for the lambda block)."""
+        return self.g(x)
+
+    def lagrangian(self, x, lam):
+        """L(x, y) on X x Y (both inside their sets): equals Phi."""
+        return self.phi(x, lam)
+
+    def proj_x(self, x):
+        return np.minimum(np.maximum(x, self.lb), self.ub)
+
+    @staticmethod
+    def proj_y(lam):
+        return np.maximum(lam, 0.0)
+
+
+def Dp(x, xk):
+    """Euclidean Bregman distance 0.5||x - xk||^2 (Sec. 2.2)."""
+    v = x - xk
+    return 0.5 * float(v @ v)
+
+
+Dd = Dp
+
+
+# ---------------------------------------------------------------------------
+# One APDB run (Algorithm 1 for xy; Sec. 3.2 rules for yx), as explicit state.
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class RoutineState:
+    x: np.ndarray
+    x_prev: np.ndarray
+    lam: np.ndarray
+    lam_prev: np.ndarray
+    tau_prev: float            # tau_{k-1}
+    sigma_prev: float          # sigma_{k-1}
+    gamma: float               # gamma_k
+    tau_init: float            # first trial value of tau_k
+    alpha_k: float             # alpha_k (set by the previous iteration)
+    beta_k: float              # beta_k
+    x0: np.ndarray = None
+    lam0: np.ndarray = None
+    tau0: float = None         # accepted tau_0 of this run
+    sigma0: float = None       # accepted sigma_0 of this run
+    k: int = 0
+    x_cum: np.ndarray = None
+    lam_cum: np.ndarray = None
+    T: float = 0.0
+
+
+def start_routine(prob: Problem, x0, lam0, p: Params) -> RoutineState:
+    """Initialisation line of Algorithm 1: (x^-1, y^-1) = (x^0, y^0),
+    tau_-1 = tau_0 = tau_bar, sigma_-1 = gamma_0 tau_0, cumulative sums zero.
+    alpha_0, beta_0 follow the recurrences at k = -1 (yx: alpha = c_alpha /
+    sigma; xy: alpha = c_alpha / tau, beta = gamma_0 c_beta / sigma)."""
+    sigma_m1 = p.gamma0 * p.tau_bar
+    if p.variant == "yx":
+        a0, b0 = p.c_alpha / sigma_m1, 0.0
+    else:
+        a0, b0 = p.c_alpha / p.tau_bar, p.gamma0 * p.c_beta / sigma_m1
+    x0 = np.array(x0, dtype=np.float64)
+    lam0 = np.array(lam0, dtype=np.float64)
+    return RoutineState(x=x0.copy(), x_prev=x0.copy(), lam=lam0.copy(), lam_prev=lam0.copy(),
+                        tau_prev=p.tau_bar, sigma_prev=sigma_m1, gamma=p.gamma0,
+                        tau_init=p.tau_bar, alpha_k=a0, beta_k=b0, x0=x0.copy(),
+                        lam0=lam0.copy(), x_cum=np.zeros_like(x0), lam_cum=np.zeros_like(lam0))
+
+
+def yx_trial(prob: Problem, st: RoutineState, tau: float, p: Params):
+    """One trial of APDB-yx (Sec. 3.2): dual step with momentum on grad_y Phi,
+    then a projected primal step at the new dual point; returns the candidate
+    and whether the test E_k <= -delta/tau D_p - delta/sigma D_d holds."""
+    sigma = st.gamma * tau
+    theta = st.sigma_prev / sigma
+    alpha_next = p.c_alpha / sigma
+    s = (1.0 + theta) * prob.grad_y(st.x, st.lam) - theta * prob.grad_y(st.x_prev, st.lam_prev)
+    lam_new = prob.proj_y(st.lam + sigma * s)
+    x_new = prob.proj_x(st.x - tau * prob.grad_x(st.x, lam_new))
+    dp, dd = Dp(x_new, st.x), Dd(lam_new, st.lam)
+    gy_diff = prob.grad_y(x_new, lam_new) - prob.grad_y(st.x, lam_new)
+    E = (prob.phi(x_new, lam_new) - prob.phi(st.x, lam_new)
+         - prob.grad_x(st.x, lam_new) @ (x_new - st.x) - dp / tau
+         + (1.0 / (2.0 * alpha_next)) * float(gy_diff @ gy_diff)
+         - (1.0 / sigma - theta * st.alpha_k) * dd)
+    ok = E <= -p.delta / tau * dp - p.delta / sigma * dd
+    return x_new, lam_new, ok, dict(sigma=sigma, theta=theta, alpha_next=alpha_next,
+                                    beta_next=0.0, E=E)
+
+
+def xy_trial(prob: Problem, st: RoutineState, tau: float, p: Params):
+    """One trial of APDB-xy (Algorithm 1): primal step with momentum on
+    grad_x Phi, dual projected ascent at the new primal point, and the test
+    function of eq. (backtracking)."""
+    sigma = st.gamma * tau
+    theta = st.sigma_prev / sigma
+    alpha_next = p.c_alpha / tau
+    beta_next = p.gamma0 * p.c_beta / sigma
+    s = (1.0 + theta) * prob.grad_x(st.x, st.lam) - theta * prob.grad_x(st.x_prev, st.lam_prev)
+    x_new = prob.proj_x(st.x - tau * s)
+    lam_new = prob.proj_y(st.lam + sigma * prob.grad_y(x_new, st.lam))
+    dp, dd = Dp(x_new, st.x), Dd(lam_new, st.lam)
+    a = prob.grad_x(x_new, lam_new) - prob.grad_x(x_new, st.lam)
+    b = prob.grad_x(x_new, st.lam) - prob.grad_x(st.x, st.lam)
+    E = ((1.0 / (2.0 * alpha_next)) * float(a @ a) - dd / sigma
+         + ((1.0 / (2.0 * beta_next)) * float(b @ b) if beta_next > 0 else
+            (0.0 if float(b @ b) == 0.0 else math.inf))
+         - (1.0 / tau - theta * (st.alpha_k + st.beta_k)) * dp)
+    ok = E <= -p.delta / tau * dp - p.delta / sigma * dd
+    return x_new, lam_new, ok, dict(sigma=sigma, theta=theta, alpha_next=alpha_next,
+                                    beta_next=beta_next, E=E)
+
+
+def apdb_iteration(prob: Problem, st: RoutineState, p: Params, log: dict | None = None) -> int:
+    """Iteration k of APDB: the backtracking loop (shrink tau by eta until the
+    test holds), then the averaging line and the gamma / tau updates
+    (Algorithm 1; eq. nonmonotone-tau when c_nm = 1).  Returns the number of
+    test evaluations.  With backtracking off the first trial is accepted and
+    tau stays at tau_bar."""
+    trial_fn = yx_trial if p.variant == "yx" else xy_trial
+    tau = st.tau_init
+    for trial in range(1, p.max_trials + 1):
+        x_new, lam_new, ok, aux = trial_fn(prob, st, tau, p)
+        if ok or not p.backtracking:
+            break
+        tau = p.eta * tau
+    else:
+        raise BacktrackError(f"no step accepted after {p.max_trials} trials")
+    sigma = aux["sigma"]
+    if st.k == 0:
+        st.tau0, st.sigma0 = tau, sigma
+    t_k = sigma / st.sigma0
+    st.x_cum = st.x_cum + t_k * x_new
+    st.lam_cum = st.lam_cum + t_k * lam_new
+    st.T += t_k
+    if p.backtracking:
+        gamma_next = st.gamma * (1.0 + p.mu * tau)
+        tau_next = tau * math.sqrt(st.gamma / gamma_next * (1.0 + p.c_nm * tau / st.tau_prev))
+    else:
+        gamma_next, tau_next = st.gamma, tau
+    if log is not None:
+        log.setdefault("tau", []).append(tau)
+        log.setdefault("tau_init", []).append(st.tau_init)
+        log.setdefault("trials", []).append(trial)
+        log.setdefault("sigma", []).append(sigma)
+        log.setdefault("gamma", []).append(st.gamma)
+    st.x_prev, st.x = st.x, x_new
+    st.lam_prev, st.lam = st.lam, lam_new
+    st.tau_prev, st.sigma_prev = tau, sigma
+    st.alpha_k, st.beta_k = aux["alpha_next"], aux["beta_next"]
+    st.gamma, st.tau_init = gamma_next, tau_next
+    st.k += 1
+    return trial
+
+
+def apdb(prob: Problem, x0, lam0, K: int, p: Params, log: dict | None = None):
+    """APDB(x^0, y^0, K): K iterations, returns the weighted averages
+    (x_cum, y_cum) / T and the final state (Algorithm 1's return line)."""
+    st = start_routine(prob, x0, lam0, p)
+    for _ in range(K):
+        apdb_iteration(prob, st, p, log)
+    return st.x_cum / st.T, st.lam_cum / st.T, st
+
+
+# ---------------------------------------------------------------------------
+# KKT residual (reading of r(x, v, lambda) with relative normalisation).
+# ---------------------------------------------------------------------------
+
+
+def kkt_residual(prob: Problem, x, lam):
+    """Returns (rel_kkt, r_stat, r_feas) with
+
+      r_stat_j = dist(0, grad_x Phi(x, lam)_j + N_X(x)_j)   (box normal cone),
+      r_feas_i = dist(0, -g_i(x) + N_{R+}(lam_i)),
+      rel_kkt = max(||r_stat|| / (1 + max(||Q_0x+q_0||, ||sum lam_i(Q_ix+q_i)||)),
+                    ||r_feas|| / (1 + max(||r||, ||(g_i(x) - r_i)_i||))).
+    """
+    x = np.asarray(x, np.float64)
+    lam = np.asarray(lam, np.float64)
+    gf = prob.Q[0] @ x + prob.c[0]
+    gc = np.zeros_like(x)
+    for i in range(1, prob.m + 1):
+        gc = gc + lam[i - 1] * (prob.Q[i] @ x + prob.c[i])
+    grad = gf + gc
+    rs = np.where(x <= prob.lb, np.maximum(-grad, 0.0),
+                  np.where(x >= prob.ub, np.maximum(grad, 0.0), np.abs(grad)))
+    g = prob.g(x)
+    rf = np.where(lam > 0.0, np.abs(g), np.maximum(g, 0.0))
+    r_stat = float(np.linalg.norm(rs))
+    r_feas = float(np.linalg.norm(rf))
+    den_s = 1.0 + max(float(np.linalg.norm(gf)), float(np.linalg.norm(gc)))
+    den_f = 1.0 + max(float(np.linalg.norm(prob.r)), float(np.linalg.norm(g - prob.r)))
+    return max(r_stat / den_s, r_feas / den_f), r_stat, r_feas
+
+
+# ---------------------------------------------------------------------------
+# Smoothed duality gap G_xi(z) with D = 0.5||.||^2 (so 2 xi D = xi ||.||^2).
+# ---------------------------------------------------------------------------
+
+
+def gap_x_subproblem(prob: Problem, x, lam, xi):
+    """argmin_{x' in X} Phi(x', lam) + xi ||x' - x||^2: a strongly convex box QP
+    (Hessian Q(lam) + 2 xi I).  Solved exactly by bounded-variable least
+    squares (an active-set method that terminates at the exact minimiser):
+    with H = L L', 0.5 x'Hx + l'x = 0.5||L'x + L^{-1} l||^2 - const."""
+    from scipy.linalg import cholesky, solve_triangular
+    from scipy.optimize import lsq_linear
+    H = prob.Q[0].copy()
+    lin = prob.c[0].copy()
+    for i in range(1, prob.m + 1):
+        H += lam[i - 1] * prob.Q[i]
+        lin += lam[i - 1] * prob.c[i]
+    H = H + 2.0 * xi * np.eye(prob.n)
+    lin = lin - 2.0 * xi * np.asarray(x, np.float64)
+    L = cholesky(H, lower=True)
+    rhs = -solve_triangular(L, lin, lower=True)
+    lb, ub = prob.lb, prob.ub
+    res = lsq_linear(L.T, rhs, bounds=(lb, ub), method="bvls", tol=1e-15,
+                     lsmr_tol=None, max_iter=None)
+    return prob.proj_x(res.x)
+
+
+def smoothed_gap(prob: Problem, x, lam, xi):
+    """Self-centred smoothed gap G_xi(z) =
+    [max_{lam' >= 0} Phi(x, lam') - xi||lam' - lam||^2]
+      - [min_{x' in X} Phi(x', lam) + xi||x' - x||^2].
+    The y-part is separable: lam' = max(0, lam + g(x) / (2 xi))."""
+    x = np.asarray(x, np.float64)
+    lam = np.asarray(lam, np.float64)
+    g = prob.g(x)
+    lam_s = prob.proj_y(lam + g / (2.0 * xi))
+    y_part = prob.phi(x, lam_s) - xi * float((lam_s - lam) @ (lam_s - lam))
+    xs = gap_x_subproblem(prob, x, lam, xi)
+    x_part = prob.phi(xs, lam) + xi * float((xs - x) @ (xs - x))
+    return y_part - x_part
+
+
+# ---------------------------------------------------------------------------
+# rAPDB (Algorithm 2) with fixed-frequency or adaptive (G_xi) restarts.
+# ---------------------------------------------------------------------------
+
+STATUS_OK, STATUS_MAXITER, STATUS_BACKTRACK = 0, 5, 4
+
+
+@dataclass
+class Result:
+    x: np.ndarray
+    lam: np.ndarray
+    iters: int
+    trials: int
+    restarts: int
+    rel_kkt: float
+    r_stat: float
+    r_feas: float
+    obj: float
+    status: int
+    log: dict = field(default_factory=dict)
+
+
+def rapdb(prob: Problem, x0=None, lam0=None, p: Params | None = None, keep_iterates: int = 0):
+    """rAPDB driver.  Iteration semantics (also followed by the CUDA path):
+
+    at the top of global iteration `it` (iterate z^it):
+      1. if kkt_every > 0 and it % kkt_every == 0: stop when rel_kkt <= tol;
+      2. stop when it == max_iter;
+      3. restart checks: fixed -- when the current run has done restart_period
+         iterations; gap -- at it == gap_first store G_ref = G_xi(z^it); at
+         it = gap_first + j * gap_every (j >= 1) restart when
+         G_xi(candidate) <= q * G_ref and then set G_ref to that value;
+         the candidate and the new start point are the last iterate, or the
+         weighted average when restart_from_average;
+      4. one APDB iteration (backtracking loop, averaging, step rule).
+    """
+    p = p or default_params()
+    x0 = np.zeros(prob.n) if x0 is None else np.asarray(x0, np.float64)
+    lam0 = np.zeros(prob.m) if lam0 is None else np.asarray(lam0, np.float64)
+    st = start_routine(prob, x0, lam0, p)
+    log: dict = {}
+    it = trials = restarts = 0
+    status = STATUS_OK
+    G_ref = None
+    rel = rs = rf = float("nan")
+    iterates = []
+    while True:
+        if p.kkt_every > 0 and it % p.kkt_every == 0:
+            rel, rs, rf = kkt_residual(prob, st.x, st.lam)
+            if rel <= p.tol:
+                break
+        if it >= p.max_iter:
+            status = STATUS_MAXITER
+            break
+        if p.restart == "fixed" and st.k == p.restart_period:
+            if p.restart_from_average:
+                xs, ls = st.x_cum / st.T, st.lam_cum / st.T
+            else:
+                xs, ls = st.x, st.lam
+            st = start_routine(prob, xs, ls, p)
+            restarts += 1
+        elif p.restart == "gap" and it >= p.gap_first:
+            if st.k > 0 and p.restart_from_average:
+                xs, ls = st.x_cum / st.T, st.lam_cum / st.T
+            else:
+                xs, ls = st.x, st.lam
+            if it == p.gap_first:
+                G_ref = smoothed_gap(prob, xs, ls, p.xi)
+                log.setdefault("gap", []).append((it, G_ref, False))
+            elif (it - p.gap_first) % p.gap_every == 0:
+                G = smoothed_gap(prob, xs, ls, p.xi)
+                fire = G <= p.q * G_ref
+                log.setdefault("gap", []).append((it, G, bool(fire)))
+                if fire:
+                    st = start_routine(prob, xs, ls, p)
+                    restarts += 1
+                    G_ref = G
+        try:
+            trials += apdb_iteration(prob, st, p, log)
+        except BacktrackError:
+            status = STATUS_BACKTRACK
+            break
+        it += 1
+        if it <= keep_iterates:
+            iterates.append((st.x.copy(), st.lam.copy()))
+    if p.kkt_every <= 0 or status != STATUS_OK:
+        rel, rs, rf = kkt_residual(prob, st.x, st.lam)
+    if keep_iterates:
+        log["iterates"] = iterates
+    return Result(st.x.copy(), st.lam.copy(), it, trials, restarts, rel, rs, rf,
+                  float(prob.f(st.x)), status, log)
