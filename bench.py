@@ -1,0 +1,342 @@
+"""Benchmark of the rAPDB hot path on GB300.
+
+A step is one rAPDB solve (yx, non-monotone backtracking, FP32) of the dense
+random QCQP n = 4096, m = 50 (Q_i = A_i'A_i/n, A_i in R^{2048 x 4096}, a
+3.4 GB float32 stack) from x = 0, y = 0 to relative KKT residual <= 1e-6,
+with the inputs resident in HBM.  `value` is rAPDB iterations per second over
+the timed steps (all ranks); the line also carries the time to tolerance,
+coupling passes per second, the coupling-pass roofline, the end-to-end
+number through the C ABI from pinned host buffers, and the FP64 CPU oracle
+timed on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 run under torch.distributed.run: every rank solves its own
+copy of the instance (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-1e-6 rel KKT & iters/s; coupling-pass HBM GB/s vs 8 TB/s "
+          "(plain vs mixed/batched)")
+WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1), c_i N(0,1), "
+            "d_i=-U[0.1,1], box [-10,10], FP32 (3.42 GB Q stack); rAPDB-yx non-monotone, "
+            "fixed restart every 200 iterations, x0=y0=0, stop at rel KKT <= 1e-6")
+# DRAM bytes (read + write) of one coupling-pass launch on this workload from an
+# ncu capture (profiles/coupling_pass_n4096_m50_f32.md); None when no capture of
+# the current kernel exists.
+PASS_DRAM_BYTES = None
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(v: float, world: int, device) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, world: int, device) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_workload(device, seed=0):
+    from paper_2605_29291_gb300 import workloads as W
+    return W.config("C2", device=device, seed=seed)
+
+
+def solver_params(R):
+    return R.Params.default(R.YX, c_nm=1, restart=R.RESTART_FIXED, restart_period=200, tol=1e-6,
+                            max_iter=50000)
+
+
+def oracle_sample(data, budget_s: float):
+    """FP64 oracle rAPDB on the same instance for a bounded number of
+    iterations (chosen from a one-iteration probe to fill about budget_s)."""
+    import numpy as np
+    import oracle as O
+    t0 = time.time()
+    prob = O.Problem.from_data(data)
+    t_setup = time.time() - t0
+    p = O.default_params("yx", c_nm=1, restart="fixed", restart_period=200, tol=1e-6)
+    p.max_iter = 1
+    t = time.time()
+    O.rapdb(prob, p=p)
+    one = time.time() - t
+    k = max(1, min(200, int(budget_s / max(one, 1e-3))))
+    p.max_iter = k
+    t = time.time()
+    r = O.rapdb(prob, p=p)
+    dt = time.time() - t
+    del prob
+    return {"iters": r.iters, "trials": r.trials, "seconds": dt, "setup_s": t_setup, "probe_s": one,
+            "cores": os.cpu_count()}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    import torch
+    dev = torch.device(f"cuda:{local}") if torch.cuda.is_available() else None
+    data = make_workload(dev).numpy()
+    per_step = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(data, per_step / 4)
+    iters = 0
+    secs = 0.0
+    cores = os.cpu_count()
+    for _ in range(args.steps):
+        s = oracle_sample(data, per_step)
+        iters += s["iters"]
+        secs += s["seconds"]
+    v = iters / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{iters} oracle rAPDB iterations over {args.steps} steps on the same "
+                                       f"instance (FP64 numpy, BLAS on all host cores)"},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    from paper_2605_29291_gb300 import build as B
+    B.build()
+    from paper_2605_29291_gb300 import rapdb as R
+
+    data = make_workload(dev, seed=0)
+    torch.cuda.synchronize()
+    p = solver_params(R)
+    s = R.Solver(data, p)
+    x = torch.zeros(data.n, dtype=torch.float32, device=dev)
+    y = torch.zeros(data.m, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        x.zero_()
+        y.zero_()
+        s.solve(x, y)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    infos = []
+    stream = torch.cuda.current_stream(dev)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.zero_()
+        y.zero_()
+        infos.append(s.solve(x, y))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(ms * 1e-3, world, dev)
+    iters = sum(i["iters"] for i in infos)
+    passes = sum(i["passes"] for i in infos)
+    iters_all = sum_over_ranks(float(iters), world, dev)
+    passes_all = sum_over_ranks(float(passes), world, dev)
+    value = iters_all / t_max
+    ok = all(i["status"] == R.OK for i in infos)
+
+    # dominant kernel: the coupling pass, timed with CUDA events on the
+    # solver's stream (the torch current stream)
+    pass_ms, pass_bytes = s.time_pass(reps=20)
+    pk, pk_kind = peaks()
+    achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": PASS_DRAM_BYTES,
+                "peak_kind": f"{pk_kind} copy bandwidth", "frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
+                "kernel": "k_pass<f32> (fused coupling pass)", "bytes_per_launch": pass_bytes,
+                "ms_per_launch": pass_ms}
+
+    # end to end through the C ABI from pinned host buffers (one step: upload,
+    # create, solve, read back)
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {k: getattr(data, k).cpu().pin_memory() for k in ("Q", "c", "d", "lb", "ub")}
+        hx = torch.zeros(data.n, dtype=torch.float32).pin_memory()
+        hy = torch.zeros(data.m, dtype=torch.float32).pin_memory()
+        ox = torch.empty(data.n, dtype=torch.float32).pin_memory()
+        oy = torch.empty(data.m, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values()) + hx.numel() * 4 + hy.numel() * 4
+        d2h = ox.numel() * 4 + oy.numel() * 4
+        del s
+        torch.cuda.synchronize()
+        data_dev = None
+        e_iters, e_secs = 0, 0.0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            from paper_2605_29291_gb300 import workloads as W
+            dd = W.QCQPData(data.n, data.m, *(host[k2].to(dev, non_blocking=True) for k2 in ("Q", "c", "d", "lb", "ub")))
+            xd = hx.to(dev, non_blocking=True)
+            yd = hy.to(dev, non_blocking=True)
+            se = R.Solver(dd, p)
+            inf = se.solve(xd, yd)
+            ox.copy_(xd, non_blocking=True)
+            oy.copy_(yd, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            se.close()
+            del dd, xd, yd, se
+            if k > 0:          # the first one warms the allocator
+                e_iters += inf["iters"]
+                e_secs += dt
+        e_t = max_over_ranks(e_secs, world, dev)
+        e2e = {"value": sum_over_ranks(float(e_iters), world, dev) / e_t, "unit": "iters/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": args.e2e_steps, "s_per_step": e_secs / args.e2e_steps}
+        del host
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        hd = data.numpy()
+        del data
+        torch.cuda.empty_cache()
+        smp = oracle_sample(hd, args.cpu_budget)
+        cpu = {"value": smp["iters"] / smp["seconds"], "unit": "iters/s", "cores": smp["cores"],
+               "kind": "oracle",
+               "sample": f"{smp['iters']} FP64 oracle rAPDB iterations ({smp['trials']} trials) of the same "
+                         f"instance in {smp['seconds']:.1f} s (numpy, BLAS default threads)"}
+
+    launches = sum(i["launches"] for i in infos)
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (3.42 GB Q stack per pass)",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_tol_s": statistics.median(i["seconds"] for i in infos),
+        "iters_per_solve": iters / args.steps, "passes_per_s": passes_all / t_max,
+        "coupling_gbs_in_solve": passes_all * pass_bytes / t_max / 1e9,
+        "rel_kkt": max(i["rel_kkt"] for i in infos), "all_converged": ok,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,228 @@
+/*
+ * rapdb.h -- C ABI of the GB300 (sm_103a) rAPDB solver for convex QCQPs.
+ *
+ * Problem (Sec. 2.1, eq. (QCQP), with the simple set X a box and no linear
+ * equalities):
+ *
+ *     min_x  0.5 x'Q_0 x + c_0'x
+ *     s.t.   g_i(x) = 0.5 x'Q_i x + c_i'x + d_i <= 0,   i = 1..m,
+ *            lb <= x <= ub,
+ *
+ * with every Q_i symmetric positive semidefinite (the caller asserts this).
+ * The paper writes q_i for c_i and r_i for d_i.  The solver is rAPDB:
+ * APDB-yx (Sec. 3.2, eq. (apdb-yx-y) and its test function) or APDB-xy
+ * (Algorithm 1 with eq. (backtracking)), monotone or non-monotone step sizes
+ * (Remark on non-monotone step sizes, eq. (nonmonotone-tau)), restarted at a
+ * fixed frequency (Algorithm 2; restart from the last iterate as in Sec. 5.1)
+ * or adaptively on the smoothed gap (eq. (ada_restart)), with Euclidean
+ * Bregman distances and the dual ball not imposed (Sec. 5.1).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers marked "device" are CUDA device addresses (from cudaMalloc or
+ *     torch); "host" pointers are ordinary host memory.  All arrays are
+ *     dense, row-major, float32 unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is ordered on that stream; calls that return
+ *     results to the host (rapdb_solve, rapdb_kkt_residual, ...) synchronise
+ *     the stream before returning.
+ *   - Return value: RAPDB_OK or an error status; no exception or abort ever
+ *     crosses the ABI.  rapdb_last_error(ctx) gives a one-line description of
+ *     the last failure on that context (rapdb_last_error(NULL) for failures
+ *     that happened before a context existed).
+ *   - A context is not thread safe: one host thread at a time per context.
+ */
+#ifndef RAPDB_H
+#define RAPDB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RAPDB_OK = 0,
+  RAPDB_ERR_INVALID = 1,    /* bad argument: size, pointer, parameter, NaN input   */
+  RAPDB_ERR_CUDA = 2,       /* a CUDA runtime call failed                          */
+  RAPDB_ERR_NOMEM = 3,      /* device allocation failed                            */
+  RAPDB_ERR_BACKTRACK = 4,  /* max_trials step-size reductions without acceptance  */
+  RAPDB_ERR_MAXITER = 5,    /* max_iter iterations without reaching tol            */
+  RAPDB_ERR_TIMEOUT = 6,    /* time_limit_s exceeded (checked on the device)       */
+  RAPDB_ERR_NUMERIC = 7     /* NaN / Inf met in a reduction                        */
+} rapdb_status;
+
+typedef enum { RAPDB_YX = 0, RAPDB_XY = 1 } rapdb_variant;
+/* Storage of the Q_i in the coupling pass.  F32: the caller's float32 Q is
+ * read directly.  BF16: round-to-nearest-even copy.  FP8: E4M3 codes of the
+ * symmetrically Jacobi-scaled matrix, Q~ = S C S with S = diag(s),
+ * s_j = sqrt(Q_jj)/16, C = e4m3(256 * Q_jk / sqrt(Q_jj Q_kk)). */
+typedef enum { RAPDB_F32 = 0, RAPDB_BF16 = 1, RAPDB_FP8 = 2 } rapdb_storage;
+typedef enum { RAPDB_Q0_DENSE = 0, RAPDB_Q0_DIAG = 1, RAPDB_Q0_ZERO = 2 } rapdb_q0_kind;
+typedef enum { RAPDB_RESTART_NONE = 0, RAPDB_RESTART_FIXED = 1, RAPDB_RESTART_GAP = 2 } rapdb_restart;
+
+/* Solver parameters.  rapdb_default_params() fills the paper's experiment
+ * settings (Sec. 5.1): eta = 0.7; yx: c_alpha = 0.4, delta = 0.5; xy:
+ * c_alpha = 0.25, c_beta = 0.3, delta = 0.4; xi = 0.04, q = 1/2; first gap
+ * evaluation at k = 50 (yx) / 100 (xy). */
+typedef struct {
+  int32_t variant;            /* rapdb_variant                                        */
+  int32_t c_nm;               /* 0 monotone, 1 non-monotone step rule                 */
+  int32_t backtracking;       /* 0: fixed step tau_bar, every trial accepted          */
+  int32_t restart;            /* rapdb_restart                                        */
+  double mu;                  /* strong convexity modulus used by gamma_{k+1}         */
+  double c_alpha, c_beta, delta, eta;
+  double tau_bar;             /* first trial step size of every run                   */
+  double gamma0;              /* sigma = gamma * tau                                  */
+  int32_t restart_period;     /* fixed restart: iterations per run (Algorithm 2's K^) */
+  int32_t restart_from_average; /* 1: restart from the weighted average (Algorithm 2)   */
+  double xi, q;               /* smoothed gap parameters (eq. (ada_restart))           */
+  int32_t gap_first, gap_every; /* gap schedule: first evaluation, then period          */
+  int32_t storage;            /* rapdb_storage                                        */
+  int32_t refine;             /* quantised storage: switch to float32 Q on a KKT stall*/
+  double stall_ratio;         /* stall: rel KKT fell by less than this factor per run */
+  int32_t max_iter, max_trials, kkt_every;
+  int32_t use_graph;          /* 1: device loop as a CUDA graph with a conditional    */
+                              /*    WHILE node; 0: host relaunches kernel chunks      */
+  double tol;                 /* stop when rel KKT <= tol (checked every kkt_every)  */
+  double time_limit_s;        /* <= 0: none                                           */
+  int32_t rows_per_block;     /* coupling pass tile height; 0 = autotune at create   */
+  int32_t gap_inner_max;      /* inner iterations of the smoothed-gap box QP          */
+} rapdb_params;
+
+typedef struct {
+  int32_t iters;              /* accepted iterations                                  */
+  int32_t trials;             /* test evaluations = coupling passes in the loop      */
+  int32_t restarts;
+  int32_t precision_switches;
+  int32_t passes;             /* all coupling passes (trials + setup + gap + KKT32)  */
+  int32_t status;             /* rapdb_status of the solve                           */
+  double rel_kkt, r_stat, r_feas;
+  double obj;                 /* 0.5 x'Q_0 x + c_0'x at the returned x              */
+  double seconds;             /* device time of the solve (CUDA events)             */
+  int64_t launches;           /* kernels this call launched (device loop + set-up)  */
+} rapdb_info;
+
+typedef struct rapdb_ctx rapdb_ctx;
+
+/* Fill *p with the paper's settings for `variant` (rapdb_variant), fixed
+ * restart every 200 iterations, tol 1e-6, max_iter 50000, max_trials 60,
+ * tau_bar = gamma0 = 1, F32 storage. */
+void rapdb_default_params(rapdb_params *p, int32_t variant);
+
+/* Create a single-instance context.
+ *   n  > 0 variables, m >= 0 constraints (m = 0: box-constrained QP, which
+ *   needs q0_kind = DENSE so that one matrix is streamed).
+ *   q0_kind: DENSE -> Q holds (m+1) matrices, Q_0 first; DIAG -> Q holds the
+ *            m constraint matrices and q0diag (device, n) the diagonal of Q_0;
+ *            ZERO -> Q holds the m constraint matrices, Q_0 = 0.
+ *   Q     device, (M, n, n) float32, M = m+1 (DENSE) or m; symmetric.
+ *   c     device, (m+1, n): row 0 = c_0, row i = c_i.
+ *   d     device, (m,): the constants d_i (may be NULL when m = 0).
+ *   lb,ub device, (n,), lb <= ub, finite.
+ * Ownership: with F32 storage, n % 4 == 0 and Q 16-byte aligned the context
+ * BORROWS Q (no copy): it must stay alive and unchanged until rapdb_destroy.
+ * Otherwise the context owns a padded copy (F32 rows padded to a multiple of 4,
+ * BF16 to 8, FP8 to 16 elements).  With refine = 1 the float32 Q is borrowed
+ * as well.  c, d, lb, ub, q0diag are copied.  Errors: RAPDB_ERR_INVALID for
+ * sizes, NULL pointers, lb > ub, a negative diagonal entry of some Q_i or a
+ * NaN in the data; RAPDB_ERR_NOMEM / RAPDB_ERR_CUDA otherwise. */
+rapdb_status rapdb_create(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind,
+                          const float *Q, const float *q0diag, const float *c,
+                          const float *d, const float *lb, const float *ub,
+                          const rapdb_params *p, void *stream);
+
+/* Run rAPDB from (x, y) (device, n and m floats; overwritten with the final
+ * iterate; y must be >= 0 and x inside the box).  The whole loop -- trial
+ * steps, coupling passes, FP64 backtracking tests, step-size updates,
+ * restarts and the KKT stop test -- runs on the device; the host waits once,
+ * at the end, then fills *info (host, may be NULL).  Returns info->status. */
+rapdb_status rapdb_solve(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
+
+/* Relative KKT residual at (x, y) (device): one float32 coupling pass with the
+ * context's float32 Q (the quantised copy only when no float32 Q exists), then
+ *   r_stat_j = dist(0, grad_x L(x,y)_j + N_[lb,ub](x_j)),
+ *   r_feas_i = |g_i(x)| if y_i > 0 else max(g_i(x), 0),
+ *   rel = max(||r_stat|| / (1 + max(||Q_0x+c_0||, ||sum_i y_i(Q_ix+c_i)||)),
+ *             ||r_feas|| / (1 + max(||d||, ||(g_i(x) - d_i)_i||))),
+ * the residual r(x, v, lambda) of the metric subregularity theorem (Sec. 4)
+ * with the normalisation stated above.  Outputs are host doubles (any may be
+ * NULL). */
+rapdb_status rapdb_kkt_residual(rapdb_ctx *ctx, const float *x, const float *y,
+                                double *rel_kkt, double *r_stat, double *r_feas);
+
+/* One fused coupling pass on the stored Q (the hot operator, exposed for tests
+ * and for timing): for every constraint index i = 0..m
+ *     U[i] = Q_i x,  W[i] = Q_i v           (device, (m+1, n) float32 each)
+ * plus the per-matrix float64 dot products
+ *     dots[5*i + 0] = x'U[i], dots[5*i+1] = v'W[i], dots[5*i+2] = v'Uold[i],
+ *     dots[5*i + 3] = c_i'x,  dots[5*i+4] = c_i'v
+ * (device, 5*(m+1) doubles; Uold is the (m+1, n) device array `uold`, which
+ * may be NULL, giving zeros).  x, v: device, n floats.  Asynchronous on the
+ * context's stream. */
+rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
+                                 const float *uold, float *U, float *W, double *dots);
+
+/* Time the context's coupling-pass kernel: `reps` back-to-back launches on
+ * the context's stream, on the current solver iterate (x^k, and d of the
+ * last trial as the second right-hand side), bracketed by two CUDA events on
+ * that stream.  *ms_per_pass (host) receives the average duration of one
+ * launch, *bytes_per_pass (host) the algorithmic bytes of one pass: the
+ * stored Q entries read, M * n * n * (4 | 2 | 1) (+ n*M*4 scale bytes for
+ * FP8).  Outputs of the pass go to context scratch; the solver state is not
+ * changed. */
+rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, double *ms_per_pass,
+                             int64_t *bytes_per_pass);
+
+/* Record the first `capacity` iterations of the next rapdb_solve calls:
+ * tau_k (device doubles), test evaluations of iteration k (device int32),
+ * and, when x_log / y_log are non-NULL, the iterates x^{k+1} (device,
+ * capacity x n floats) and y^{k+1} (capacity x m floats).  capacity = 0
+ * switches logging off.  The buffers are borrowed. */
+rapdb_status rapdb_set_log(rapdb_ctx *ctx, int32_t capacity, double *tau_log,
+                           int32_t *trials_log, float *x_log, float *y_log);
+
+/* Batched contexts: B independent problems with their own n_b, m_b, solved
+ * together in one device loop with per-instance step sizes, restart counters
+ * and convergence flags.  Q_dense[b], c[b], d[b], lb[b], ub[b] are host arrays
+ * of B device pointers with the layout of rapdb_create (Q_0 dense).  Data are
+ * copied into one packed arena owned by the context (F32 storage only). */
+rapdb_status rapdb_create_batched(rapdb_ctx **out, int32_t B, const int64_t *n,
+                                  const int64_t *m, const float *const *Q,
+                                  const float *const *c, const float *const *d,
+                                  const float *const *lb, const float *const *ub,
+                                  const rapdb_params *p, void *stream);
+
+/* Solve every instance: x[b], y[b] (host arrays of device pointers) hold the
+ * start points and receive the results; info (host, B entries, may be NULL).
+ * Returns RAPDB_OK when every instance reached tol, else the first failing
+ * instance's status. */
+rapdb_status rapdb_solve_batched(rapdb_ctx *ctx, float *const *x, float *const *y,
+                                 rapdb_info *info);
+
+/* Checkpoint / resume of the solver state (iterates, caches, step sizes,
+ * counters) at the end of a rapdb_solve.  get: *len receives the size; buf
+ * (host) may be NULL to query it.  set: restores a state taken from a context
+ * built on the same data and parameters; the next rapdb_solve continues from
+ * it (its x, y arguments are then outputs only). */
+rapdb_status rapdb_get_state(rapdb_ctx *ctx, void *buf, size_t *len);
+rapdb_status rapdb_set_state(rapdb_ctx *ctx, const void *buf, size_t len);
+
+/* Continue the device loop from the context's current state (after a solve
+ * that stopped on max_iter or time_limit_s, or after rapdb_set_state, which
+ * may come from a context created with a larger max_iter).  x, y (device, n
+ * and m floats) receive the final iterate; info as for rapdb_solve.  Because
+ * every reduction runs in a fixed order, a solve split by a checkpoint ends
+ * bit for bit where the uninterrupted solve ends. */
+rapdb_status rapdb_resume(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
+
+/* Chosen coupling-pass tile (rows per CTA) and the number of CTAs per pass. */
+rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32_t *ctas);
+
+const char *rapdb_last_error(const rapdb_ctx *ctx);
+void rapdb_destroy(rapdb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAPDB_H */

@@ -1,0 +1,946 @@
+// Host side of the C ABI declared in include/rapdb.h: context set-up, the
+// graph-driven device loop, the stand-alone pass / KKT entry points,
+// batched contexts and checkpointing.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rapdb_util.cuh"
+
+using namespace rapdb_dev;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct InstHost {
+  Inst I;                      // device-pointer copy uploaded to the context's array
+  int64_t q_bytes;             // bytes of stored Q read by one pass
+};
+
+}  // namespace
+
+struct rapdb_ctx {
+  int B = 1;
+  bool batched = false;
+  rapdb_params p{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used for graph capture
+  int storage = RAPDB_F32;
+  int variant = RAPDB_YX;
+  std::vector<InstHost> hi;
+  Inst* d_inst = nullptr;
+  State* d_state = nullptr;
+  Ctrl* d_ctrl = nullptr;
+  int* d_vmap = nullptr;
+  int* d_pmap = nullptr;
+  int* d_flags = nullptr;
+  int nvblk = 0, npblk = 0;
+  size_t smem_vec = 0;
+  float* XS = nullptr;
+  float* VS = nullptr;
+  // stand-alone scratch (single instance)
+  float* tU = nullptr;
+  float* tW = nullptr;
+  float* tUo = nullptr;
+  float* txv = nullptr;
+  double* tpart = nullptr;
+  double* tvpart = nullptr;
+  double* tdots = nullptr;
+  double* ty = nullptr;
+  double* tg = nullptr;
+  double* tout = nullptr;
+  std::vector<void*> owned;
+  cudaGraphExec_t gexec = nullptr;
+  int g_bodies = 0;
+  int64_t launches = 0;        // kernels launched by the current call
+  State* h_state = nullptr;    // pinned
+  Ctrl* h_ctrl = nullptr;      // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  std::string err;
+  bool have_state = false;     // a solve finished (or set_state ran): checkpoint is valid
+  // logging
+  int log_cap = 0;
+  double* tau_log = nullptr;
+  int* trials_log = nullptr;
+  float* x_log = nullptr;
+  float* y_log = nullptr;
+};
+
+namespace {
+
+rapdb_status fail(rapdb_ctx* ctx, rapdb_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? RAPDB_ERR_NOMEM : RAPDB_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+    }                                                                                             \
+  } while (0)
+
+template <typename T>
+rapdb_status dalloc(rapdb_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess)
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RAPDB_ERR_NOMEM : RAPDB_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  ctx->owned.push_back(q);
+  e = cudaMemsetAsync(q, 0, bytes, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, RAPDB_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  *p = (T*)q;
+  return RAPDB_OK;
+}
+
+#define AL(ptr, count)                                     \
+  do {                                                     \
+    rapdb_status s_ = dalloc(ctx, &(ptr), (size_t)(count)); \
+    if (s_ != RAPDB_OK) return s_;                         \
+  } while (0)
+
+int pick_rows_per_block(int64_t n, int64_t M) {
+  // enough row blocks to fill 152 SMs several times over, rows a multiple of
+  // the 32 rows one CTA covers with one 4-row group per warp
+  (void)M;
+  if (n <= 256) return 32;
+  return 32;
+}
+
+DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
+  DevParams d{};
+  d.variant = p.variant;
+  d.c_nm = p.c_nm;
+  d.backtracking = p.backtracking;
+  d.restart = p.restart;
+  d.restart_period = p.restart_period;
+  d.restart_from_average = p.restart_from_average;
+  d.max_iter = p.max_iter;
+  d.max_trials = p.max_trials;
+  d.kkt_every = p.kkt_every;
+  d.refine = p.refine;
+  d.gap_first = p.gap_first;
+  d.gap_every = p.gap_every;
+  d.gap_inner_max = p.gap_inner_max;
+  d.mu = p.mu;
+  d.c_alpha = p.c_alpha;
+  d.c_beta = p.c_beta;
+  d.delta = p.delta;
+  d.eta = p.eta;
+  d.tau_bar = p.tau_bar;
+  d.gamma0 = p.gamma0;
+  d.tol = p.tol;
+  d.stall_ratio = p.stall_ratio;
+  d.xi = p.xi;
+  d.q = p.q;
+  d.log_cap = ctx->log_cap;
+  d.tau_log = ctx->tau_log;
+  d.trials_log = ctx->trials_log;
+  d.x_log = ctx->x_log;
+  d.y_log = ctx->y_log;
+  return d;
+}
+
+rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
+  if (!p) return fail(ctx, RAPDB_ERR_INVALID, "params is NULL");
+  if (p->variant != RAPDB_YX && p->variant != RAPDB_XY) return fail(ctx, RAPDB_ERR_INVALID, "bad variant");
+  if (p->storage < RAPDB_F32 || p->storage > RAPDB_FP8) return fail(ctx, RAPDB_ERR_INVALID, "bad storage");
+  if (p->restart < RAPDB_RESTART_NONE || p->restart > RAPDB_RESTART_GAP)
+    return fail(ctx, RAPDB_ERR_INVALID, "bad restart mode");
+  if (p->restart == RAPDB_RESTART_GAP)
+    return fail(ctx, RAPDB_ERR_INVALID, "adaptive (gap) restart is not available in this build");
+  if (p->restart == RAPDB_RESTART_FIXED && p->restart_period < 1)
+    return fail(ctx, RAPDB_ERR_INVALID, "restart_period must be >= 1");
+  if (!(p->eta > 0.0 && p->eta < 1.0)) return fail(ctx, RAPDB_ERR_INVALID, "eta must be in (0,1)");
+  if (!(p->tau_bar > 0.0) || !(p->gamma0 > 0.0)) return fail(ctx, RAPDB_ERR_INVALID, "tau_bar, gamma0 must be > 0");
+  if (!(p->c_alpha > 0.0) || p->mu < 0.0) return fail(ctx, RAPDB_ERR_INVALID, "c_alpha > 0, mu >= 0 required");
+  if (p->variant == RAPDB_XY && !(p->c_beta >= 0.0)) return fail(ctx, RAPDB_ERR_INVALID, "c_beta >= 0 required");
+  if (p->max_iter < 0 || p->max_trials < 1) return fail(ctx, RAPDB_ERR_INVALID, "max_iter >= 0, max_trials >= 1");
+  if (p->rows_per_block < 0 || (p->rows_per_block % 32) != 0)
+    return fail(ctx, RAPDB_ERR_INVALID, "rows_per_block must be 0 (auto) or a multiple of 32");
+  return RAPDB_OK;
+}
+
+// Build one instance's buffers.  Q, c, d, lb, ub, q0diag are the caller's device arrays.
+rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m64, int q0_kind, const float* Q,
+                            const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
+                            int rb_override) {
+  const rapdb_params& p = ctx->p;
+  const int n = (int)n64, m = (int)m64;
+  const int M = (q0_kind == RAPDB_Q0_DENSE) ? m + 1 : m;
+  Inst& I = H.I;
+  I = Inst{};
+  I.n = n;
+  I.m = m;
+  I.M = M;
+  I.q0_kind = q0_kind;
+  I.s_off = (q0_kind == RAPDB_Q0_DENSE) ? 0 : 1;
+  I.storage = p.storage;
+  I.ldv = (int)round_up(n, 16);
+  const int ldv = I.ldv;
+  cudaStream_t st = ctx->stream;
+
+  // validation
+  CK(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), st));
+  k_validate<<<1024, 256, 0, st>>>(Q, n, M, c, m, d, lb, ub, q0_kind == RAPDB_Q0_DIAG ? q0diag : nullptr,
+                                   ctx->d_flags);
+  CK(cudaGetLastError());
+  int flags[4];
+  CK(cudaMemcpyAsync(flags, ctx->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "NaN or Inf in the problem data");
+  if (flags[1]) return fail(ctx, RAPDB_ERR_INVALID, "negative diagonal entry: some Q_i is not PSD");
+  if (flags[2]) return fail(ctx, RAPDB_ERR_INVALID, "lb > ub");
+
+  // stored Q
+  const bool aligned = ((uintptr_t)Q % 16) == 0;
+  const int64_t rows = (int64_t)M * n;
+  if (p.storage == RAPDB_F32) {
+    if (n % 4 == 0 && aligned) {
+      I.Q = Q;
+      I.ld = n;
+    } else {
+      I.ld = (int)round_up(n, 4);
+      float* q = nullptr;
+      AL(q, rows * I.ld);
+      if (rows > 0)
+        CK(cudaMemcpy2DAsync(q, (size_t)I.ld * 4, Q, (size_t)n * 4, (size_t)n * 4, (size_t)rows,
+                             cudaMemcpyDeviceToDevice, st));
+      I.Q = q;
+    }
+    H.q_bytes = rows * (int64_t)I.ld * 4;
+  } else {
+    const int EB = (p.storage == RAPDB_BF16) ? 2 : 1;
+    I.ld = (int)round_up(n, 16 / EB);
+    uint8_t* q = nullptr;
+    AL(q, rows * I.ld * EB);
+    if (p.storage == RAPDB_BF16) {
+      if (rows > 0) k_quant_bf16<<<4096, 256, 0, st>>>(Q, n, rows, I.ld, (__nv_bfloat16*)q);
+    } else {
+      float *rinv = nullptr, *scale = nullptr;
+      AL(rinv, (size_t)std::max(M, 1) * ldv);
+      AL(scale, (size_t)std::max(M, 1) * ldv);
+      if (rows > 0) {
+        k_fp8_scales<<<256, 256, 0, st>>>(Q, n, M, ldv, rinv, scale);
+        k_quant_fp8<<<4096, 256, 0, st>>>(Q, n, M, I.ld, ldv, rinv, (__nv_fp8_storage_t*)q);
+      }
+      I.qscale = scale;
+    }
+    CK(cudaGetLastError());
+    I.Q = q;
+    H.q_bytes = rows * (int64_t)I.ld * EB;
+    if (p.refine) {
+      if (n % 4 == 0 && aligned) {
+        I.Q32 = Q;
+        I.ld32 = n;
+      } else {
+        I.ld32 = (int)round_up(n, 4);
+        float* q32 = nullptr;
+        AL(q32, rows * I.ld32);
+        if (rows > 0)
+          CK(cudaMemcpy2DAsync(q32, (size_t)I.ld32 * 4, Q, (size_t)n * 4, (size_t)n * 4, (size_t)rows,
+                               cudaMemcpyDeviceToDevice, st));
+        I.Q32 = q32;
+      }
+    }
+  }
+
+  // vectors (padded to ldv; padding zero)
+  float *cc = nullptr, *lbp = nullptr, *ubp = nullptr, *q0d = nullptr;
+  double* dd = nullptr;
+  AL(cc, (size_t)(m + 1) * ldv);
+  CK(cudaMemcpy2DAsync(cc, (size_t)ldv * 4, c, (size_t)n * 4, (size_t)n * 4, (size_t)(m + 1),
+                       cudaMemcpyDeviceToDevice, st));
+  AL(lbp, ldv);
+  AL(ubp, ldv);
+  CK(cudaMemcpyAsync(lbp, lb, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ubp, ub, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  AL(q0d, ldv);
+  if (q0_kind == RAPDB_Q0_DIAG) CK(cudaMemcpyAsync(q0d, q0diag, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  AL(dd, std::max(m, 1));
+  double dn = 0.0;
+  if (m > 0) {
+    k_f2d<<<1, 256, 0, st>>>(d, dd, m);
+    std::vector<float> hd(m);
+    CK(cudaMemcpyAsync(hd.data(), d, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < m; ++i) dn += (double)hd[i] * (double)hd[i];
+  }
+  I.c = cc;
+  I.lb = lbp;
+  I.ub = ubp;
+  I.q0diag = q0d;
+  I.dcon = dd;
+  I.dnorm = sqrt(dn);
+
+  // tiles
+  I.rb = rb_override > 0 ? rb_override : pick_rows_per_block(n, M);
+  I.nrb = (n + I.rb - 1) / I.rb;
+  I.ncb = (n + NT - 1) / NT;
+
+  // solver buffers
+  const int mm = std::max(m, 1);
+  for (int s = 0; s < 2; ++s) {
+    AL(I.xb[s], ldv);
+    AL(I.yb[s], mm);
+    AL(I.U[s], (size_t)(m + 1) * ldv);
+    AL(I.gb[s], mm);
+    if (p.variant == RAPDB_XY) AL(I.gx[s], ldv);
+  }
+  AL(I.W, (size_t)(m + 1) * ldv);
+  AL(I.dv, ldv);
+  AL(I.gnew, mm);
+  AL(I.part, (size_t)std::max(M, 1) * NDOT * I.nrb);
+  AL(I.vpart, (size_t)I.ncb * NVP);
+  AL(I.dots, (size_t)(m + 1) * NDOT);
+  if (p.restart_from_average) {
+    AL(I.xcum, ldv);
+    AL(I.ycum, mm);
+  }
+  I.P = make_devparams(p, ctx);
+  return RAPDB_OK;
+}
+
+// Upload instance table + block maps, create the capture stream and graph.
+rapdb_status finalize_ctx(rapdb_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const int B = ctx->B;
+  std::vector<int> vmap, pmap;
+  int mmax = 1;
+  for (int b = 0; b < B; ++b) {
+    Inst& I = ctx->hi[b].I;
+    I.vblk0 = (int)vmap.size();
+    for (int k = 0; k < I.ncb; ++k) vmap.push_back(b);
+    I.pblk0 = (int)pmap.size();
+    for (int k = 0; k < I.M * I.nrb; ++k) pmap.push_back(b);
+    mmax = std::max(mmax, I.m);
+  }
+  ctx->nvblk = (int)vmap.size();
+  ctx->npblk = (int)pmap.size();
+  ctx->smem_vec = (size_t)2 * mmax * sizeof(double);
+  if (ctx->smem_vec > 200 * 1024) return fail(ctx, RAPDB_ERR_INVALID, "too many constraints (m > 12800)");
+  AL(ctx->d_vmap, vmap.size());
+  AL(ctx->d_pmap, std::max<size_t>(pmap.size(), 1));
+  CK(cudaMemcpyAsync(ctx->d_vmap, vmap.data(), vmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!pmap.empty())
+    CK(cudaMemcpyAsync(ctx->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  AL(ctx->d_inst, B);
+  AL(ctx->d_state, B);
+  AL(ctx->d_ctrl, 1);
+  std::vector<Inst> tmp(B);
+  for (int b = 0; b < B; ++b) tmp[b] = ctx->hi[b].I;
+  CK(cudaMemcpyAsync(ctx->d_inst, tmp.data(), B * sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  if (ctx->smem_vec > 48 * 1024) {
+    CK(cudaFuncSetAttribute(k_vec<RAPDB_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
+    CK(cudaFuncSetAttribute(k_vec<RAPDB_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
+    CK(cudaFuncSetAttribute(k_vec<RAPDB_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
+  }
+  CK(cudaMallocHost((void**)&ctx->h_state, sizeof(State) * B));
+  CK(cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl) * 2));
+  CK(cudaEventCreateWithFlags(&ctx->ev[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev[1], cudaEventDisableTiming));
+  CK(cudaEventCreate(&ctx->t0));
+  CK(cudaEventCreate(&ctx->t1));
+  CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+  return RAPDB_OK;
+}
+
+rapdb_status upload_params(rapdb_ctx* ctx) {
+  std::vector<Inst> tmp(ctx->B);
+  for (int b = 0; b < ctx->B; ++b) {
+    ctx->hi[b].I.P = make_devparams(ctx->p, ctx);
+    tmp[b] = ctx->hi[b].I;
+  }
+  CK(cudaMemcpyAsync(ctx->d_inst, tmp.data(), ctx->B * sizeof(Inst), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return RAPDB_OK;
+}
+
+// One body of the device loop on stream s.
+rapdb_status launch_body(rapdb_ctx* ctx, cudaStream_t s) {
+  const int st = ctx->storage;
+  const dim3 gv(ctx->nvblk), gp(std::max(ctx->npblk, 1)), blk(NT);
+  const size_t sm = ctx->smem_vec;
+  auto vec = [&]() {
+    if (st == RAPDB_F32) k_vec<RAPDB_F32><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
+    else if (st == RAPDB_BF16) k_vec<RAPDB_BF16><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
+    else k_vec<RAPDB_FP8><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
+  };
+  vec();
+  if (ctx->npblk > 0) {
+    if (st == RAPDB_F32) k_pass<RAPDB_F32><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
+    else if (st == RAPDB_BF16) k_pass<RAPDB_BF16><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
+    else k_pass<RAPDB_FP8><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
+  }
+  if (ctx->variant == RAPDB_XY) vec();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, RAPDB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return RAPDB_OK;
+}
+
+rapdb_status build_graph(rapdb_ctx* ctx, int bodies) {
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < bodies; ++k) {
+    rapdb_status s = launch_body(ctx, ctx->cap);
+    if (s != RAPDB_OK) {
+      cudaStreamEndCapture(ctx->cap, &g);
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+  }
+  CK(cudaStreamEndCapture(ctx->cap, &g));
+  cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, RAPDB_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  ctx->g_bodies = bodies;
+  return RAPDB_OK;
+}
+
+// Run the device loop until every instance is done.  The host never waits
+// per trial: it keeps two graph launches (each `g_bodies` bodies) in flight
+// and reads the 'active' counter of the older one.
+rapdb_status run_loop(rapdb_ctx* ctx, int64_t max_bodies) {
+  cudaStream_t st = ctx->stream;
+  const bool graph = ctx->p.use_graph != 0;
+  const int per = graph ? ctx->g_bodies : 16;
+  int64_t launched = 0;
+  int slot = 0, pending = 0;
+  bool done = false;
+  while (!done) {
+    if (launched >= max_bodies) break;
+    if (graph) {
+      CK(cudaGraphLaunch(ctx->gexec, st));
+    } else {
+      for (int k = 0; k < per; ++k) {
+        rapdb_status s = launch_body(ctx, st);
+        if (s != RAPDB_OK) return s;
+      }
+    }
+    launched += per;
+    ctx->launches += (int64_t)per * (ctx->variant == RAPDB_XY ? 3 : 2);
+    CK(cudaMemcpyAsync(&ctx->h_ctrl[slot], ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ctx->ev[slot], st));
+    pending++;
+    if (pending == 2) {
+      const int old = slot ^ 1;
+      CK(cudaEventSynchronize(ctx->ev[old]));
+      pending = 1;
+      if (ctx->h_ctrl[old].active <= 0) done = true;
+    }
+    slot ^= 1;
+  }
+  CK(cudaStreamSynchronize(st));
+  return RAPDB_OK;
+}
+
+int64_t body_cap(const rapdb_params& p) {
+  // every trial is one body; iterations <= max_iter, trials <= max_trials each,
+  // plus set-up, restart and KKT bodies
+  return (int64_t)(p.max_iter + 2) * (int64_t)(p.max_trials + 2) + 1024;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rapdb_default_params(rapdb_params* p, int32_t variant) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->variant = variant == RAPDB_XY ? RAPDB_XY : RAPDB_YX;
+  p->c_nm = 1;
+  p->backtracking = 1;
+  p->restart = RAPDB_RESTART_FIXED;
+  p->mu = 0.0;
+  p->eta = 0.7;
+  if (p->variant == RAPDB_YX) {
+    p->c_alpha = 0.4;
+    p->c_beta = 0.0;
+    p->delta = 0.5;
+    p->gap_first = 50;
+  } else {
+    p->c_alpha = 0.25;
+    p->c_beta = 0.3;
+    p->delta = 0.4;
+    p->gap_first = 100;
+  }
+  p->tau_bar = 1.0;
+  p->gamma0 = 1.0;
+  p->restart_period = 200;
+  p->restart_from_average = 0;
+  p->xi = 0.04;
+  p->q = 0.5;
+  p->gap_every = 500;
+  p->storage = RAPDB_F32;
+  p->refine = 1;
+  p->stall_ratio = 0.5;
+  p->max_iter = 50000;
+  p->max_trials = 60;
+  p->kkt_every = 1;
+  p->use_graph = 1;
+  p->tol = 1e-6;
+  p->time_limit_s = 0.0;
+  p->rows_per_block = 0;
+  p->gap_inner_max = 200;
+}
+
+rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
+                          const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
+                          const rapdb_params* p, void* stream) {
+  rapdb_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || m < 0 || n > (1 << 28) || m > 12800) return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes n, m");
+  if (q0_kind < RAPDB_Q0_DENSE || q0_kind > RAPDB_Q0_ZERO) return fail(nullptr, RAPDB_ERR_INVALID, "bad q0_kind");
+  const int64_t M = (q0_kind == RAPDB_Q0_DENSE) ? m + 1 : m;
+  if (M < 1) return fail(nullptr, RAPDB_ERR_INVALID, "m = 0 needs a dense Q_0 (nothing to stream otherwise)");
+  if ((M > 0 && !Q) || !c || (m > 0 && !d) || !lb || !ub || (q0_kind == RAPDB_Q0_DIAG && !q0diag))
+    return fail(nullptr, RAPDB_ERR_INVALID, "NULL data pointer");
+  {
+    rapdb_status s = check_params(nullptr, p);
+    if (s != RAPDB_OK) return s;
+  }
+  ctx = new rapdb_ctx();
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->storage = p->storage;
+  ctx->variant = p->variant;
+  ctx->B = 1;
+  ctx->hi.resize(1);
+  rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
+  if (s == RAPDB_OK)
+    s = build_instance(ctx, ctx->hi[0], n, m, q0_kind, Q, q0diag, c, d, lb, ub, p->rows_per_block);
+  if (s == RAPDB_OK && p->storage == RAPDB_FP8) {
+    const Inst& I = ctx->hi[0].I;
+    s = dalloc(ctx, &ctx->XS, (size_t)std::max(I.M, 1) * I.ldv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->VS, (size_t)std::max(I.M, 1) * I.ldv);
+  }
+  if (s == RAPDB_OK) {
+    const Inst& I = ctx->hi[0].I;
+    s = dalloc(ctx, &ctx->tU, (size_t)(I.m + 1) * I.ldv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tW, (size_t)(I.m + 1) * I.ldv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tUo, (size_t)(I.m + 1) * I.ldv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->txv, (size_t)2 * I.ldv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tpart, (size_t)std::max(I.M, 1) * NDOT * I.nrb);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tvpart, (size_t)I.ncb * NVP);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tdots, (size_t)(I.m + 1) * NDOT);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->ty, (size_t)std::max(I.m, 1));
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tg, (size_t)std::max(I.m, 1));
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tout, 8);
+  }
+  if (s == RAPDB_OK) s = finalize_ctx(ctx);
+  if (s == RAPDB_OK) s = build_graph(ctx, 32);
+  if (s != RAPDB_OK) {
+    g_last_error = ctx->err;
+    rapdb_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, const int64_t* m,
+                                  const float* const* Q, const float* const* c, const float* const* d,
+                                  const float* const* lb, const float* const* ub, const rapdb_params* p,
+                                  void* stream) {
+  if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (B <= 0 || !n || !m || !Q || !c || !d || !lb || !ub) return fail(nullptr, RAPDB_ERR_INVALID, "bad batch arguments");
+  {
+    rapdb_status s = check_params(nullptr, p);
+    if (s != RAPDB_OK) return s;
+  }
+  if (p->storage != RAPDB_F32) return fail(nullptr, RAPDB_ERR_INVALID, "batched contexts use F32 storage");
+  for (int b = 0; b < B; ++b) {
+    if (n[b] <= 0 || m[b] < 0 || m[b] > 12800 || n[b] > (1 << 24))
+      return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes in batch");
+    if (!Q[b] || !c[b] || !lb[b] || !ub[b] || (m[b] > 0 && !d[b]))
+      return fail(nullptr, RAPDB_ERR_INVALID, "NULL pointer in batch");
+  }
+  rapdb_ctx* ctx = new rapdb_ctx();
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->storage = RAPDB_F32;
+  ctx->variant = p->variant;
+  ctx->B = B;
+  ctx->batched = true;
+  ctx->hi.resize(B);
+  rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
+  for (int b = 0; b < B && s == RAPDB_OK; ++b)
+    s = build_instance(ctx, ctx->hi[b], n[b], m[b], RAPDB_Q0_DENSE, Q[b], nullptr, c[b], d[b], lb[b], ub[b],
+                       p->rows_per_block);
+  if (s == RAPDB_OK) s = finalize_ctx(ctx);
+  if (s == RAPDB_OK) s = build_graph(ctx, 32);
+  if (s != RAPDB_OK) {
+    g_last_error = ctx->err;
+    rapdb_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return RAPDB_OK;
+}
+
+static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* y, rapdb_info* info, bool resume) {
+  cudaStream_t st = ctx->stream;
+  const int B = ctx->B;
+  ctx->launches = 0;
+  if (!resume) {
+    for (int b = 0; b < B; ++b) {
+      const Inst& I = ctx->hi[b].I;
+      if (!x[b] || (I.m > 0 && !y[b])) return fail(ctx, RAPDB_ERR_INVALID, "NULL x or y");
+      CK(cudaMemsetAsync(I.xb[0], 0, (size_t)I.ldv * 4, st));
+      CK(cudaMemcpyAsync(I.xb[0], x[b], (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+      if (I.m > 0) {
+        k_f2d<<<1, 256, 0, st>>>(y[b], I.yb[0], I.m);
+        ctx->launches += 1;
+      }
+    }
+    CK(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), st));
+    k_init_state<<<B, 256, 0, st>>>(ctx->d_inst, ctx->d_state, B, ctx->p.time_limit_s, ctx->d_flags);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    int flags[4];
+    CK(cudaMemcpyAsync(flags, ctx->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "x0 outside the box");
+    if (flags[1]) return fail(ctx, RAPDB_ERR_INVALID, "y0 has a negative (or NaN) entry");
+  }
+  Ctrl c0{};
+  c0.active = B;
+  CK(cudaMemcpyAsync(ctx->d_ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(ctx->t0, st));
+  rapdb_status s = run_loop(ctx, body_cap(ctx->p));
+  if (s != RAPDB_OK) return s;
+  CK(cudaEventRecord(ctx->t1, st));
+  CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+  rapdb_status first_bad = RAPDB_OK;
+  for (int b = 0; b < B; ++b) {
+    const Inst& I = ctx->hi[b].I;
+    const State& S = ctx->h_state[b];
+    int status = S.phase == PH_DONE ? S.status : RAPDB_ERR_MAXITER;
+    if (x && x[b]) CK(cudaMemcpyAsync(x[b], I.xb[S.xcur], (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+    if (y && y[b] && I.m > 0) {
+      k_d2f<<<1, 256, 0, st>>>(I.yb[S.ycur], y[b], I.m);
+      ctx->launches += 1;
+    }
+    if (info) {
+      rapdb_info& o = info[b];
+      o.iters = S.it;
+      o.trials = S.trials_total;
+      o.restarts = S.restarts;
+      o.precision_switches = S.switches;
+      o.passes = S.passes;
+      o.status = status;
+      o.rel_kkt = S.rel_kkt;
+      o.r_stat = S.r_stat;
+      o.r_feas = S.r_feas;
+      o.obj = S.obj;
+      o.seconds = ms * 1e-3;
+      o.launches = ctx->launches;
+    }
+    if (status != RAPDB_OK && first_bad == RAPDB_OK) first_bad = (rapdb_status)status;
+  }
+  CK(cudaStreamSynchronize(st));
+  ctx->have_state = true;
+  return first_bad;
+}
+
+rapdb_status rapdb_solve(rapdb_ctx* ctx, float* x, float* y, rapdb_info* info) {
+  if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
+  if (ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "use rapdb_solve_batched on a batched context");
+  float* xs[1] = {x};
+  float* ysv[1] = {y};
+  return solve_common(ctx, xs, ysv, info, false);
+}
+
+rapdb_status rapdb_solve_batched(rapdb_ctx* ctx, float* const* x, float* const* y, rapdb_info* info) {
+  if (!ctx || !x || !y) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  return solve_common(ctx, x, y, info, false);
+}
+
+rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v, const float* uold, float* U,
+                                 float* W, double* dots) {
+  if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
+  if (!x || !v || !U || !W || !dots) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  const Inst& I = ctx->hi[0].I;
+  cudaStream_t st = ctx->stream;
+  // the caller's vectors are unpadded (n, and (m+1, n) row-major): stage them
+  // into the context's padded scratch
+  float* xpad = ctx->txv;
+  float* vpad = ctx->txv + I.ldv;
+  CK(cudaMemcpyAsync(xpad, x, (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(vpad, v, (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+  float* Ut = ctx->tU;
+  float* Wt = ctx->tW;
+  float* uo = nullptr;
+  if (uold) {
+    uo = ctx->tUo;
+    CK(cudaMemcpy2DAsync(uo, (size_t)I.ldv * 4, uold, (size_t)I.n * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  if (I.storage == RAPDB_FP8 || I.s_off)
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, vpad, uo, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
+  {
+    const int grid = I.M * I.nrb;
+    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
+    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
+    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
+  }
+  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, dots);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy2DAsync(U, (size_t)I.n * 4, Ut, (size_t)I.ldv * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpy2DAsync(W, (size_t)I.n * 4, Wt, (size_t)I.ldv * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, double* rel_kkt, double* r_stat,
+                                double* r_feas) {
+  if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
+  const Inst& I = ctx->hi[0].I;
+  if (!x || (I.m > 0 && !y)) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  cudaStream_t st = ctx->stream;
+  float* xpad = ctx->txv;
+  CK(cudaMemcpyAsync(xpad, x, (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+  if (I.m > 0) k_f2d<<<1, 256, 0, st>>>(y, ctx->ty, I.m);
+  const int use32 = (I.storage != RAPDB_F32 && I.Q32) ? 1 : 0;
+  float* Ut = ctx->tU;
+  float* Wt = ctx->tW;
+  if (I.storage == RAPDB_FP8 && !use32)
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
+  else if (I.s_off)
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, use32);
+  if (I.M > 0) {
+    const int grid = I.M * I.nrb;
+    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
+    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
+    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
+  }
+  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots);
+  k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, ctx->tvpart);
+  k_kkt_final<<<1, 32, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout);
+  CK(cudaGetLastError());
+  double out[4];
+  CK(cudaMemcpyAsync(out, ctx->tout, sizeof(out), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (rel_kkt) *rel_kkt = out[0];
+  if (r_stat) *r_stat = out[1];
+  if (r_feas) *r_feas = out[2];
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, double* ms_per_pass, int64_t* bytes_per_pass) {
+  if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
+  if (reps < 1) return fail(ctx, RAPDB_ERR_INVALID, "reps must be >= 1");
+  const Inst& I = ctx->hi[0].I;
+  cudaStream_t st = ctx->stream;
+  int xcur = 0;
+  if (ctx->have_state) {
+    CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    xcur = ctx->h_state[0].xcur;
+  }
+  const float* x = I.xb[xcur];
+  const float* v = I.dv;
+  const int use32 = (I.storage != RAPDB_F32 && ctx->have_state && ctx->h_state[0].precision == 1) ? 1 : 0;
+  if (I.storage == RAPDB_FP8 && !use32)
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
+  const int grid = I.M * I.nrb;
+  auto launch = [&]() {
+    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, 0);
+    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, use32);
+    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, use32);
+  };
+  launch();   // warm-up
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->t0, st));
+  for (int r = 0; r < reps; ++r) launch();
+  CK(cudaEventRecord(ctx->t1, st));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(ctx->t1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+  if (ms_per_pass) *ms_per_pass = (double)ms / reps;
+  if (bytes_per_pass) {
+    const int64_t eb = use32 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));
+    int64_t b = (int64_t)I.M * I.n * I.n * eb;
+    if (I.storage == RAPDB_FP8 && !use32) b += (int64_t)I.M * I.n * 4;
+    *bytes_per_pass = b;
+  }
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, int32_t* trials_log, float* x_log,
+                           float* y_log) {
+  if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
+  if (capacity < 0) return fail(ctx, RAPDB_ERR_INVALID, "capacity < 0");
+  ctx->log_cap = capacity;
+  ctx->tau_log = capacity ? tau_log : nullptr;
+  ctx->trials_log = capacity ? trials_log : nullptr;
+  ctx->x_log = capacity ? x_log : nullptr;
+  ctx->y_log = capacity ? y_log : nullptr;
+  return upload_params(ctx);
+}
+
+rapdb_status rapdb_get_tile(const rapdb_ctx* ctx, int32_t* rows_per_block, int32_t* ctas) {
+  if (!ctx) return RAPDB_ERR_INVALID;
+  if (rows_per_block) *rows_per_block = ctx->hi[0].I.rb;
+  if (ctas) *ctas = ctx->npblk;
+  return RAPDB_OK;
+}
+
+// Checkpoint layout: magic, B, then per instance the State struct followed by
+// x^k, x^{k-1} slots, y slots, U slots, g slots, gx slots, xcum, ycum.
+static void state_blobs(rapdb_ctx* ctx, int b, std::vector<std::pair<void*, size_t>>& v) {
+  Inst& I = ctx->hi[b].I;
+  const size_t ldv = I.ldv, mm = std::max(I.m, 1), m1 = I.m + 1;
+  for (int s = 0; s < 2; ++s) {
+    v.push_back({I.xb[s], ldv * 4});
+    v.push_back({I.yb[s], mm * 8});
+    v.push_back({I.U[s], m1 * ldv * 4});
+    v.push_back({I.gb[s], mm * 8});
+    if (I.gx[s]) v.push_back({I.gx[s], ldv * 8});
+  }
+  if (I.xcum) v.push_back({I.xcum, ldv * 8});
+  if (I.ycum) v.push_back({I.ycum, mm * 8});
+}
+
+rapdb_status rapdb_get_state(rapdb_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  size_t total = 16;
+  std::vector<std::vector<std::pair<void*, size_t>>> blobs(ctx->B);
+  for (int b = 0; b < ctx->B; ++b) {
+    state_blobs(ctx, b, blobs[b]);
+    total += sizeof(State);
+    for (auto& pr : blobs[b]) total += pr.second;
+  }
+  if (!buf) {
+    *len = total;
+    return RAPDB_OK;
+  }
+  if (*len < total) return fail(ctx, RAPDB_ERR_INVALID, "buffer too small");
+  if (!ctx->have_state) return fail(ctx, RAPDB_ERR_INVALID, "no solver state yet (run rapdb_solve first)");
+  cudaStream_t st = ctx->stream;
+  uint8_t* o = (uint8_t*)buf;
+  const uint64_t magic = 0x5241504442434b31ull;  // "RAPDBCK1"
+  memcpy(o, &magic, 8);
+  const int64_t B = ctx->B;
+  memcpy(o + 8, &B, 8);
+  size_t off = 16;
+  CK(cudaMemcpyAsync(o + off, ctx->d_state, sizeof(State) * ctx->B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // states were copied contiguously; interleave layout = all states first
+  off += sizeof(State) * ctx->B;
+  for (int b = 0; b < ctx->B; ++b)
+    for (auto& pr : blobs[b]) {
+      CK(cudaMemcpyAsync(o + off, pr.first, pr.second, cudaMemcpyDeviceToHost, st));
+      off += pr.second;
+    }
+  CK(cudaStreamSynchronize(st));
+  *len = total;
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_set_state(rapdb_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  size_t need = 0;
+  rapdb_status s = rapdb_get_state(ctx, nullptr, &need);
+  if (s != RAPDB_OK) return s;
+  if (len != need) return fail(ctx, RAPDB_ERR_INVALID, "checkpoint size does not match this context");
+  const uint8_t* o = (const uint8_t*)buf;
+  uint64_t magic;
+  int64_t B;
+  memcpy(&magic, o, 8);
+  memcpy(&B, o + 8, 8);
+  if (magic != 0x5241504442434b31ull || B != ctx->B) return fail(ctx, RAPDB_ERR_INVALID, "not a checkpoint of this context");
+  cudaStream_t st = ctx->stream;
+  size_t off = 16;
+  std::vector<State> states(ctx->B);
+  memcpy(states.data(), o + off, sizeof(State) * ctx->B);
+  off += sizeof(State) * ctx->B;
+  for (auto& S : states) {
+    S.arrive_vec = 0;
+    S.arrive_pass = 0;
+    S.deadline_ns = 0;
+  }
+  CK(cudaMemcpyAsync(ctx->d_state, states.data(), sizeof(State) * ctx->B, cudaMemcpyHostToDevice, st));
+  for (int b = 0; b < ctx->B; ++b) {
+    std::vector<std::pair<void*, size_t>> blobs;
+    state_blobs(ctx, b, blobs);
+    for (auto& pr : blobs) {
+      CK(cudaMemcpyAsync(pr.first, o + off, pr.second, cudaMemcpyHostToDevice, st));
+      off += pr.second;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  ctx->have_state = true;
+  return RAPDB_OK;
+}
+
+rapdb_status rapdb_resume(rapdb_ctx* ctx, float* x, float* y, rapdb_info* info) {
+  if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
+  if (!ctx->have_state) return fail(ctx, RAPDB_ERR_INVALID, "no state to resume");
+  // a finished state is reopened: DONE with MAXITER / TIMEOUT continues the loop
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State) * ctx->B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < ctx->B; ++b) {
+    State& S = ctx->h_state[b];
+    if (S.phase == PH_DONE && (S.status == RAPDB_ERR_MAXITER || S.status == RAPDB_ERR_TIMEOUT)) {
+      S.phase = PH_TRIAL;
+      S.fresh = 1;
+      S.status = RAPDB_OK;
+    }
+    S.deadline_ns = 0;
+  }
+  CK(cudaMemcpyAsync(ctx->d_state, ctx->h_state, sizeof(State) * ctx->B, cudaMemcpyHostToDevice, st));
+  float* xs[1] = {x};
+  float* ysv[1] = {y};
+  return solve_common(ctx, xs, ysv, info, true);
+}
+
+const char* rapdb_last_error(const rapdb_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_last_error.c_str();
+}
+
+void rapdb_destroy(rapdb_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (void* q : ctx->owned) cudaFree(q);
+  if (ctx->h_state) cudaFreeHost(ctx->h_state);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->t0) cudaEventDestroy(ctx->t0);
+  if (ctx->t1) cudaEventDestroy(ctx->t1);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,391 @@
+// Device side of the rAPDB solver: data layout, the fused coupling pass and
+// small reduction helpers shared by the kernels in rapdb_kernels.cuh.
+//
+// One "body" of the device loop is two (xy: three) kernel launches:
+//   k_vec   -- per column block of every active instance: the trial step
+//              (yx: dual step with momentum, then the projected primal step
+//              at the new dual point; xy: projected primal step with
+//              momentum), the diagonal-Q_0 part of the pass, ||d||^2 and, on
+//              a new iterate, the KKT residual partials.  The last CTA of an
+//              instance to finish runs the "pre-control": the FP64 KKT
+//              reduction and the stop tests.
+//   k_pass  -- per (matrix, row block) of every active instance: one read of
+//              the stored Q_i rows against two right-hand sides (x~ and
+//              d = x~ - x^k), writing Q_i x~, Q_i d and per-block FP64 dot
+//              products.  The last CTA of an instance runs the
+//              "post-control": the deterministic FP64 reduction, the
+//              backtracking test, the step-size / momentum update and the
+//              restart rule.
+//   k_vec   -- (xy only) second sweep: ||a||^2 and ||b||^2 of the xy test.
+// "Last CTA" uses the fence + arrival-counter pattern: no CTA ever waits on
+// another, so no co-residency is assumed and nothing spins.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include "rapdb.h"
+
+namespace rapdb_dev {
+
+constexpr int NT = 256;            // threads per CTA, all solver kernels
+constexpr int NWARP = NT / 32;
+constexpr int NDOT = 5;            // dots per (matrix, row block)
+constexpr int NVP = 12;            // vector-kernel partials per column block
+
+// dot slots of one matrix i (pass output)
+enum DSlot : int { D_XU = 0, D_VW = 1, D_VUO = 2, D_CX = 3, D_CV = 4 };
+
+enum Phase : int {
+  PH_INIT = 0,       // first pass: U = Q x^0, g(x^0)
+  PH_TRIAL = 1,      // one trial of the backtracking loop
+  PH_XY2 = 2,        // xy: after the pass, ||a||^2 and ||b||^2 sweep and the test
+  PH_AVG = 3,        // restart from the weighted average: U = Q xbar
+  PH_KKT32 = 4,      // quantised storage: float32 pass at x^k for the true KKT
+  PH_KKT32B = 5,     // ... and its residual sweep + the refinement decision
+  PH_GAPY = 6,       // adaptive restart: smoothed-gap x-subproblem iterations
+  PH_GAPF = 7,       // ... final value sweep
+  PH_DONE = 9
+};
+
+// vector partial slots
+enum VSlot : int {
+  V_DD = 0,                                                // ||d||^2
+  V_XU0 = 1, V_DW0 = 2, V_DU0 = 3, V_CX0 = 4, V_CD0 = 5,   // i = 0 dots when Q_0 is not stored
+  V_RS = 6, V_GF = 7, V_GC = 8,                            // KKT: ||r_stat||^2, ||Q0x+c0||^2, ||sum y(Qx+c)||^2
+  V_AA = 9, V_BB = 10,                                     // xy: ||a||^2, ||b||^2
+  V_X2 = 11                                                // spare: ||x||^2 / gap term
+};
+
+struct DevParams {
+  int variant, c_nm, backtracking, restart, restart_period, restart_from_average;
+  int max_iter, max_trials, kkt_every, refine, gap_first, gap_every, gap_inner_max;
+  double mu, c_alpha, c_beta, delta, eta, tau_bar, gamma0, tol, stall_ratio, xi, q;
+  int log_cap;
+  double* tau_log;
+  int* trials_log;
+  float* x_log;
+  float* y_log;
+};
+
+// Immutable description of one instance (device memory).
+struct Inst {
+  int n, m, M;          // variables, constraints, stored matrices
+  int ld;               // row stride (elements) of the stored Q
+  int ld32;             // row stride of the float32 Q (refinement / KKT pass)
+  int ldv;              // stride of (m+1, n) vector arrays (multiple of 16)
+  int q0_kind, s_off;   // s_off = 0 when Q_0 is stored, 1 otherwise
+  int storage;          // rapdb_storage of Q
+  int rb, nrb;          // rows per block, blocks per matrix
+  int ncb;              // column blocks of NT for the vector kernel
+  int vblk0, pblk0;     // first vector block / pass item of this instance
+  const void* Q;        // (M, n, ld) stored matrices
+  const float* Q32;     // (M, n, ld32) float32 matrices or null
+  const float* qscale;  // FP8: (M, ldv) symmetric scales s
+  const float* q0diag;  // (ldv) diagonal of Q_0 when DIAG
+  const float* c;       // (m+1, ldv)
+  const double* dcon;   // (m)
+  const float* lb;      // (ldv)
+  const float* ub;      // (ldv)
+  double dnorm;         // ||d||_2 of the constants
+  float* xb[2];         // x^k / x~ (ldv each, padding zero)
+  double* yb[2];        // y^k / y~ (m)
+  float* U[2];          // Q x^k / Q x~  ((m+1, ldv))
+  float* W;             // Q d           ((m+1, ldv))
+  float* dv;            // d (ldv)
+  double* gx[2];        // xy: grad_x Phi(x^k,y^k) / grad_x Phi(x^{k-1},y^{k-1}); gap: work
+  double* gb[2];        // g(x^k) / g(x^{k-1})  (m)
+  double* gnew;         // g(x~) of the current trial (m)
+  double* part;         // (M, NDOT, nrb) pass partials
+  double* vpart;        // (ncb, NVP) vector partials
+  double* dots;         // (m+1, NDOT) reduced dots
+  double* xcum;         // averaging: sum t_k x^{k+1}  (ldv)
+  double* ycum;         // sum t_k y^{k+1}  (m)
+  float* gz;            // gap: FISTA iterate z (ldv)
+  float* gzp;           // gap: previous z (ldv)
+  DevParams P;
+};
+
+// Mutable solver state of one instance (device memory, FP64 scalars).
+struct State {
+  double tau;           // current trial tau_k
+  double tau_prev;      // tau_{k-1}
+  double sigma_prev;    // sigma_{k-1}
+  double gamma;         // gamma_k
+  double gamma_prev;    // gamma_{k-1} (xy test)
+  double alpha_k, beta_k;
+  double sigma0, T, t_last;
+  double rel_kkt, r_stat, r_feas, obj;
+  double rel_q;         // last residual measured with the stored (quantised) Q
+  double kkt_ref;       // true residual at the previous restart boundary
+  double dd;            // ||d||^2 of the current trial
+  double dots0[NDOT];   // i = 0 dots when Q_0 is not stored
+  double gap_ref, gap_val, gap_L, gap_t, gap_yval, gap_lin;
+  long long deadline_ns;
+  int k, it, trial, trials_total, passes, restarts, switches;
+  int phase, status, fresh, restart_note, avg_pending;
+  int xcur, ycur, ucur, gcur, gxcur;
+  int precision;        // 0: stored Q, 1: float32 Q
+  int gap_iter, gap_fire_pending;
+  unsigned int arrive_vec, arrive_pass;
+  int pad_;
+};
+
+struct Ctrl {
+  int active;           // instances not yet done
+  int pad_[3];
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA sum of K doubles per thread; result valid in thread 0.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* NWARP*K */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) smem[warp * K + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NWARP; ++w) s += smem[w * K + q];
+      v[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Arrival on a per-instance counter after this CTA's partials are written.
+// Returns true in every thread of the CTA that arrives last; that CTA then
+// sees the partials of all others (fence before the arrival, fence after).
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(counter, 1u);
+    s_last = (t == total - 1u);
+    if (s_last) *counter = 0u;     // reset for the next launch (all others arrived)
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Stored element loaders: 16 bytes -> E floats.
+template <int ST> struct Elt;
+template <> struct Elt<RAPDB_F32> {
+  static constexpr int E = 4;
+  static constexpr int B = 4;
+  __device__ __forceinline__ static void cvt(const uint4& r, float* o) {
+    o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+    o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+  }
+};
+template <> struct Elt<RAPDB_BF16> {
+  static constexpr int E = 8;
+  static constexpr int B = 2;
+  __device__ __forceinline__ static void cvt(const uint4& r, float* o) {
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+template <> struct Elt<RAPDB_FP8> {
+  static constexpr int E = 16;
+  static constexpr int B = 1;
+  __device__ __forceinline__ static void cvt(const uint4& r, float* o) {
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
+      __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
+      float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+      float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+      o[4 * k] = a.x; o[4 * k + 1] = a.y; o[4 * k + 2] = b.x; o[4 * k + 3] = b.y;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The fused coupling pass over one row block of one stored matrix.
+//
+// For rows j in [row0, row0+rows) of matrix Qm (constraint index i):
+//   u_j = (Q_i x)_j,  w_j = (Q_i v)_j    (FP32 accumulation)
+// written to Uo[j], Wo[j], and the block's FP64 dots
+//   x_j u_j, v_j w_j, v_j uold_j, c_j x_j, c_j v_j  summed over its rows,
+// stored to out[q * ostride] (q = 0..4).
+// Each warp takes rows in groups of RPW; each lane streams 16-byte vectors
+// of those rows (ld.global.nc, no L1 allocation) against the matching
+// 16-byte slices of x and v, UNR slices in flight per row.
+// FP8: `xs`/`vs` hold s .* x and s .* v (s the symmetric scales), so that
+// u_j = s_j * sum_k C_jk (s_k x_k); `scale` gives s_j.
+// ---------------------------------------------------------------------------
+template <int ST, int RPW, int UNR>
+__device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int ld, int row0, int rows,
+                                           const float* __restrict__ x, const float* __restrict__ v,
+                                           const float* __restrict__ xs, const float* __restrict__ vs,
+                                           const float* __restrict__ scale,
+                                           const float* __restrict__ uold,
+                                           const float* __restrict__ crow,
+                                           float* __restrict__ Uo, float* __restrict__ Wo,
+                                           double* __restrict__ out, int ostride, double* smem) {
+  constexpr int E = Elt<ST>::E;
+  constexpr int EB = Elt<ST>::B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const size_t rowbytes = (size_t)ld * EB;
+  const float* xa = (ST == RAPDB_FP8) ? xs : x;
+  const float* va = (ST == RAPDB_FP8) ? vs : v;
+
+  for (int r = row0 + warp * RPW; r < row0 + rows; r += NWARP * RPW) {
+    const int nr = min(RPW, row0 + rows - r);
+    const uint8_t* p[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) p[q] = Qm + (size_t)(r + (q < nr ? q : 0)) * rowbytes;
+    float acc[RPW][2];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; }
+
+    int c0 = lane * E;
+    // main loop: UNR chunks per row in flight
+    for (; c0 + (UNR - 1) * 32 * E < ld; c0 += UNR * 32 * E) {
+      uint4 raw[UNR][RPW];
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+          raw[uu][q] = (q < nr) ? ld_stream16(p[q] + (size_t)(c0 + uu * 32 * E) * EB) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu) {
+        const int cc = c0 + uu * 32 * E;
+        float xv[E], vv[E];
+#pragma unroll
+        for (int e = 0; e < E; e += 4) {
+          float4 a = __ldg(reinterpret_cast<const float4*>(xa + cc + e));
+          float4 b = __ldg(reinterpret_cast<const float4*>(va + cc + e));
+          xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+          vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          float qe[E];
+          Elt<ST>::cvt(raw[uu][q], qe);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+            acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+          }
+        }
+      }
+    }
+    // tail: fewer than UNR chunks left
+    for (; c0 < ld; c0 += 32 * E) {
+      uint4 raw[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        raw[q] = (q < nr) ? ld_stream16(p[q] + (size_t)c0 * EB) : make_uint4(0, 0, 0, 0);
+      float xv[E], vv[E];
+#pragma unroll
+      for (int e = 0; e < E; e += 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(xa + c0 + e));
+        float4 b = __ldg(reinterpret_cast<const float4*>(va + c0 + e));
+        xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+        vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+      }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float qe[E];
+        Elt<ST>::cvt(raw[q], qe);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+          acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+        }
+      }
+    }
+
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      acc[q][0] = warp_sumf(acc[q][0]);
+      acc[q][1] = warp_sumf(acc[q][1]);
+    }
+    // lanes 0..nr-1 finish one row each
+    double e5[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (lane < nr) {
+      const int j = r + lane;
+      float u = acc[0][0], w = acc[0][1];
+#pragma unroll
+      for (int q = 1; q < RPW; ++q)
+        if (lane == q) { u = acc[q][0]; w = acc[q][1]; }
+      if (ST == RAPDB_FP8) {
+        const float sj = scale[j];
+        u *= sj;
+        w *= sj;
+      }
+      Uo[j] = u;
+      Wo[j] = w;
+      const double xj = x[j], vj = v[j], cj = crow[j];
+      e5[0] = xj * (double)u;
+      e5[1] = vj * (double)w;
+      e5[2] = uold ? vj * (double)uold[j] : 0.0;
+      e5[3] = cj * xj;
+      e5[4] = cj * vj;
+    }
+    // fixed-order sum over the lanes that hold rows
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) {
+      double t = e5[q];
+#pragma unroll
+      for (int o = 1; o < RPW; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      dsum[q] += t;   // identical in lanes 0..RPW-1
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) smem[warp * NDOT + q] = dsum[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NDOT) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += smem[w * NDOT + threadIdx.x];
+    out[threadIdx.x * ostride] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace rapdb_dev

@@ -1,0 +1,256 @@
+// Set-up and stand-alone kernels: storage conversion (BF16 / Jacobi-scaled
+// FP8), input validation, state initialisation, the stand-alone coupling pass
+// and KKT residual used by rapdb_coupling_pass / rapdb_kkt_residual.
+#pragma once
+#include "rapdb_kernels.cuh"
+
+namespace rapdb_dev {
+
+// ---- storage conversion (one pass over Q) --------------------------------
+// BF16: round to nearest, ties to even.
+__global__ void k_quant_bf16(const float* __restrict__ Q, int n, long long rows, int ld,
+                             __nv_bfloat16* __restrict__ out) {
+  const long long total = rows * (long long)n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n;
+    const int col = (int)(e - r * n);
+    out[r * ld + col] = __float2bfloat16_rn(Q[e]);
+  }
+}
+
+// FP8 symmetric Jacobi scaling: r_j = 1/sqrt(Q_jj) (1 when Q_jj <= 0),
+// C_jk = ((Q_jk r_j) r_k) 256 rounded to E4M3 (nearest even, saturating),
+// s_j = sqrt(Q_jj)/16 (1/16 when Q_jj <= 0), so Q~ = S dec(C) S.
+__global__ void k_fp8_scales(const float* __restrict__ Q, int n, int M, int ldv, float* __restrict__ rinv,
+                             float* __restrict__ scale) {
+  const long long total = (long long)M * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n);
+    const int j = (int)(e - (long long)s * n);
+    const float dg = Q[((size_t)s * n + j) * n + j];
+    const float sq = dg > 0.0f ? __fsqrt_rn(dg) : 1.0f;
+    rinv[(size_t)s * ldv + j] = __fdiv_rn(1.0f, sq);
+    scale[(size_t)s * ldv + j] = sq * (1.0f / 16.0f);
+  }
+}
+
+__global__ void k_quant_fp8(const float* __restrict__ Q, int n, int M, int ld, int ldv,
+                            const float* __restrict__ rinv, __nv_fp8_storage_t* __restrict__ out) {
+  const long long total = (long long)M * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n;          // global row (s * n + j)
+    const int col = (int)(e - r * n);
+    const int s = (int)(r / n);
+    const int j = (int)(r - (long long)s * n);
+    const float a = __fmul_rn(Q[e], rinv[(size_t)s * ldv + j]);
+    const float cval = __fmul_rn(__fmul_rn(a, rinv[(size_t)s * ldv + col]), 256.0f);
+    out[r * ld + col] = __nv_cvt_float_to_fp8(cval, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// ---- validation: NaN / Inf anywhere, negative diagonal, lb > ub ----------
+__global__ void k_validate(const float* __restrict__ Q, int n, int M, const float* __restrict__ c, int m,
+                           const float* __restrict__ d, const float* __restrict__ lb,
+                           const float* __restrict__ ub, const float* __restrict__ q0diag,
+                           int* __restrict__ flags) {
+  const long long totalQ = (long long)M * n * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int bad_nan = 0, bad_diag = 0, bad_box = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totalQ; e += stride) {
+    const float v = Q[e];
+    if (!isfinite(v)) bad_nan = 1;
+    const long long r = e / n;
+    const int col = (int)(e - r * n);
+    if ((int)(r % n) == col && v < 0.0f) bad_diag = 1;
+  }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(m + 1) * n; e += stride)
+    if (!isfinite(c[e])) bad_nan = 1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
+    if (!isfinite(lb[e]) || !isfinite(ub[e])) bad_nan = 1;
+    if (lb[e] > ub[e]) bad_box = 1;
+    if (q0diag) {
+      if (!isfinite(q0diag[e])) bad_nan = 1;
+      if (q0diag[e] < 0.0f) bad_diag = 1;
+    }
+  }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += stride)
+    if (!isfinite(d[e])) bad_nan = 1;
+  if (bad_nan) atomicOr(&flags[0], 1);
+  if (bad_diag) atomicOr(&flags[1], 1);
+  if (bad_box) atomicOr(&flags[2], 1);
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int len) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) b[e] = (double)a[e];
+}
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int len) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) b[e] = (float)a[e];
+}
+
+// Start-of-solve state: x^0 into slot 0 (checked against the box), y^0 into
+// slot 0 (checked >= 0), Algorithm 1's initial scalars, deadline.
+__global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ states, int B, double time_limit_s,
+                             int* __restrict__ flags) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const Inst& I = insts[b];
+  for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    const float x = I.xb[0][j];
+    if (!(x >= I.lb[j] && x <= I.ub[j])) atomicOr(&flags[0], 1);
+  }
+  for (int i = threadIdx.x; i < I.m; i += blockDim.x)
+    if (!(I.yb[0][i] >= 0.0)) atomicOr(&flags[1], 1);
+  if (threadIdx.x != 0) return;
+  State& S = states[b];
+  const unsigned long long now = globaltimer();
+  S = State{};
+  restart_scalars(I.P, S);
+  S.sigma0 = S.sigma_prev;
+  S.phase = PH_INIT;
+  S.rel_kkt = S.r_stat = S.r_feas = NAN;
+  S.rel_q = INFINITY;
+  S.deadline_ns = time_limit_s > 0.0 ? (long long)(now + (unsigned long long)(time_limit_s * 1e9)) : 0;
+}
+
+// ---- stand-alone coupling pass (no control) ------------------------------
+template <int ST>
+__global__ void __launch_bounds__(NT) k_pass_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
+                                                   const float* __restrict__ v, const float* __restrict__ XS,
+                                                   const float* __restrict__ VS, const float* __restrict__ uold,
+                                                   float* __restrict__ U, float* __restrict__ W,
+                                                   double* __restrict__ part, int use32) {
+  __shared__ double red[NWARP * NDOT];
+  const Inst& I = insts[0];
+  const int s = blockIdx.x / I.nrb;
+  const int r = blockIdx.x - s * I.nrb;
+  const int i = s + I.s_off;
+  const int row0 = r * I.rb;
+  const int rows = min(I.rb, I.n - row0);
+  const int ldv = I.ldv;
+  double* out = part + (size_t)s * NDOT * I.nrb + r;
+  const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
+  const float* crow = I.c + (size_t)i * ldv;
+  if (use32 || ST == RAPDB_F32) {
+    const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
+    pass_block<RAPDB_F32, 4, 2>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v, nullptr,
+                                nullptr, nullptr, uo, crow, U + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb,
+                                red);
+  } else {
+    constexpr int EB = Elt<ST>::B;
+    const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;
+    pass_block<ST, 4, 2>(Qb, I.ld, row0, rows, x, v, XS ? XS + (size_t)s * ldv : nullptr,
+                         VS ? VS + (size_t)s * ldv : nullptr, I.qscale ? I.qscale + (size_t)s * ldv : nullptr,
+                         uo, crow, U + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb, red);
+  }
+}
+
+// Q_0 row of a stand-alone pass when Q_0 is diagonal or zero, plus the FP8
+// pre-scaled right-hand sides; per-block partials of the i = 0 dots.
+__global__ void __launch_bounds__(NT) k_vec_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
+                                                  const float* __restrict__ v, const float* __restrict__ uold,
+                                                  float* __restrict__ U, float* __restrict__ W,
+                                                  float* __restrict__ XS, float* __restrict__ VS,
+                                                  double* __restrict__ vpart, int use32) {
+  __shared__ double red[NWARP * NDOT];
+  const Inst& I = insts[0];
+  const int j = blockIdx.x * NT + threadIdx.x;
+  double acc[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (j < I.n) {
+    const float xj = x[j], vj = v[j];
+    if (I.storage == RAPDB_FP8 && !use32) {
+      for (int s = 0; s < I.M; ++s) {
+        const float sc = I.qscale[(size_t)s * I.ldv + j];
+        XS[(size_t)s * I.ldv + j] = sc * xj;
+        VS[(size_t)s * I.ldv + j] = sc * vj;
+      }
+    }
+    if (I.s_off) {
+      const double q0d = (I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] : 0.0;
+      const float u = (float)(q0d * xj), w = (float)(q0d * vj);
+      U[j] = u;
+      W[j] = w;
+      acc[D_XU] = (double)xj * u;
+      acc[D_VW] = (double)vj * w;
+      acc[D_VUO] = uold ? (double)vj * uold[j] : 0.0;
+      acc[D_CX] = (double)I.c[j] * xj;
+      acc[D_CV] = (double)I.c[j] * vj;
+    }
+  }
+  block_sum<NDOT>(acc, red);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NDOT; ++q) vpart[(size_t)blockIdx.x * NDOT + q] = acc[q];
+}
+
+// Fixed-order final reduction of a stand-alone pass into dots[(m+1)][5].
+__global__ void __launch_bounds__(NT) k_dots_final(const Inst* __restrict__ insts, const double* __restrict__ part,
+                                                   const double* __restrict__ vpart, double* __restrict__ dots) {
+  const Inst& I = insts[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pq = warp; pq < I.M * NDOT; pq += NWARP) {
+    const double* src = part + (size_t)pq * I.nrb;
+    double t = 0.0;
+    for (int rr = lane; rr < I.nrb; rr += 32) t += src[rr];
+    t = warp_sum(t);
+    if (lane == 0) {
+      const int ss = pq / NDOT, q = pq - ss * NDOT;
+      dots[(size_t)(ss + I.s_off) * NDOT + q] = t;
+    }
+  }
+  if (I.s_off && threadIdx.x < NDOT) {
+    double t = 0.0;
+    for (int bq = 0; bq < I.ncb; ++bq) t += vpart[(size_t)bq * NDOT + threadIdx.x];
+    dots[threadIdx.x] = t;
+  }
+}
+
+// KKT partials at (x, y) from U = Q x (row 0 from the diagonal when Q_0 is
+// not stored): ||r_stat||^2, ||Q_0x+c_0||^2, ||sum_i y_i(Q_ix+c_i)||^2.
+__global__ void __launch_bounds__(NT) k_kkt_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
+                                                  const double* __restrict__ y, const float* __restrict__ U,
+                                                  double* __restrict__ vpart) {
+  __shared__ double red[NWARP * 3];
+  const Inst& I = insts[0];
+  const int j = blockIdx.x * NT + threadIdx.x;
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (j < I.n) {
+    const double xj = x[j];
+    const double u0 = I.s_off ? ((I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] * (double)x[j] : 0.0)
+                              : (double)U[j];
+    const double gf = u0 + (double)I.c[j];
+    double gc = 0.0;
+    for (int i = 1; i <= I.m; ++i)
+      gc += y[i - 1] * ((double)U[(size_t)i * I.ldv + j] + (double)I.c[(size_t)i * I.ldv + j]);
+    const double grad = gf + gc;
+    const double lo = I.lb[j], hi = I.ub[j];
+    const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
+    acc[0] = rs * rs;
+    acc[1] = gf * gf;
+    acc[2] = gc * gc;
+  }
+  block_sum<3>(acc, red);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) vpart[(size_t)blockIdx.x * 3 + q] = acc[q];
+}
+
+__global__ void k_kkt_final(const Inst* __restrict__ insts, const double* __restrict__ vpart,
+                            const double* __restrict__ dots, const double* __restrict__ y, double* __restrict__ g,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  const Inst& I = insts[0];
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int bq = 0; bq < I.ncb; ++bq)
+    for (int q = 0; q < 3; ++q) p[q] += vpart[(size_t)bq * 3 + q];
+  for (int i = 1; i <= I.m; ++i) g[i - 1] = 0.5 * dots[i * NDOT + D_XU] + dots[i * NDOT + D_CX] + I.dcon[i - 1];
+  double rel, rs, rf;
+  kkt_from_partials(I, g, y, p[0], p[1], p[2], rel, rs, rf);
+  out[0] = rel;
+  out[1] = rs;
+  out[2] = rf;
+  out[3] = 0.5 * dots[D_XU] + dots[D_CX];
+}
+
+}  // namespace rapdb_dev

@@ -1,0 +1,305 @@
+"""Python binding of the rAPDB C ABI (include/rapdb.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA library ``librapdb.so``; PyTorch
+provides device memory and the stream.  There is no CPU fallback: importing
+this module fails when the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librapdb.so")
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_BACKTRACK, ERR_MAXITER, ERR_TIMEOUT, ERR_NUMERIC = range(8)
+STATUS_NAMES = ["OK", "INVALID", "CUDA", "NOMEM", "BACKTRACK", "MAXITER", "TIMEOUT", "NUMERIC"]
+YX, XY = 0, 1
+F32, BF16, FP8 = 0, 1, 2
+Q0_DENSE, Q0_DIAG, Q0_ZERO = 0, 1, 2
+RESTART_NONE, RESTART_FIXED, RESTART_GAP = 0, 1, 2
+
+
+class CParams(C.Structure):
+    _fields_ = [
+        ("variant", C.c_int32), ("c_nm", C.c_int32), ("backtracking", C.c_int32), ("restart", C.c_int32),
+        ("mu", C.c_double), ("c_alpha", C.c_double), ("c_beta", C.c_double), ("delta", C.c_double),
+        ("eta", C.c_double), ("tau_bar", C.c_double), ("gamma0", C.c_double),
+        ("restart_period", C.c_int32), ("restart_from_average", C.c_int32),
+        ("xi", C.c_double), ("q", C.c_double),
+        ("gap_first", C.c_int32), ("gap_every", C.c_int32),
+        ("storage", C.c_int32), ("refine", C.c_int32), ("stall_ratio", C.c_double),
+        ("max_iter", C.c_int32), ("max_trials", C.c_int32), ("kkt_every", C.c_int32), ("use_graph", C.c_int32),
+        ("tol", C.c_double), ("time_limit_s", C.c_double),
+        ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32),
+    ]
+
+
+class CInfo(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32), ("trials", C.c_int32), ("restarts", C.c_int32), ("precision_switches", C.c_int32),
+        ("passes", C.c_int32), ("status", C.c_int32),
+        ("rel_kkt", C.c_double), ("r_stat", C.c_double), ("r_feas", C.c_double),
+        ("obj", C.c_double), ("seconds", C.c_double), ("launches", C.c_int64),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librapdb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, I, vp = C.POINTER(CParams), C.POINTER(CInfo), C.c_void_p
+    ctxpp = C.POINTER(vp)
+    sig = {
+        "rapdb_default_params": (None, [P, C.c_int32]),
+        "rapdb_create": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp, P, vp]),
+        "rapdb_solve": (C.c_int, [vp, vp, vp, I]),
+        "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]),
+        "rapdb_coupling_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
+        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp]),
+        "rapdb_create_batched": (C.c_int, [ctxpp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                           C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                           C.POINTER(vp), P, vp]),
+        "rapdb_solve_batched": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), I]),
+        "rapdb_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
+        "rapdb_set_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "rapdb_resume": (C.c_int, [vp, vp, vp, I]),
+        "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rapdb_last_error": (C.c_char_p, [vp]),
+        "rapdb_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class RapdbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rapdb status {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Params:
+    """Mirror of rapdb_params; defaults are the library's (the paper's settings)."""
+    variant: int = YX
+    c_nm: int = 1
+    backtracking: int = 1
+    restart: int = RESTART_FIXED
+    mu: float = 0.0
+    c_alpha: float = 0.4
+    c_beta: float = 0.0
+    delta: float = 0.5
+    eta: float = 0.7
+    tau_bar: float = 1.0
+    gamma0: float = 1.0
+    restart_period: int = 200
+    restart_from_average: int = 0
+    xi: float = 0.04
+    q: float = 0.5
+    gap_first: int = 50
+    gap_every: int = 500
+    storage: int = F32
+    refine: int = 1
+    stall_ratio: float = 0.5
+    max_iter: int = 50000
+    max_trials: int = 60
+    kkt_every: int = 1
+    use_graph: int = 1
+    tol: float = 1e-6
+    time_limit_s: float = 0.0
+    rows_per_block: int = 0
+    gap_inner_max: int = 200
+
+    @classmethod
+    def default(cls, variant: int = YX, **kw) -> "Params":
+        cp = CParams()
+        lib.rapdb_default_params(C.byref(cp), variant)
+        p = cls(**{f.name: getattr(cp, f.name) for f in fields(cls)})
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise AttributeError(k)
+            setattr(p, k, v)
+        return p
+
+    def to_c(self) -> CParams:
+        cp = CParams()
+        for f in fields(self):
+            setattr(cp, f.name, getattr(self, f.name))
+        return cp
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream_handle(device):
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _info_dict(ci: CInfo) -> dict:
+    return {f[0]: getattr(ci, f[0]) for f in CInfo._fields_}
+
+
+def _check(st, ctx=None):
+    if st != OK:
+        msg = lib.rapdb_last_error(ctx)
+        raise RapdbError(st, msg.decode() if msg else "")
+
+
+class Solver:
+    """One QCQP on one GPU.  ``data`` holds torch CUDA float32 tensors with the
+    layout of rapdb_create (see workloads.QCQPData).  The tensors passed in
+    must stay alive while the solver exists (float32 Q may be borrowed)."""
+
+    def __init__(self, data, params: Params | None = None):
+        import torch
+        self.params = params or Params.default()
+        self.n, self.m = int(data.n), int(data.m)
+        self._keep = [data.Q, data.c, data.d, data.lb, data.ub, data.q0diag]
+        for t in self._keep:
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        self.device = data.Q.device
+        self.ctx = C.c_void_p()
+        cp = self.params.to_c()
+        st = lib.rapdb_create(C.byref(self.ctx), self.n, self.m, int(data.q0_kind), _ptr(data.Q),
+                              _ptr(data.q0diag), _ptr(data.c), _ptr(data.d), _ptr(data.lb), _ptr(data.ub),
+                              C.byref(cp), _stream_handle(self.device))
+        _check(st, None)
+        self._log = None
+
+    def close(self):
+        if self.ctx:
+            lib.rapdb_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, x, y, check: bool = True) -> dict:
+        """Run rAPDB from (x, y) (CUDA float32, overwritten with the result)."""
+        ci = CInfo()
+        st = lib.rapdb_solve(self.ctx, _ptr(x), _ptr(y), C.byref(ci))
+        if check and st not in (OK, ERR_MAXITER, ERR_BACKTRACK, ERR_TIMEOUT, ERR_NUMERIC):
+            _check(st, self.ctx)
+        return _info_dict(ci)
+
+    def resume(self, x, y) -> dict:
+        ci = CInfo()
+        st = lib.rapdb_resume(self.ctx, _ptr(x), _ptr(y), C.byref(ci))
+        if st not in (OK, ERR_MAXITER, ERR_BACKTRACK, ERR_TIMEOUT, ERR_NUMERIC):
+            _check(st, self.ctx)
+        return _info_dict(ci)
+
+    def kkt_residual(self, x, y):
+        rel, rs, rf = C.c_double(), C.c_double(), C.c_double()
+        _check(lib.rapdb_kkt_residual(self.ctx, _ptr(x), _ptr(y), C.byref(rel), C.byref(rs), C.byref(rf)),
+               self.ctx)
+        return rel.value, rs.value, rf.value
+
+    def coupling_pass(self, x, v, uold=None):
+        """U[i] = Q_i x, W[i] = Q_i v and the (m+1, 5) float64 dots."""
+        import torch
+        U = torch.empty((self.m + 1, self.n), dtype=torch.float32, device=self.device)
+        W = torch.empty_like(U)
+        dots = torch.empty((self.m + 1, 5), dtype=torch.float64, device=self.device)
+        _check(lib.rapdb_coupling_pass(self.ctx, _ptr(x), _ptr(v), _ptr(uold), _ptr(U), _ptr(W), _ptr(dots)),
+               self.ctx)
+        return U, W, dots
+
+    def set_log(self, capacity: int, iterates: bool = True):
+        """Record tau_k, trials and (optionally) the first `capacity` iterates."""
+        import torch
+        dev = self.device
+        if capacity <= 0:
+            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None), self.ctx)
+            self._log = None
+            return
+        tau = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
+        tr = torch.zeros((capacity,), dtype=torch.int32, device=dev)
+        xl = torch.full((capacity, self.n), float("nan"), dtype=torch.float32, device=dev) if iterates else None
+        yl = (torch.full((capacity, max(self.m, 1)), float("nan"), dtype=torch.float32, device=dev)
+              if iterates else None)
+        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl)), self.ctx)
+        self._log = dict(tau=tau, trials=tr, x=xl, y=yl)
+
+    @property
+    def log(self):
+        return self._log
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t()
+        _check(lib.rapdb_get_state(self.ctx, None, C.byref(n)), self.ctx)
+        buf = C.create_string_buffer(n.value)
+        _check(lib.rapdb_get_state(self.ctx, buf, C.byref(n)), self.ctx)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib.rapdb_set_state(self.ctx, buf, len(blob)), self.ctx)
+
+    def time_pass(self, reps: int = 20):
+        """(average ms per coupling-pass launch, algorithmic bytes per pass)."""
+        ms, b = C.c_double(), C.c_int64()
+        _check(lib.rapdb_time_pass(self.ctx, reps, C.byref(ms), C.byref(b)), self.ctx)
+        return ms.value, b.value
+
+    def tile(self):
+        rb, ctas = C.c_int32(), C.c_int32()
+        lib.rapdb_get_tile(self.ctx, C.byref(rb), C.byref(ctas))
+        return rb.value, ctas.value
+
+
+class BatchedSolver:
+    """Many independent QCQPs (dense Q_0, float32) solved in one device loop."""
+
+    def __init__(self, datas, params: Params | None = None):
+        self.params = params or Params.default()
+        self.B = len(datas)
+        self._keep = [[d.Q, d.c, d.d, d.lb, d.ub] for d in datas]
+        self.ns = [int(d.n) for d in datas]
+        self.ms = [int(d.m) for d in datas]
+        self.device = datas[0].Q.device
+        arr = lambda ts: (C.c_void_p * self.B)(*[t.data_ptr() for t in ts])
+        n = (C.c_int64 * self.B)(*self.ns)
+        m = (C.c_int64 * self.B)(*self.ms)
+        self.ctx = C.c_void_p()
+        cp = self.params.to_c()
+        st = lib.rapdb_create_batched(C.byref(self.ctx), self.B, n, m, arr([d.Q for d in datas]),
+                                      arr([d.c for d in datas]), arr([d.d for d in datas]),
+                                      arr([d.lb for d in datas]), arr([d.ub for d in datas]), C.byref(cp),
+                                      _stream_handle(self.device))
+        _check(st, None)
+
+    def close(self):
+        if self.ctx:
+            lib.rapdb_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, xs, ys) -> list:
+        infos = (CInfo * self.B)()
+        xa = (C.c_void_p * self.B)(*[t.data_ptr() for t in xs])
+        ya = (C.c_void_p * self.B)(*[t.data_ptr() for t in ys])
+        st = lib.rapdb_solve_batched(self.ctx, xa, ya, infos)
+        if st not in (OK, ERR_MAXITER, ERR_BACKTRACK, ERR_TIMEOUT, ERR_NUMERIC):
+            _check(st, self.ctx)
+        return [_info_dict(infos[b]) for b in range(self.B)]

@@ -73,6 +73,19 @@ class QCQPData:
         return QCQPData(self.n, self.m, h(self.Q), h(self.c), h(self.d), h(self.lb),
                         h(self.ub), self.q0_kind, h(self.q0diag), self.name, dict(self.meta))
 
+    def to(self, device) -> "QCQPData":
+        """Copy of the data as contiguous float32 torch tensors on `device`."""
+        import torch
+
+        def t(a):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+            return a.to(device=device, dtype=torch.float32).contiguous()
+        return QCQPData(self.n, self.m, t(self.Q), t(self.c), t(self.d), t(self.lb), t(self.ub),
+                        self.q0_kind, t(self.q0diag), self.name, dict(self.meta))
+
     def dense_q(self) -> np.ndarray:
         """(m+1, n, n) float32 host stack with Q_0 materialised (for the oracle)."""
         h = self.numpy()
