@@ -135,7 +135,11 @@ def make_workload(device, seed=0):
 
 def solver_params(R):
     return R.Params.default(R.YX, c_nm=1, restart=R.RESTART_FIXED, restart_period=200, tol=1e-6,
-                            max_iter=50000)
+                            max_iter=50000, time_limit_s=300.0)
+
+
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def oracle_sample(data, budget_s: float):
@@ -206,14 +210,17 @@ def run_ours(args):
 
     data = make_workload(dev, seed=0)
     torch.cuda.synchronize()
+    log("workload generated")
     p = solver_params(R)
     s = R.Solver(data, p)
+    log(f"solver created, tile {s.tile()}")
     x = torch.zeros(data.n, dtype=torch.float32, device=dev)
     y = torch.zeros(data.m, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         x.zero_()
         y.zero_()
-        s.solve(x, y)
+        wi = s.solve(x, y)
+        log(f"warm-up solve: {wi}")
     torch.cuda.synchronize()
     clocks = Clocks(local)
     infos = []
@@ -232,6 +239,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ck = clocks.stop()
     barrier(world)
+    log(f"timed solves done: {[i['iters'] for i in infos]}")
     ms = e0.elapsed_time(e1)
     t_max = max_over_ranks(ms * 1e-3, world, dev)
     iters = sum(i["iters"] for i in infos)
@@ -250,7 +258,7 @@ def run_ours(args):
                 "frac": achieved / pk["hbm_gbs"], "traffic": PASS_DRAM_BYTES,
                 "peak_kind": f"{pk_kind} copy bandwidth", "frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
                 "kernel": "k_pass<f32> (fused coupling pass)", "bytes_per_launch": pass_bytes,
-                "ms_per_launch": pass_ms}
+                "ms_per_launch": pass_ms, "tile": s.tile()}
 
     # end to end through the C ABI from pinned host buffers (one step: upload,
     # create, solve, read back)
@@ -292,10 +300,18 @@ def run_ours(args):
         del host
 
     cpu = None
+    fp64_check = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
         hd = data.numpy()
         del data
         torch.cuda.empty_cache()
+        # the oracle's float64 KKT residual at the last step's GPU result
+        prob = O.Problem.from_data(hd)
+        rel64, rs64, rf64 = O.kkt_residual(prob, x.cpu().numpy().astype(np.float64),
+                                           y.cpu().numpy().astype(np.float64))
+        fp64_check = {"rel_kkt_fp64_at_result": rel64, "obj_fp64": float(prob.f(x.cpu().numpy().astype(np.float64)))}
+        del prob
         smp = oracle_sample(hd, args.cpu_budget)
         cpu = {"value": smp["iters"] / smp["seconds"], "unit": "iters/s", "cores": smp["cores"],
                "kind": "oracle",
@@ -314,6 +330,7 @@ def run_ours(args):
         "coupling_gbs_in_solve": passes_all * pass_bytes / t_max / 1e9,
         "rel_kkt": max(i["rel_kkt"] for i in infos), "all_converged": ok,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches),
+        "oracle_check": fp64_check,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -88,6 +88,8 @@ typedef struct {
   double time_limit_s;        /* <= 0: none                                           */
   int32_t rows_per_block;     /* coupling pass tile height; 0 = autotune at create   */
   int32_t gap_inner_max;      /* inner iterations of the smoothed-gap box QP          */
+  int32_t pass_variant;       /* tile variant when rows_per_block > 0 (0..4, see     */
+                              /* rapdb_get_tile); ignored when autotuning           */
 } rapdb_params;
 
 typedef struct {
@@ -176,11 +178,14 @@ rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, double *ms_per_pass,
 
 /* Record the first `capacity` iterations of the next rapdb_solve calls:
  * tau_k (device doubles), test evaluations of iteration k (device int32),
- * and, when x_log / y_log are non-NULL, the iterates x^{k+1} (device,
- * capacity x n floats) and y^{k+1} (capacity x m floats).  capacity = 0
+ * and, when non-NULL, the iterates x^{k+1} (x_log: device, capacity x n
+ * floats), y^{k+1} (y_log: capacity x m floats) and the relative KKT
+ * residual measured at iterate k (kkt_log: capacity doubles; entries of
+ * iterations where it was not evaluated are left untouched).  capacity = 0
  * switches logging off.  The buffers are borrowed. */
 rapdb_status rapdb_set_log(rapdb_ctx *ctx, int32_t capacity, double *tau_log,
-                           int32_t *trials_log, float *x_log, float *y_log);
+                           int32_t *trials_log, float *x_log, float *y_log,
+                           double *kkt_log);
 
 /* Batched contexts: B independent problems with their own n_b, m_b, solved
  * together in one device loop with per-instance step sizes, restart counters
@@ -216,8 +221,13 @@ rapdb_status rapdb_set_state(rapdb_ctx *ctx, const void *buf, size_t len);
  * bit for bit where the uninterrupted solve ends. */
 rapdb_status rapdb_resume(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
 
-/* Chosen coupling-pass tile (rows per CTA) and the number of CTAs per pass. */
-rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32_t *ctas);
+/* Coupling-pass tile of the context: rows per CTA, CTAs per pass, rows each
+ * warp streams together, and 16-byte chunks in flight per row (any output
+ * may be NULL).  With rows_per_block = 0 in the parameters, rapdb_create
+ * times every supported tile on the context's own data (CUDA events on its
+ * stream) and keeps the fastest. */
+rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32_t *ctas,
+                            int32_t *rows_per_warp, int32_t *chunks_in_flight);
 
 const char *rapdb_last_error(const rapdb_ctx *ctx);
 void rapdb_destroy(rapdb_ctx *ctx);

@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librapdb.so")
-SOURCES = ["rapdb.cu"]
-DEPS = SOURCES + ["rapdb_device.cuh", "rapdb_kernels.cuh", "rapdb_util.cuh"]
+SOURCES = ["rapdb.cu", "kern_f32.cu", "kern_bf16.cu", "kern_fp8.cu"]
+DEPS = SOURCES + ["rapdb_device.cuh", "rapdb_kernels.cuh", "rapdb_util.cuh", "rapdb_launch.h", "kern_impl.cuh"]
+BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,14 +37,27 @@ def needs_build(lib: str = LIB) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
+    """Compile the translation units in parallel, then link the shared library."""
     if not force and not needs_build():
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-cudart", "shared", "-I", INCLUDE, "-o", LIB + ".tmp",
-           *[os.path.join(CSRC, f) for f in SOURCES], *(extra or [])]
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+              *(extra or [])]
+    procs, objs = [], []
+    for f in SOURCES:
+        obj = os.path.join(BUILD_DIR, f.replace(".cu", ".o"))
+        objs.append(obj)
+        cmd = common + ["-c", os.path.join(CSRC, f), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((f, subprocess.Popen(cmd)))
+    failed = [f for f, pr in procs if pr.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {failed}")
+    link = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs]
     if verbose:
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+        print(" ".join(link), flush=True)
+    subprocess.run(link, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

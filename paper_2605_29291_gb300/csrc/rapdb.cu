@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "rapdb_launch.h"
 #include "rapdb_util.cuh"
 
 using namespace rapdb_dev;
@@ -61,6 +62,8 @@ struct rapdb_ctx {
   cudaGraphExec_t gexec = nullptr;
   int g_bodies = 0;
   int64_t launches = 0;        // kernels launched by the current call
+  int pvar = 0;                // coupling-pass tile variant (kVarRPW / kVarUNR)
+  float tune_ms = 0.0f;        // autotuner: best pass time
   State* h_state = nullptr;    // pinned
   Ctrl* h_ctrl = nullptr;      // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -70,12 +73,36 @@ struct rapdb_ctx {
   // logging
   int log_cap = 0;
   double* tau_log = nullptr;
+  double* kkt_log = nullptr;
   int* trials_log = nullptr;
   float* x_log = nullptr;
   float* y_log = nullptr;
 };
 
 namespace {
+
+// Storage-dispatching launchers (the kernels live in kern_{f32,bf16,fp8}.cu).
+void launch_vec(int storage, dim3 g, size_t smem, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* vm,
+                float* XS, float* VS) {
+  if (storage == RAPDB_F32) launch_vec_f32(g, smem, s, I, S, C, vm, XS, VS);
+  else if (storage == RAPDB_BF16) launch_vec_bf16(g, smem, s, I, S, C, vm, XS, VS);
+  else launch_vec_fp8(g, smem, s, I, S, C, vm, XS, VS);
+}
+
+void launch_pass(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* pm,
+                 const float* XS, const float* VS) {
+  if (storage == RAPDB_F32) launch_pass_f32(vi, g, s, I, S, C, pm, XS, VS);
+  else if (storage == RAPDB_BF16) launch_pass_bf16(vi, g, s, I, S, C, pm, XS, VS);
+  else launch_pass_fp8(vi, g, s, I, S, C, pm, XS, VS);
+}
+
+void launch_plain(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x, const float* v,
+                  const float* XS, const float* VS, const float* uold, float* U, float* W, double* part, int use32,
+                  int* err) {
+  if (storage == RAPDB_F32) launch_plain_f32(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
+  else if (storage == RAPDB_BF16) launch_plain_bf16(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
+  else launch_plain_fp8(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
+}
 
 rapdb_status fail(rapdb_ctx* ctx, rapdb_status st, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -114,10 +141,10 @@ rapdb_status dalloc(rapdb_ctx* ctx, T** p, size_t count) {
   } while (0)
 
 int pick_rows_per_block(int64_t n, int64_t M) {
-  // enough row blocks to fill 152 SMs several times over, rows a multiple of
-  // the 32 rows one CTA covers with one 4-row group per warp
+  // starting tile (and the batched default): 32 rows, one 4-row group per
+  // warp; the autotuner widens it for large single instances
+  (void)n;
   (void)M;
-  if (n <= 256) return 32;
   return 32;
 }
 
@@ -149,6 +176,7 @@ DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
   d.q = p.q;
   d.log_cap = ctx->log_cap;
   d.tau_log = ctx->tau_log;
+  d.kkt_log = ctx->kkt_log;
   d.trials_log = ctx->trials_log;
   d.x_log = ctx->x_log;
   d.y_log = ctx->y_log;
@@ -172,6 +200,8 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
   if (p->max_iter < 0 || p->max_trials < 1) return fail(ctx, RAPDB_ERR_INVALID, "max_iter >= 0, max_trials >= 1");
   if (p->rows_per_block < 0 || (p->rows_per_block % 32) != 0)
     return fail(ctx, RAPDB_ERR_INVALID, "rows_per_block must be 0 (auto) or a multiple of 32");
+  if (p->rows_per_block > 0 && (p->pass_variant < 0 || p->pass_variant >= NVAR))
+    return fail(ctx, RAPDB_ERR_INVALID, "pass_variant out of range");
   return RAPDB_OK;
 }
 
@@ -290,12 +320,13 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   // tiles
   I.rb = rb_override > 0 ? rb_override : pick_rows_per_block(n, M);
   I.nrb = (n + I.rb - 1) / I.rb;
-  I.ncb = (n + NT - 1) / NT;
+  I.ncb = (n + VCOL - 1) / VCOL;
 
   // solver buffers
   const int mm = std::max(m, 1);
   for (int s = 0; s < 2; ++s) {
     AL(I.xb[s], ldv);
+    AL(I.xf[s], ldv);
     AL(I.yb[s], mm);
     AL(I.U[s], (size_t)(m + 1) * ldv);
     AL(I.gb[s], mm);
@@ -305,6 +336,7 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   AL(I.dv, ldv);
   AL(I.gnew, mm);
   AL(I.part, (size_t)std::max(M, 1) * NDOT * I.nrb);
+  AL(I.mcount, std::max(M, 1));
   AL(I.vpart, (size_t)I.ncb * NVP);
   AL(I.dots, (size_t)(m + 1) * NDOT);
   if (p.restart_from_average) {
@@ -345,11 +377,9 @@ rapdb_status finalize_ctx(rapdb_ctx* ctx) {
   for (int b = 0; b < B; ++b) tmp[b] = ctx->hi[b].I;
   CK(cudaMemcpyAsync(ctx->d_inst, tmp.data(), B * sizeof(Inst), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
-  if (ctx->smem_vec > 48 * 1024) {
-    CK(cudaFuncSetAttribute(k_vec<RAPDB_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
-    CK(cudaFuncSetAttribute(k_vec<RAPDB_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
-    CK(cudaFuncSetAttribute(k_vec<RAPDB_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_vec));
-  }
+  CK(prepare_f32());
+  CK(prepare_bf16());
+  CK(prepare_fp8());
   CK(cudaMallocHost((void**)&ctx->h_state, sizeof(State) * B));
   CK(cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl) * 2));
   CK(cudaEventCreateWithFlags(&ctx->ev[0], cudaEventDisableTiming));
@@ -376,17 +406,10 @@ rapdb_status launch_body(rapdb_ctx* ctx, cudaStream_t s) {
   const int st = ctx->storage;
   const dim3 gv(ctx->nvblk), gp(std::max(ctx->npblk, 1)), blk(NT);
   const size_t sm = ctx->smem_vec;
-  auto vec = [&]() {
-    if (st == RAPDB_F32) k_vec<RAPDB_F32><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
-    else if (st == RAPDB_BF16) k_vec<RAPDB_BF16><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
-    else k_vec<RAPDB_FP8><<<gv, blk, sm, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS);
-  };
+  (void)blk;
+  auto vec = [&]() { launch_vec(st, gv, sm, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS); };
   vec();
-  if (ctx->npblk > 0) {
-    if (st == RAPDB_F32) k_pass<RAPDB_F32><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
-    else if (st == RAPDB_BF16) k_pass<RAPDB_BF16><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
-    else k_pass<RAPDB_FP8><<<gp, blk, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
-  }
+  if (ctx->npblk > 0) launch_pass(st, ctx->pvar, gp, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
   if (ctx->variant == RAPDB_XY) vec();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, RAPDB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -453,6 +476,62 @@ rapdb_status run_loop(rapdb_ctx* ctx, int64_t max_bodies) {
   return RAPDB_OK;
 }
 
+// Re-tile instance 0 (single-instance contexts): rows per CTA and the pass
+// block map.  Buffers were sized for the smallest tile (32 rows).
+rapdb_status retile(rapdb_ctx* ctx, int rb) {
+  cudaStream_t st = ctx->stream;
+  Inst& I = ctx->hi[0].I;
+  I.rb = rb;
+  I.nrb = (I.n + rb - 1) / rb;
+  ctx->npblk = I.M * I.nrb;
+  std::vector<int> pmap((size_t)ctx->npblk, 0);
+  CK(cudaMemcpyAsync(ctx->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return RAPDB_OK;
+}
+
+// Autotuner: time every (tile variant, rows per CTA) on the caller's data with
+// CUDA events and keep the fastest.
+rapdb_status autotune(rapdb_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const Inst I0 = ctx->hi[0].I;
+  const int rbs[3] = {32, 64, 128};
+  const int64_t bytes = ctx->hi[0].q_bytes;
+  const int reps = bytes > (int64_t)(256 << 20) ? 2 : 5;
+  float best = 1e30f;
+  int best_v = 0, best_rb = 32;
+  for (int ri = 0; ri < 3; ++ri) {
+    if (ri > 0 && rbs[ri] > 2 * I0.n) break;
+    rapdb_status s = retile(ctx, rbs[ri]);
+    if (s != RAPDB_OK) return s;
+    const int grid = ctx->npblk;
+    for (int vi = 0; vi < NVAR; ++vi) {
+      const Inst& I = ctx->hi[0].I;
+      auto go = [&]() {
+        launch_plain(I.storage, vi, dim3(grid), st, ctx->d_inst, I.xf[0], I.dv, ctx->XS, ctx->VS, nullptr, ctx->tU,
+                     ctx->tW, ctx->tpart, 0, &ctx->d_ctrl->err);
+      };
+      go();
+      CK(cudaGetLastError());
+      CK(cudaEventRecord(ctx->t0, st));
+      for (int r = 0; r < reps; ++r) go();
+      CK(cudaEventRecord(ctx->t1, st));
+      CK(cudaEventSynchronize(ctx->t1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+      if (ms < best) {
+        best = ms;
+        best_v = vi;
+        best_rb = rbs[ri];
+      }
+    }
+  }
+  ctx->pvar = best_v;
+  ctx->tune_ms = best / reps;
+  return retile(ctx, best_rb);
+}
+
 int64_t body_cap(const rapdb_params& p) {
   // every trial is one body; iterations <= max_iter, trials <= max_trials each,
   // plus set-up, restart and KKT bodies
@@ -501,6 +580,7 @@ void rapdb_default_params(rapdb_params* p, int32_t variant) {
   p->time_limit_s = 0.0;
   p->rows_per_block = 0;
   p->gap_inner_max = 200;
+  p->pass_variant = 0;
 }
 
 rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
@@ -548,6 +628,8 @@ rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind
     if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tout, 8);
   }
   if (s == RAPDB_OK) s = finalize_ctx(ctx);
+  if (s == RAPDB_OK && p->rows_per_block == 0) s = autotune(ctx);
+  if (s == RAPDB_OK && p->rows_per_block > 0) ctx->pvar = p->pass_variant;
   if (s == RAPDB_OK) s = build_graph(ctx, 32);
   if (s != RAPDB_OK) {
     g_last_error = ctx->err;
@@ -607,8 +689,8 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
     for (int b = 0; b < B; ++b) {
       const Inst& I = ctx->hi[b].I;
       if (!x[b] || (I.m > 0 && !y[b])) return fail(ctx, RAPDB_ERR_INVALID, "NULL x or y");
-      CK(cudaMemsetAsync(I.xb[0], 0, (size_t)I.ldv * 4, st));
-      CK(cudaMemcpyAsync(I.xb[0], x[b], (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemsetAsync(I.xf[0], 0, (size_t)I.ldv * 4, st));
+      CK(cudaMemcpyAsync(I.xf[0], x[b], (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
       if (I.m > 0) {
         k_f2d<<<1, 256, 0, st>>>(y[b], I.yb[0], I.m);
         ctx->launches += 1;
@@ -632,7 +714,9 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
   if (s != RAPDB_OK) return s;
   CK(cudaEventRecord(ctx->t1, st));
   CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ctx->h_ctrl[0], ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (ctx->h_ctrl[0].err) return fail(ctx, RAPDB_ERR_CUDA, "a bounded wait in the coupling pass gave up");
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
   rapdb_status first_bad = RAPDB_OK;
@@ -640,7 +724,10 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
     const Inst& I = ctx->hi[b].I;
     const State& S = ctx->h_state[b];
     int status = S.phase == PH_DONE ? S.status : RAPDB_ERR_MAXITER;
-    if (x && x[b]) CK(cudaMemcpyAsync(x[b], I.xb[S.xcur], (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
+    if (x && x[b]) {
+      k_d2f<<<(I.n + 255) / 256, 256, 0, st>>>(I.xb[S.xcur], x[b], I.n);
+      ctx->launches += 1;
+    }
     if (y && y[b] && I.m > 0) {
       k_d2f<<<1, 256, 0, st>>>(I.yb[S.ycur], y[b], I.m);
       ctx->launches += 1;
@@ -702,12 +789,8 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v,
   }
   if (I.storage == RAPDB_FP8 || I.s_off)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, vpad, uo, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
-  {
-    const int grid = I.M * I.nrb;
-    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
-    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
-    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt, ctx->tpart, 0);
-  }
+  launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt,
+               ctx->tpart, 0, &ctx->d_ctrl->err);
   k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, dots);
   CK(cudaGetLastError());
   CK(cudaMemcpy2DAsync(U, (size_t)I.n * 4, Ut, (size_t)I.ldv * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
@@ -734,12 +817,8 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
   else if (I.s_off)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, use32);
-  if (I.M > 0) {
-    const int grid = I.M * I.nrb;
-    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
-    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
-    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut, Wt, ctx->tpart, use32);
-  }
+  launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut,
+               Wt, ctx->tpart, use32, &ctx->d_ctrl->err);
   k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots);
   k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, ctx->tvpart);
   k_kkt_final<<<1, 32, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout);
@@ -764,16 +843,15 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, double* ms_per_pass, 
     CK(cudaStreamSynchronize(st));
     xcur = ctx->h_state[0].xcur;
   }
-  const float* x = I.xb[xcur];
+  const float* x = I.xf[xcur];
   const float* v = I.dv;
   const int use32 = (I.storage != RAPDB_F32 && ctx->have_state && ctx->h_state[0].precision == 1) ? 1 : 0;
   if (I.storage == RAPDB_FP8 && !use32)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
-    if (I.storage == RAPDB_F32) k_pass_plain<RAPDB_F32><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, 0);
-    else if (I.storage == RAPDB_BF16) k_pass_plain<RAPDB_BF16><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, use32);
-    else k_pass_plain<RAPDB_FP8><<<grid, NT, 0, st>>>(ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW, ctx->tpart, use32);
+    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW,
+                 ctx->tpart, use32, &ctx->d_ctrl->err);
   };
   launch();   // warm-up
   CK(cudaGetLastError());
@@ -795,7 +873,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, double* ms_per_pass, 
 }
 
 rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, int32_t* trials_log, float* x_log,
-                           float* y_log) {
+                           float* y_log, double* kkt_log) {
   if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
   if (capacity < 0) return fail(ctx, RAPDB_ERR_INVALID, "capacity < 0");
   ctx->log_cap = capacity;
@@ -803,13 +881,17 @@ rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, in
   ctx->trials_log = capacity ? trials_log : nullptr;
   ctx->x_log = capacity ? x_log : nullptr;
   ctx->y_log = capacity ? y_log : nullptr;
+  ctx->kkt_log = capacity ? kkt_log : nullptr;
   return upload_params(ctx);
 }
 
-rapdb_status rapdb_get_tile(const rapdb_ctx* ctx, int32_t* rows_per_block, int32_t* ctas) {
+rapdb_status rapdb_get_tile(const rapdb_ctx* ctx, int32_t* rows_per_block, int32_t* ctas, int32_t* rows_per_warp,
+                            int32_t* chunks_in_flight) {
   if (!ctx) return RAPDB_ERR_INVALID;
   if (rows_per_block) *rows_per_block = ctx->hi[0].I.rb;
   if (ctas) *ctas = ctx->npblk;
+  if (rows_per_warp) *rows_per_warp = kVarRPW[ctx->pvar];
+  if (chunks_in_flight) *chunks_in_flight = kVarUNR[ctx->pvar];
   return RAPDB_OK;
 }
 
@@ -819,7 +901,8 @@ static void state_blobs(rapdb_ctx* ctx, int b, std::vector<std::pair<void*, size
   Inst& I = ctx->hi[b].I;
   const size_t ldv = I.ldv, mm = std::max(I.m, 1), m1 = I.m + 1;
   for (int s = 0; s < 2; ++s) {
-    v.push_back({I.xb[s], ldv * 4});
+    v.push_back({I.xb[s], ldv * 8});
+    v.push_back({I.xf[s], ldv * 4});
     v.push_back({I.yb[s], mm * 8});
     v.push_back({I.U[s], m1 * ldv * 4});
     v.push_back({I.gb[s], mm * 8});

@@ -30,6 +30,8 @@ namespace rapdb_dev {
 
 constexpr int NT = 256;            // threads per CTA, all solver kernels
 constexpr int NWARP = NT / 32;
+constexpr int VCOL = 64;           // vector kernel: columns per CTA
+constexpr int NGRP = NT / VCOL;    // ... and constraint groups per column
 constexpr int NDOT = 5;            // dots per (matrix, row block)
 constexpr int NVP = 12;            // vector-kernel partials per column block
 
@@ -40,7 +42,8 @@ enum Phase : int {
   PH_INIT = 0,       // first pass: U = Q x^0, g(x^0)
   PH_TRIAL = 1,      // one trial of the backtracking loop
   PH_XY2 = 2,        // xy: after the pass, ||a||^2 and ||b||^2 sweep and the test
-  PH_AVG = 3,        // restart from the weighted average: U = Q xbar
+  PH_AVG = 3,        // restart from the weighted average: xbar (vector kernel) ...
+  PH_AVGP = 8,       // ... then U = Q xbar (pass kernel)
   PH_KKT32 = 4,      // quantised storage: float32 pass at x^k for the true KKT
   PH_KKT32B = 5,     // ... and its residual sweep + the refinement decision
   PH_GAPY = 6,       // adaptive restart: smoothed-gap x-subproblem iterations
@@ -62,6 +65,7 @@ struct DevParams {
   int max_iter, max_trials, kkt_every, refine, gap_first, gap_every, gap_inner_max;
   double mu, c_alpha, c_beta, delta, eta, tau_bar, gamma0, tol, stall_ratio, xi, q;
   int log_cap;
+  double* kkt_log;
   double* tau_log;
   int* trials_log;
   float* x_log;
@@ -77,7 +81,7 @@ struct Inst {
   int q0_kind, s_off;   // s_off = 0 when Q_0 is stored, 1 otherwise
   int storage;          // rapdb_storage of Q
   int rb, nrb;          // rows per block, blocks per matrix
-  int ncb;              // column blocks of NT for the vector kernel
+  int ncb;              // column blocks of VCOL for the vector kernel
   int vblk0, pblk0;     // first vector block / pass item of this instance
   const void* Q;        // (M, n, ld) stored matrices
   const float* Q32;     // (M, n, ld32) float32 matrices or null
@@ -88,7 +92,8 @@ struct Inst {
   const float* lb;      // (ldv)
   const float* ub;      // (ldv)
   double dnorm;         // ||d||_2 of the constants
-  float* xb[2];         // x^k / x~ (ldv each, padding zero)
+  double* xb[2];        // x^k / x~ master copies (ldv each, padding zero)
+  float* xf[2];         // float32 copies of xb: the pass right-hand side
   double* yb[2];        // y^k / y~ (m)
   float* U[2];          // Q x^k / Q x~  ((m+1, ldv))
   float* W;             // Q d           ((m+1, ldv))
@@ -97,6 +102,7 @@ struct Inst {
   double* gb[2];        // g(x^k) / g(x^{k-1})  (m)
   double* gnew;         // g(x~) of the current trial (m)
   double* part;         // (M, NDOT, nrb) pass partials
+  unsigned int* mcount; // (M) per-matrix arrival counters of the pass
   double* vpart;        // (ncb, NVP) vector partials
   double* dots;         // (m+1, NDOT) reduced dots
   double* xcum;         // averaging: sum t_k x^{k+1}  (ldv)
@@ -133,7 +139,8 @@ struct State {
 
 struct Ctrl {
   int active;           // instances not yet done
-  int pad_[3];
+  int err;              // a bounded wait in a kernel gave up (never expected)
+  int pad_[2];
 };
 
 // ---------------------------------------------------------------------------
@@ -182,6 +189,20 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* NWARP*
       v[q] = s;
     }
   }
+  __syncthreads();
+}
+
+// Deterministic CTA sum of K doubles per thread, result in every thread.
+template <int K>
+__device__ __forceinline__ void block_allsum(double (&v)[K], double* smem /* NWARP*K */) {
+  block_sum<K>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) smem[q] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = smem[q];
   __syncthreads();
 }
 
@@ -266,6 +287,12 @@ __device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int l
                                            double* __restrict__ out, int ostride, double* smem) {
   constexpr int E = Elt<ST>::E;
   constexpr int EB = Elt<ST>::B;
+  // float32 storage: each 16-byte chunk's E products are summed into a fresh
+  // register, and the chunk sums are added with Kahan compensation, so the
+  // rounding error of a row does not grow with the length of the lane's
+  // accumulation chain.  Quantised storage keeps the plain FMA chain (its
+  // storage error dominates).
+  constexpr bool COMP = (ST == RAPDB_F32);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const size_t rowbytes = (size_t)ld * EB;
@@ -277,9 +304,48 @@ __device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int l
     const uint8_t* p[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) p[q] = Qm + (size_t)(r + (q < nr ? q : 0)) * rowbytes;
-    float acc[RPW][2];
+    float acc[RPW][2], cmp[RPW][2];
 #pragma unroll
-    for (int q = 0; q < RPW; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; }
+    for (int q = 0; q < RPW; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; cmp[q][0] = 0.f; cmp[q][1] = 0.f; }
+
+    auto consume = [&](const uint4 (&raw)[RPW], const float (&xv)[E], const float (&vv)[E]) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float qe[E];
+        Elt<ST>::cvt(raw[q], qe);
+        if (COMP) {
+          float px = qe[0] * xv[0], pv = qe[0] * vv[0];
+#pragma unroll
+          for (int e = 1; e < E; ++e) {
+            px = fmaf(qe[e], xv[e], px);
+            pv = fmaf(qe[e], vv[e], pv);
+          }
+          const float yx = px - cmp[q][0];
+          const float tx = acc[q][0] + yx;
+          cmp[q][0] = (tx - acc[q][0]) - yx;
+          acc[q][0] = tx;
+          const float yv = pv - cmp[q][1];
+          const float tv = acc[q][1] + yv;
+          cmp[q][1] = (tv - acc[q][1]) - yv;
+          acc[q][1] = tv;
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+            acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+          }
+        }
+      }
+    };
+    auto load_rhs = [&](int cc, float (&xv)[E], float (&vv)[E]) {
+#pragma unroll
+      for (int e = 0; e < E; e += 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(xa + cc + e));
+        float4 b = __ldg(reinterpret_cast<const float4*>(va + cc + e));
+        xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+        vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+      }
+    };
 
     int c0 = lane * E;
     // main loop: UNR chunks per row in flight
@@ -292,25 +358,9 @@ __device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int l
           raw[uu][q] = (q < nr) ? ld_stream16(p[q] + (size_t)(c0 + uu * 32 * E) * EB) : make_uint4(0, 0, 0, 0);
 #pragma unroll
       for (int uu = 0; uu < UNR; ++uu) {
-        const int cc = c0 + uu * 32 * E;
         float xv[E], vv[E];
-#pragma unroll
-        for (int e = 0; e < E; e += 4) {
-          float4 a = __ldg(reinterpret_cast<const float4*>(xa + cc + e));
-          float4 b = __ldg(reinterpret_cast<const float4*>(va + cc + e));
-          xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
-          vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
-        }
-#pragma unroll
-        for (int q = 0; q < RPW; ++q) {
-          float qe[E];
-          Elt<ST>::cvt(raw[uu][q], qe);
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
-            acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
-          }
-        }
+        load_rhs(c0 + uu * 32 * E, xv, vv);
+        consume(raw[uu], xv, vv);
       }
     }
     // tail: fewer than UNR chunks left
@@ -320,38 +370,30 @@ __device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int l
       for (int q = 0; q < RPW; ++q)
         raw[q] = (q < nr) ? ld_stream16(p[q] + (size_t)c0 * EB) : make_uint4(0, 0, 0, 0);
       float xv[E], vv[E];
-#pragma unroll
-      for (int e = 0; e < E; e += 4) {
-        float4 a = __ldg(reinterpret_cast<const float4*>(xa + c0 + e));
-        float4 b = __ldg(reinterpret_cast<const float4*>(va + c0 + e));
-        xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
-        vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
-      }
-#pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        float qe[E];
-        Elt<ST>::cvt(raw[q], qe);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
-          acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
-        }
-      }
+      load_rhs(c0, xv, vv);
+      consume(raw, xv, vv);
     }
 
+    // cross-lane sums (float32 trees; the compensation terms are summed
+    // separately and subtracted once)
+    float uu_[RPW], ww_[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-      acc[q][0] = warp_sumf(acc[q][0]);
-      acc[q][1] = warp_sumf(acc[q][1]);
+      uu_[q] = warp_sumf(acc[q][0]);
+      ww_[q] = warp_sumf(acc[q][1]);
+      if (COMP) {
+        uu_[q] -= warp_sumf(cmp[q][0]);
+        ww_[q] -= warp_sumf(cmp[q][1]);
+      }
     }
-    // lanes 0..nr-1 finish one row each
-    double e5[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    // lanes 0..nr-1 finish one row each; each such lane keeps float64 sums of
+    // its rows' dot products (products of two floats are exact in float64)
     if (lane < nr) {
       const int j = r + lane;
-      float u = acc[0][0], w = acc[0][1];
+      float u = uu_[0], w = ww_[0];
 #pragma unroll
       for (int q = 1; q < RPW; ++q)
-        if (lane == q) { u = acc[q][0]; w = acc[q][1]; }
+        if (lane == q) { u = uu_[q]; w = ww_[q]; }
       if (ST == RAPDB_FP8) {
         const float sj = scale[j];
         u *= sj;
@@ -360,20 +402,236 @@ __device__ __forceinline__ void pass_block(const uint8_t* __restrict__ Qm, int l
       Uo[j] = u;
       Wo[j] = w;
       const double xj = x[j], vj = v[j], cj = crow[j];
-      e5[0] = xj * (double)u;
-      e5[1] = vj * (double)w;
-      e5[2] = uold ? vj * (double)uold[j] : 0.0;
-      e5[3] = cj * xj;
-      e5[4] = cj * vj;
+      dsum[0] = fma(xj, (double)u, dsum[0]);
+      dsum[1] = fma(vj, (double)w, dsum[1]);
+      if (uold) dsum[2] = fma(vj, (double)uold[j], dsum[2]);
+      dsum[3] = fma(cj, xj, dsum[3]);
+      dsum[4] = fma(cj, vj, dsum[4]);
     }
-    // fixed-order sum over the lanes that hold rows
+  }
+  // fixed-order sum over the lanes, then over the warps
 #pragma unroll
-    for (int q = 0; q < NDOT; ++q) {
-      double t = e5[q];
+  for (int q = 0; q < NDOT; ++q) {
 #pragma unroll
-      for (int o = 1; o < RPW; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      dsum[q] += t;   // identical in lanes 0..RPW-1
+    for (int o = 1; o < RPW; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) smem[warp * NDOT + q] = dsum[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NDOT) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += smem[w * NDOT + threadIdx.x];
+    out[threadIdx.x * ostride] = s;
+  }
+  __syncthreads();
+}
+
+
+// ---------------------------------------------------------------------------
+// Bulk-copy staging (TMA unit): 1-D cp.async.bulk global -> shared with
+// mbarrier completion.  Every wait is bounded: after ~2 s of polling the wait
+// gives up, sets *err and returns false (never expected on a healthy GPU).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 0 && globaltimer() - t0 > 2000000000ull) {
+      if (err) atomicExch(err, 1);
+      return false;
     }
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The fused coupling pass with the Q rows staged through shared memory.
+// Each warp owns row groups of RPW rows of the CTA's block and streams them
+// through its own ring of NSTAGE slots; a slot holds CWB bytes of each of the
+// group's rows (one bulk copy per row), completed on the slot's mbarrier.
+// Lane 0 keeps NSTAGE slots in flight; the lanes consume 16-byte pieces from
+// shared memory against x and v as in pass_block.  Same outputs as
+// pass_block.  `sbuf` = NWARP*NSTAGE*RPW*CWB bytes, `bars` = NWARP*NSTAGE.
+template <int ST, int RPW, int NSTAGE, int CWB>
+__device__ __forceinline__ void pass_block_tma(const uint8_t* __restrict__ Qm, int ld, int row0, int rows,
+                                               const float* __restrict__ x, const float* __restrict__ v,
+                                               const float* __restrict__ xs, const float* __restrict__ vs,
+                                               const float* __restrict__ scale,
+                                               const float* __restrict__ uold,
+                                               const float* __restrict__ crow,
+                                               float* __restrict__ Uo, float* __restrict__ Wo,
+                                               double* __restrict__ out, int ostride, double* smem,
+                                               uint8_t* sbuf, uint64_t* bars, int* err) {
+  constexpr int E = Elt<ST>::E;
+  constexpr int EB = Elt<ST>::B;
+  constexpr bool COMP = (ST == RAPDB_F32);
+  static_assert(CWB % 16 == 0, "slot width must be a multiple of 16 bytes");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* xa = (ST == RAPDB_FP8) ? xs : x;
+  const float* va = (ST == RAPDB_FP8) ? vs : v;
+  const uint32_t rowbytes = (uint32_t)ld * EB;
+  const int nchunk = (int)((rowbytes + CWB - 1) / CWB);
+  uint8_t* wbuf = sbuf + (size_t)warp * NSTAGE * RPW * CWB;
+  uint64_t* wbar = bars + warp * NSTAGE;
+  // this warp's row groups: r = row0 + (warp + k*NWARP)*RPW
+  const int ngrp_all = (rows + RPW - 1) / RPW;
+  const int ngrp = (ngrp_all > warp) ? (ngrp_all - warp + NWARP - 1) / NWARP : 0;
+  const int T = ngrp * nchunk;
+  if (lane == 0) {
+    for (int sidx = 0; sidx < NSTAGE; ++sidx) mbar_init(&wbar[sidx], 1);
+    fence_proxy_async();
+  }
+  __syncwarp();
+  auto issue = [&](int t) {   // lane 0: item t -> slot t % NSTAGE
+    const int g = t / nchunk, ch = t - g * nchunk;
+    const int r = row0 + (warp + g * NWARP) * RPW;
+    const int nr = min(RPW, row0 + rows - r);
+    const uint32_t off = (uint32_t)ch * CWB;
+    const uint32_t bytes = min((uint32_t)CWB, rowbytes - off);
+    const int slot = t % NSTAGE;
+    mbar_expect_tx(&wbar[slot], bytes * nr);
+    for (int q = 0; q < nr; ++q)
+      bulk_g2s(wbuf + ((size_t)slot * RPW + q) * CWB, Qm + (size_t)(r + q) * rowbytes + off, bytes, &wbar[slot]);
+  };
+  if (lane == 0)
+    for (int t = 0; t < NSTAGE && t < T; ++t) issue(t);
+
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  float acc[RPW][2], cmp[RPW][2];
+#pragma unroll
+  for (int q = 0; q < RPW; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; cmp[q][0] = 0.f; cmp[q][1] = 0.f; }
+  bool ok = true;
+  int t = 0;
+  for (; t < T; ++t) {
+    const int slot = t % NSTAGE;
+    const bool got = mbar_wait_bounded(&wbar[slot], (uint32_t)((t / NSTAGE) & 1), err);
+    if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+    const int g = t / nchunk, ch = t - g * nchunk;
+    const int r = row0 + (warp + g * NWARP) * RPW;
+    const int nr = min(RPW, row0 + rows - r);
+    const uint32_t off = (uint32_t)ch * CWB;
+    const int npieces = (int)(min((uint32_t)CWB, rowbytes - off) / 16);
+    const uint8_t* sb = wbuf + (size_t)slot * RPW * CWB;
+    for (int pc = lane; pc < npieces; pc += 32) {
+      const int col = (int)(off / EB) + pc * E;
+      float xv[E], vv[E];
+#pragma unroll
+      for (int e = 0; e < E; e += 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(xa + col + e));
+        float4 b = __ldg(reinterpret_cast<const float4*>(va + col + e));
+        xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+        vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+      }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (q < nr) {
+          const uint4 raw = *reinterpret_cast<const uint4*>(sb + (size_t)q * CWB + (size_t)pc * 16);
+          float qe[E];
+          Elt<ST>::cvt(raw, qe);
+          if (COMP) {
+            float px = qe[0] * xv[0], pv = qe[0] * vv[0];
+#pragma unroll
+            for (int e = 1; e < E; ++e) {
+              px = fmaf(qe[e], xv[e], px);
+              pv = fmaf(qe[e], vv[e], pv);
+            }
+            const float yx = px - cmp[q][0];
+            const float tx = acc[q][0] + yx;
+            cmp[q][0] = (tx - acc[q][0]) - yx;
+            acc[q][0] = tx;
+            const float yv = pv - cmp[q][1];
+            const float tv = acc[q][1] + yv;
+            cmp[q][1] = (tv - acc[q][1]) - yv;
+            acc[q][1] = tv;
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+              acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+            }
+          }
+        }
+      }
+    }
+    if (ch == nchunk - 1) {
+      // row group complete: cross-lane sums and the row outputs
+      float uu_[RPW], ww_[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        uu_[q] = warp_sumf(acc[q][0]);
+        ww_[q] = warp_sumf(acc[q][1]);
+        if (COMP) {
+          uu_[q] -= warp_sumf(cmp[q][0]);
+          ww_[q] -= warp_sumf(cmp[q][1]);
+        }
+        acc[q][0] = 0.f; acc[q][1] = 0.f; cmp[q][0] = 0.f; cmp[q][1] = 0.f;
+      }
+      if (lane < nr) {
+        const int j = r + lane;
+        float u = uu_[0], w = ww_[0];
+#pragma unroll
+        for (int q = 1; q < RPW; ++q)
+          if (lane == q) { u = uu_[q]; w = ww_[q]; }
+        if (ST == RAPDB_FP8) {
+          const float sj = scale[j];
+          u *= sj;
+          w *= sj;
+        }
+        Uo[j] = u;
+        Wo[j] = w;
+        const double xj = x[j], vj = v[j], cj = crow[j];
+        dsum[0] = fma(xj, (double)u, dsum[0]);
+        dsum[1] = fma(vj, (double)w, dsum[1]);
+        if (uold) dsum[2] = fma(vj, (double)uold[j], dsum[2]);
+        dsum[3] = fma(cj, xj, dsum[3]);
+        dsum[4] = fma(cj, vj, dsum[4]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && t + NSTAGE < T) {
+      fence_proxy_async();   // the slot's generic-proxy reads are done before the async write
+      issue(t + NSTAGE);
+    }
+  }
+  if (!ok && lane == 0) {
+    // drain this warp's copies still in flight (bounded) before the CTA exits
+    for (int t2 = t; t2 < T && t2 < t + NSTAGE; ++t2)
+      mbar_wait_bounded(&wbar[t2 % NSTAGE], (uint32_t)((t2 / NSTAGE) & 1), err);
+  }
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) {
+#pragma unroll
+    for (int o = 1; o < RPW; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
   }
   if (lane == 0) {
 #pragma unroll

@@ -1,7 +1,9 @@
 // Solver kernels of the device-resident rAPDB loop (see rapdb_device.cuh for
-// the body structure).  All control decisions are taken on the device by one
-// thread of the last-arriving CTA of an instance, in FP64, from partial sums
-// reduced in a fixed order (bit-for-bit reproducible runs).
+// the body structure).  All control decisions are taken on the device by the
+// last-arriving CTA of an instance, in FP64, from partial sums reduced in a
+// fixed order (bit-for-bit reproducible runs).  Per-constraint work of the
+// control (g_i, the test's sums, buffer moves) is spread over the CTA's
+// threads; only the scalar decisions run on thread 0.
 //
 // Method (arXiv 2605.29291):
 //   APDB-yx trial (Sec. 3.2, eq. apdb-yx-y):
@@ -29,11 +31,10 @@
 namespace rapdb_dev {
 
 __device__ __forceinline__ bool vec_phase(int ph) {
-  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_XY2 || ph == PH_AVG || ph == PH_KKT32B ||
-         ph == PH_GAPY || ph == PH_GAPF;
+  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_XY2 || ph == PH_AVG || ph == PH_KKT32B;
 }
 __device__ __forceinline__ bool pass_phase(int ph) {
-  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_AVG || ph == PH_KKT32 || ph == PH_GAPY;
+  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_AVGP || ph == PH_KKT32;
 }
 
 __device__ __forceinline__ void finish(State& S, Ctrl* ctrl, int status) {
@@ -45,7 +46,7 @@ __device__ __forceinline__ void finish(State& S, Ctrl* ctrl, int status) {
 // Reset of Algorithm 1's initialisation line at a (re)start:
 // tau_{-1} = tau_0 = tau_bar, sigma_{-1} = gamma_0 tau_bar, gamma = gamma_0,
 // alpha_0 / beta_0 from the parameter recurrences at k = -1.
-__device__ void restart_scalars(const DevParams& P, State& S) {
+static __device__ void restart_scalars(const DevParams& P, State& S) {
   S.tau_prev = P.tau_bar;
   S.sigma_prev = P.gamma0 * P.tau_bar;
   S.gamma = P.gamma0;
@@ -66,17 +67,23 @@ __device__ __forceinline__ bool quantised_refining(const Inst& I, const State& S
   return I.storage != RAPDB_F32 && I.P.refine && I.Q32 != nullptr && S.precision == 0;
 }
 
-// Relative KKT residual from the reduced partials (thread 0).
-__device__ void kkt_from_partials(const Inst& I, const double* g, const double* y, double rs2, double gf2,
-                                  double gc2, double& rel, double& r_stat, double& r_feas) {
-  double rf2 = 0.0, gd2 = 0.0;
-  for (int i = 0; i < I.m; ++i) {
+// Per-constraint terms of the feasibility residual: r_feas_i^2 and
+// (g_i - d_i)^2, summed over this thread's constraints.
+__device__ __forceinline__ void kkt_feas_terms(const Inst& I, const double* g, const double* y, double& rf2,
+                                               double& gd2) {
+  rf2 = 0.0;
+  gd2 = 0.0;
+  for (int i = threadIdx.x; i < I.m; i += NT) {
     const double gi = g[i];
     const double ri = (y[i] > 0.0) ? fabs(gi) : fmax(gi, 0.0);
     rf2 += ri * ri;
     const double t = gi - I.dcon[i];
     gd2 += t * t;
   }
+}
+
+__device__ __forceinline__ void kkt_finish(const Inst& I, double rs2, double gf2, double gc2, double rf2,
+                                           double gd2, double& rel, double& r_stat, double& r_feas) {
   r_stat = sqrt(rs2);
   r_feas = sqrt(rf2);
   const double den_s = 1.0 + fmax(sqrt(gf2), sqrt(gc2));
@@ -84,19 +91,27 @@ __device__ void kkt_from_partials(const Inst& I, const double* g, const double* 
   rel = fmax(r_stat / den_s, r_feas / den_f);
 }
 
-// Acceptance of the current trial (thread 0): averaging weights, step rule,
-// buffer swaps, logging and the fixed-frequency restart rule.
-__device__ void accept_trial(const Inst& I, State& S, double sigma, double alpha_next, double beta_next) {
+// Acceptance, vector part (all threads of the CTA): g^{k-1} <- g^k is done by
+// writing g(x~) over the old slot, and the dual average sum.  k0, gcur0,
+// ycur0, t are the values read before any scalar update.
+__device__ __forceinline__ void accept_vectors(const Inst& I, int k0, int gcur0, int ycur0, double t) {
+  double* gdst = I.gb[gcur0 ^ 1];
+  const double* yn = I.yb[ycur0 ^ 1];
+  for (int i = threadIdx.x; i < I.m; i += NT) {
+    gdst[i] = I.gnew[i];
+    if (I.P.restart_from_average) I.ycum[i] = (k0 == 0 ? 0.0 : I.ycum[i]) + t * yn[i];
+  }
+}
+
+// Acceptance, scalar part (thread 0, after accept_vectors and a barrier):
+// averaging weights, step rule, buffer swaps, logging and the
+// fixed-frequency restart rule.
+static __device__ void accept_scalars(const Inst& I, State& S, double sigma, double alpha_next, double beta_next) {
   const DevParams& P = I.P;
-  const int nx = S.ycur ^ 1;
   const double tau = S.tau;
   const int trials_this = S.trial + 1;
   if (S.k == 0) S.sigma0 = sigma;
   const double t = sigma / S.sigma0;
-  if (P.restart_from_average) {
-    const double* yn = I.yb[nx];
-    for (int i = 0; i < I.m; ++i) I.ycum[i] = (S.k == 0 ? 0.0 : I.ycum[i]) + t * yn[i];
-  }
   S.T += t;
   S.t_last = t;
   double gnext = S.gamma, tnext = tau;
@@ -117,15 +132,13 @@ __device__ void accept_trial(const Inst& I, State& S, double sigma, double alpha
   S.xcur ^= 1;
   S.ycur ^= 1;
   S.ucur ^= 1;
-  double* gdst = I.gb[S.gcur ^ 1];
-  for (int i = 0; i < I.m; ++i) gdst[i] = I.gnew[i];
   S.gcur ^= 1;
   S.gxcur ^= 1;
   S.k += 1;
   S.it += 1;
   S.trial = 0;
   S.fresh = 1;
-  S.obj = 0.5 * I.dots[D_XU] + I.dots[D_CX];
+  S.obj = 0.5 * __ldcg(&I.dots[D_XU]) + __ldcg(&I.dots[D_CX]);
   S.phase = PH_TRIAL;
   if (P.restart == RAPDB_RESTART_FIXED && S.k == P.restart_period) {
     if (P.restart_from_average) {
@@ -138,7 +151,7 @@ __device__ void accept_trial(const Inst& I, State& S, double sigma, double alpha
   }
 }
 
-__device__ void reject_trial(const Inst& I, State& S, Ctrl* ctrl) {
+static __device__ void reject_trial(const Inst& I, State& S, Ctrl* ctrl) {
   S.trial += 1;
   if (S.trial >= I.P.max_trials) {
     finish(S, ctrl, RAPDB_ERR_BACKTRACK);
@@ -149,7 +162,9 @@ __device__ void reject_trial(const Inst& I, State& S, Ctrl* ctrl) {
 }
 
 // ---------------------------------------------------------------------------
-// k_vec: trial step / KKT partials / xy second sweep / averaged restart point
+// k_vec: trial step / KKT partials / xy second sweep / restart points.
+// A CTA covers VCOL columns; its NGRP thread groups split the constraint sum
+// of each column (fixed-order combination in shared memory).
 // ---------------------------------------------------------------------------
 template <int ST>
 __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, State* __restrict__ states,
@@ -158,6 +173,9 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   extern __shared__ double sm[];            // ys[m], yts[m]
   __shared__ double red[NWARP * NVP];
   __shared__ double vfin[NVP];
+  __shared__ double pg[2][NGRP][VCOL];
+  __shared__ float sx[VCOL], sd[VCOL];
+  __shared__ int s_dec;
   const int b = vmap[blockIdx.x];
   const Inst& I = insts[b];
   State& S = states[b];
@@ -167,6 +185,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const int m = I.m, n = I.n, ldv = I.ldv;
   const int cb = blockIdx.x - I.vblk0;
   const int tid = threadIdx.x;
+  const int lc = tid % VCOL, grp = tid / VCOL;
   const int fresh = S.fresh;
   const int k = S.k, it = S.it;
   double* ys = sm;
@@ -175,29 +194,31 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const double tau = S.tau;
   const double sigma = S.gamma * tau;
   const double theta = S.sigma_prev / sigma;
-  const double* ycur = I.yb[S.ycur];
-  const double* gk = I.gb[S.gcur];
-  const double* gp = (k == 0) ? gk : I.gb[S.gcur ^ 1];
+  const int ycur0 = S.ycur, gcur0 = S.gcur;
+  const double* ycur = I.yb[ycur0];
+  const double* gk = I.gb[gcur0];
+  const double* gp = (k == 0) ? gk : I.gb[gcur0 ^ 1];
   for (int i = tid; i < m; i += NT) {
     ys[i] = ycur[i];
     if (phase == PH_TRIAL && P.variant == RAPDB_YX) {
       const double s = (1.0 + theta) * gk[i] - theta * gp[i];
       yts[i] = fmax(0.0, ycur[i] + sigma * s);
     } else if (phase == PH_XY2) {
-      yts[i] = I.yb[S.ycur ^ 1][i];
+      yts[i] = I.yb[ycur0 ^ 1][i];
     } else {
       yts[i] = ycur[i];
     }
   }
   __syncthreads();
   if (cb == 0 && phase == PH_TRIAL && P.variant == RAPDB_YX)
-    for (int i = tid; i < m; i += NT) I.yb[S.ycur ^ 1][i] = yts[i];
+    for (int i = tid; i < m; i += NT) I.yb[ycur0 ^ 1][i] = yts[i];
 
   const bool kkt_due = (phase == PH_TRIAL && fresh &&
                         ((P.kkt_every > 0 && it % P.kkt_every == 0) || it >= P.max_iter)) ||
                        phase == PH_KKT32B;
-  const float* xk = I.xb[S.xcur];
-  float* xt_out = I.xb[S.xcur ^ 1];
+  const double* xk = I.xb[S.xcur];
+  double* xt_out = I.xb[S.xcur ^ 1];
+  float* xt_out32 = I.xf[S.xcur ^ 1];
   const float* Uc = I.U[S.ucur];
   float* Un = I.U[S.ucur ^ 1];
   const float* c = I.c;
@@ -205,23 +226,46 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
 #pragma unroll
   for (int q = 0; q < NVP; ++q) acc[q] = 0.0;
 
-  const int j = cb * NT + tid;
-  if (j < n) {
-    const double xj = (double)xk[j];
-    const float xj32 = xk[j];
+  const int j = cb * VCOL + lc;
+  // ---- constraint sums, split over the NGRP groups ----
+  {
+    double s0 = 0.0, s1 = 0.0;
+    if (j < n) {
+      if (phase == PH_TRIAL || phase == PH_KKT32B) {
+        const float* Us = (phase == PH_KKT32B) ? Un : Uc;
+        for (int i = 1 + grp; i <= m; i += NGRP) {
+          const double v = (double)Us[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j];
+          s0 += ys[i - 1] * v;
+          s1 += yts[i - 1] * v;
+        }
+      } else if (phase == PH_XY2) {
+        for (int i = 1 + grp; i <= m; i += NGRP) {
+          const double dy = yts[i - 1] - ys[i - 1];
+          s0 += dy * ((double)Un[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j]);
+          s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
+        }
+      }
+    }
+    pg[0][grp][lc] = s0;
+    pg[1][grp][lc] = s1;
+  }
+  __syncthreads();
+
+  if (grp == 0 && j < n) {
+    double gc = 0.0, gt = 0.0;
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) {
+      gc += pg[0][g][lc];
+      gt += pg[1][g][lc];
+    }
+    const double xj = xk[j];
+    const float xj32 = I.xf[S.xcur][j];
     const double c0 = c[j];
     const double q0d = (I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] : 0.0;
     if (phase == PH_TRIAL || phase == PH_KKT32B) {
-      // U (or the float32 KKT pass output) at x^k
       const float* Us = (phase == PH_KKT32B) ? Un : Uc;
       const double u0 = (I.s_off ? q0d * (double)xj32 : (double)Us[j]);
       const double gf = u0 + c0;
-      double gc = 0.0, gt = 0.0;
-      for (int i = 1; i <= m; ++i) {
-        const double v = (double)Us[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j];
-        gc += ys[i - 1] * v;
-        gt += yts[i - 1] * v;
-      }
       const double grad = gf + gc;
       if (kkt_due) {
         const double lo = I.lb[j], hi = I.ub[j];
@@ -233,7 +277,6 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       if (phase == PH_KKT32B) {
         if (I.s_off) Un[j] = (float)(q0d * (double)xj32);
       } else {
-        // trial point
         double step;
         if (P.variant == RAPDB_YX) {
           step = gf + gt;
@@ -244,10 +287,15 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         }
         const double lo = I.lb[j], hi = I.ub[j];
         const double xt = fmin(fmax(xj - tau * step, lo), hi);
+        // the iterate is kept in float64 (steps far below one float32 ulp of
+        // x still move it); the pass reads float32 copies of x~ and of d
         const float xt32 = (float)xt;
-        const float d32 = xt32 - xj32;
-        xt_out[j] = xt32;
+        const float d32 = (float)(xt - xj);
+        xt_out[j] = xt;
+        xt_out32[j] = xt32;
         I.dv[j] = d32;
+        sx[lc] = xt32;
+        sd[lc] = d32;
         acc[V_DD] = (double)d32 * (double)d32;
         if (I.s_off) {
           const float u0n = (float)(q0d * (double)xt32);
@@ -260,36 +308,27 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         }
         acc[V_CX0] = c0 * (double)xt32;
         acc[V_CD0] = c0 * (double)d32;
-        if (ST == RAPDB_FP8) {
-          for (int s = 0; s < I.M; ++s) {
-            const float sc = I.qscale[(size_t)s * ldv + j];
-            XS[(size_t)s * ldv + j] = sc * xt32;
-            VS[(size_t)s * ldv + j] = sc * d32;
-          }
-        }
         if (fresh) {
           if (P.log_cap > 0 && it >= 1 && it <= P.log_cap && P.x_log)
-            P.x_log[(size_t)(it - 1) * n + j] = xj32;
+            P.x_log[(size_t)(it - 1) * n + j] = (float)xj;
           if (P.restart_from_average && k >= 1)
             I.xcum[j] = (k == 1 ? 0.0 : I.xcum[j]) + S.t_last * xj;
         }
       }
     } else if (phase == PH_XY2) {
       // a = sum_i dy_i (u~_i + c_i),  b = Q(y^k) d = w_0 + sum_i y_i w_i
-      const float* Ut = Un;
-      double a = 0.0, bb = (double)I.W[j];
-      for (int i = 1; i <= m; ++i) {
-        const double dy = yts[i - 1] - ys[i - 1];
-        a += dy * ((double)Ut[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j]);
-        bb += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
-      }
-      acc[V_AA] = a * a;
+      const double bb = (double)I.W[j] + gt;
+      acc[V_AA] = gc * gc;
       acc[V_BB] = bb * bb;
     } else if (phase == PH_INIT || phase == PH_AVG) {
       // the new start point: x^0 itself, or the weighted average of the run
-      const float xt32 = (phase == PH_INIT) ? xj32 : (float)(I.xcum[j] / S.T);
-      xt_out[j] = xt32;
+      const double xt = (phase == PH_INIT) ? xj : I.xcum[j] / S.T;
+      const float xt32 = (float)xt;
+      xt_out[j] = xt;
+      xt_out32[j] = xt32;
       I.dv[j] = 0.0f;
+      sx[lc] = xt32;
+      sd[lc] = 0.0f;
       if (I.s_off) {
         const float u0n = (float)(q0d * (double)xt32);
         Un[j] = u0n;
@@ -297,11 +336,17 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         acc[V_XU0] = (double)xt32 * (double)u0n;
       }
       acc[V_CX0] = c0 * (double)xt32;
-      if (ST == RAPDB_FP8) {
-        for (int s = 0; s < I.M; ++s) {
-          XS[(size_t)s * ldv + j] = I.qscale[(size_t)s * ldv + j] * xt32;
-          VS[(size_t)s * ldv + j] = 0.0f;
-        }
+    }
+  }
+  if (ST == RAPDB_FP8 && (phase == PH_TRIAL || phase == PH_INIT || phase == PH_AVG)) {
+    // pre-scaled right-hand sides s_i .* x~ and s_i .* d of every stored matrix
+    __syncthreads();
+    if (j < n) {
+      const float xv = sx[lc], dvv = sd[lc];
+      for (int s = grp; s < I.M; s += NGRP) {
+        const float sc = I.qscale[(size_t)s * ldv + j];
+        XS[(size_t)s * ldv + j] = sc * xv;
+        VS[(size_t)s * ldv + j] = sc * dvv;
       }
     }
   }
@@ -324,19 +369,28 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     vfin[tid] = s;
   }
   __syncthreads();
-  if (tid != 0) return;
 
   if (phase == PH_INIT || phase == PH_AVG || phase == PH_TRIAL) {
-    S.dd = vfin[V_DD];
-    for (int q = 0; q < NDOT; ++q) S.dots0[q] = vfin[V_XU0 + q];
+    if (tid == 0) {
+      S.dd = vfin[V_DD];
+      for (int q = 0; q < NDOT; ++q) S.dots0[q] = vfin[V_XU0 + q];
+      if (phase == PH_AVG) S.phase = PH_AVGP;   // the pass of this body forms U = Q xbar
+    }
   }
   if (phase == PH_TRIAL && fresh) {
+    double fe[2] = {0.0, 0.0};
+    if (kkt_due) {
+      kkt_feas_terms(I, gk, ys, fe[0], fe[1]);
+      block_allsum<2>(fe, red);
+    }
+    if (tid != 0) return;
     if (kkt_due) {
       double rel, rs, rf;
-      kkt_from_partials(I, gk, ys, vfin[V_RS], vfin[V_GF], vfin[V_GC], rel, rs, rf);
+      kkt_finish(I, vfin[V_RS], vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
       S.rel_kkt = rel;
       S.r_stat = rs;
       S.r_feas = rf;
+      if (P.kkt_log && it < P.log_cap) P.kkt_log[it] = rel;
       if (!(rel == rel)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
       if (quantised_refining(I, S)) {
         S.rel_q = rel;
@@ -357,71 +411,126 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       S.phase = PH_AVG;
       return;
     }
-    if (P.restart == RAPDB_RESTART_GAP && it >= P.gap_first &&
-        (it == P.gap_first || (it - P.gap_first) % P.gap_every == 0) && S.gap_iter == 0) {
-      // smoothed-gap evaluation at this iterate before the iteration
-      S.fresh = 0;
-      S.gap_iter = 1;
-      S.phase = PH_GAPY;
-      return;
-    }
     S.restarts += S.restart_note;
     S.restart_note = 0;
     S.fresh = 0;
     return;
   }
   if (phase == PH_XY2) {
-    const double tau_ = S.tau;
-    const double sig = S.gamma * tau_;
-    const double th = S.sigma_prev / sig;
-    double ddy = 0.0;
-    for (int i = 0; i < m; ++i) { const double t = yts[i] - ys[i]; ddy += t * t; }
-    ddy *= 0.5;
-    const double dp = 0.5 * S.dd;
-    const double an = P.c_alpha / tau_;
-    const double bn = P.gamma0 * P.c_beta / sig;
-    const double bterm = (bn > 0.0) ? vfin[V_BB] / (2.0 * bn) : (vfin[V_BB] == 0.0 ? 0.0 : INFINITY);
-    const double E = vfin[V_AA] / (2.0 * an) - ddy / sig + bterm - (1.0 / tau_ - th * (S.alpha_k + S.beta_k)) * dp;
-    const bool ok = E <= -P.delta / tau_ * dp - P.delta / sig * ddy;
-    S.trials_total += 1;
-    if (!(E == E)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
-    if (ok || !P.backtracking) accept_trial(I, S, sig, an, bn);
-    else reject_trial(I, S, ctrl);
+    double dy2[1] = {0.0};
+    for (int i = tid; i < m; i += NT) { const double t = yts[i] - ys[i]; dy2[0] += t * t; }
+    block_allsum<1>(dy2, red);
+    const double sig = sigma, an = P.c_alpha / tau, bn = P.gamma0 * P.c_beta / sig;
+    const int k0 = S.k;
+    const double t_acc = sig / (k0 == 0 ? sig : S.sigma0);
+    if (tid == 0) {
+      const double ddy = 0.5 * dy2[0];
+      const double dp = 0.5 * S.dd;
+      const double bterm = (bn > 0.0) ? vfin[V_BB] / (2.0 * bn) : (vfin[V_BB] == 0.0 ? 0.0 : INFINITY);
+      const double E = vfin[V_AA] / (2.0 * an) - ddy / sig + bterm - (1.0 / tau - theta * (S.alpha_k + S.beta_k)) * dp;
+      const bool ok = E <= -P.delta / tau * dp - P.delta / sig * ddy;
+      S.trials_total += 1;
+      s_dec = !(E == E) ? 2 : ((ok || !P.backtracking) ? 1 : 0);
+    }
+    __syncthreads();
+    const int dec = s_dec;
+    if (dec == 1) {
+      accept_vectors(I, k0, gcur0, ycur0, t_acc);
+      __syncthreads();
+      if (tid == 0) accept_scalars(I, S, sig, an, bn);
+    } else if (tid == 0) {
+      if (dec == 2) finish(S, ctrl, RAPDB_ERR_NUMERIC);
+      else reject_trial(I, S, ctrl);
+    }
     return;
   }
   if (phase == PH_KKT32B) {
-    double rel, rs, rf;
-    kkt_from_partials(I, I.gnew, ys, vfin[V_RS], vfin[V_GF], vfin[V_GC], rel, rs, rf);
-    S.rel_kkt = rel;
-    S.r_stat = rs;
-    S.r_feas = rf;
-    if (rel <= P.tol) { finish(S, ctrl, RAPDB_OK); return; }
-    const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
-    S.kkt_ref = rel;
-    if (stalled || S.rel_q <= P.tol) {
-      // switch to the float32 Q: the KKT pass output becomes the current U
-      S.precision = 1;
-      S.switches += 1;
-      S.ucur ^= 1;
-      double* gd = I.gb[S.gcur];
-      for (int i = 0; i < m; ++i) gd[i] = I.gnew[i];
-      restart_scalars(P, S);
-      S.restart_note = 1;
+    double fe[2] = {0.0, 0.0};
+    kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1]);
+    block_allsum<2>(fe, red);
+    if (tid == 0) {
+      double rel, rs, rf;
+      kkt_finish(I, vfin[V_RS], vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
+      S.rel_kkt = rel;
+      S.r_stat = rs;
+      S.r_feas = rf;
+      int dec = 0;
+      if (rel <= P.tol) {
+        dec = 2;
+      } else {
+        const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
+        S.kkt_ref = rel;
+        if (stalled || S.rel_q <= P.tol) dec = 1;
+      }
+      s_dec = dec;
     }
-    S.fresh = 1;
-    S.phase = PH_TRIAL;
+    __syncthreads();
+    const int dec = s_dec;
+    if (dec == 1) {   // switch to the float32 Q: the KKT pass output becomes the current U
+      double* gd = I.gb[gcur0];
+      for (int i = tid; i < m; i += NT) gd[i] = I.gnew[i];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (dec == 2) {
+        finish(S, ctrl, RAPDB_OK);
+      } else {
+        if (dec == 1) {
+          S.precision = 1;
+          S.switches += 1;
+          S.ucur ^= 1;
+          restart_scalars(P, S);
+          S.restart_note = 1;
+        }
+        S.fresh = 1;
+        S.phase = PH_TRIAL;
+      }
+    }
     return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tile variant of the coupling pass: NST == 0 streams Q through registers
+// (RPW rows x UNR 16-byte chunks in flight per lane); NST > 0 stages Q through
+// shared memory with bulk copies (NST slots of CWB bytes per row and warp).
+// ---------------------------------------------------------------------------
+// dynamic shared memory of a bulk-copy variant: the warps' mbarriers (8 bytes
+// each, area rounded up to 128 bytes) followed by the slot buffers
+template <int NST>
+__host__ __device__ constexpr size_t tma_bar_bytes() {
+  return ((size_t)NWARP * NST * 8 + 127) / 128 * 128;
+}
+template <int NST, int RPW, int CWB>
+__host__ __device__ constexpr size_t tma_smem_bytes() {
+  return NST == 0 ? 0 : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB;
+}
+
+template <int ST, int RPW, int UNR, int NST, int CWB>
+__device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, int rows, const float* x,
+                                          const float* v, const float* xs, const float* vs, const float* scale,
+                                          const float* uold, const float* crow, float* Uo, float* Wo, double* out,
+                                          int ostride, double* red, uint8_t* dsm, int* err) {
+  if constexpr (NST == 0) {
+    pass_block<ST, RPW, UNR>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red);
+  } else {
+    uint64_t* bars = reinterpret_cast<uint64_t*>(dsm);
+    uint8_t* sbuf = dsm + tma_bar_bytes<NST>();
+    pass_block_tma<ST, RPW, NST, CWB>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride,
+                                      red, sbuf, bars, err);
   }
 }
 
 // ---------------------------------------------------------------------------
 // k_pass: the fused coupling pass + post-control
 // ---------------------------------------------------------------------------
-template <int ST>
+template <int ST, int RPW, int UNR, int NST, int CWB>
 __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, State* __restrict__ states,
                                              Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
                                              const float* __restrict__ XS, const float* __restrict__ VS) {
+  extern __shared__ __align__(128) uint8_t dsm[];
   __shared__ double red[NWARP * NDOT];
+  __shared__ int s_dec;
   const int b = pmap[blockIdx.x];
   const Inst& I = insts[b];
   State& S = states[b];
@@ -435,8 +544,8 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
   const int rows = min(I.rb, I.n - row0);
   const int ldv = I.ldv;
   const bool use32 = (phase == PH_KKT32) || (ST != RAPDB_F32 && S.precision == 1);
-  const float* x = (phase == PH_KKT32) ? I.xb[S.xcur] : I.xb[S.xcur ^ 1];
-  const float* v = (phase == PH_KKT32) ? I.xb[S.xcur] : I.dv;
+  const float* x = (phase == PH_KKT32) ? I.xf[S.xcur] : I.xf[S.xcur ^ 1];
+  const float* v = (phase == PH_KKT32) ? I.xf[S.xcur] : I.dv;
   const float* uold = (phase == PH_KKT32) ? nullptr : I.U[S.ucur] + (size_t)i * ldv;
   float* Uo = I.U[S.ucur ^ 1] + (size_t)i * ldv;
   float* Wo = I.W + (size_t)i * ldv;
@@ -445,98 +554,160 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
   if (use32 || ST == RAPDB_F32) {
     const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
-    pass_block<RAPDB_F32, 4, 2>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v, nullptr,
-                                nullptr, nullptr, uold, crow, Uo, Wo, out, I.nrb, red);
+    pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,
+                                             nullptr, nullptr, nullptr, uold, crow, Uo, Wo, out, I.nrb, red, dsm,
+                                             &ctrl->err);
   } else {
     constexpr int EB = Elt<ST>::B;
     const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;
-    pass_block<ST, 4, 2>(Qb, I.ld, row0, rows, x, v, XS ? XS + (size_t)s * ldv : nullptr,
-                         VS ? VS + (size_t)s * ldv : nullptr, I.qscale ? I.qscale + (size_t)s * ldv : nullptr,
-                         uold, crow, Uo, Wo, out, I.nrb, red);
+    pass_tile<ST, RPW, UNR, NST, CWB>(Qb, I.ld, row0, rows, x, v, XS ? XS + (size_t)s * ldv : nullptr,
+                                      VS ? VS + (size_t)s * ldv : nullptr,
+                                      I.qscale ? I.qscale + (size_t)s * ldv : nullptr, uold, crow, Uo, Wo, out,
+                                      I.nrb, red, dsm, &ctrl->err);
   }
-  if (!arrive_last(&S.arrive_pass, (unsigned)(I.M * I.nrb))) return;
-
-  // ---- last CTA: fixed-order reduction of the block partials ----
+  // ---- last CTA of matrix s: fixed-order reduction of its row-block partials ----
+  if (!arrive_last(&I.mcount[s], (unsigned)I.nrb)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int pq = warp; pq < I.M * NDOT; pq += NWARP) {
-    const double* src = I.part + (size_t)pq * I.nrb;
+  if (warp < NDOT) {
+    const double* src = I.part + ((size_t)s * NDOT + warp) * I.nrb;
     double t = 0.0;
     for (int rr = lane; rr < I.nrb; rr += 32) t += __ldcg(src + rr);
     t = warp_sum(t);
-    if (lane == 0) {
-      const int ss = pq / NDOT, q = pq - ss * NDOT;
-      I.dots[(size_t)(ss + I.s_off) * NDOT + q] = t;
-    }
+    if (lane == 0) I.dots[(size_t)i * NDOT + warp] = t;
   }
-  if (I.s_off && threadIdx.x < NDOT) I.dots[threadIdx.x] = S.dots0[threadIdx.x];
-  __threadfence_block();
+  // ---- last matrix of the instance: control ----
+  if (!arrive_last(&S.arrive_pass, (unsigned)I.M)) return;
+  const int tid = threadIdx.x;
+  if (I.s_off && tid < NDOT) I.dots[tid] = S.dots0[tid];
   __syncthreads();
-  if (threadIdx.x != 0) return;
 
   const DevParams& P = I.P;
   const int m = I.m;
   const double* D = I.dots;
-  S.passes += 1;
-  // g at the pass point: g_i = 0.5 x'Q_i x + c_i'x + d_i
-  for (int ii = 1; ii <= m; ++ii)
-    I.gnew[ii - 1] = 0.5 * __ldcg(&D[ii * NDOT + D_XU]) + __ldcg(&D[ii * NDOT + D_CX]) + I.dcon[ii - 1];
-
-  if (phase == PH_INIT || phase == PH_AVG) {
-    S.xcur ^= 1;
-    S.ucur ^= 1;
-    double* gd = I.gb[S.gcur];
-    for (int ii = 0; ii < m; ++ii) gd[ii] = I.gnew[ii];
-    S.obj = 0.5 * D[D_XU] + D[D_CX];
-    if (phase == PH_INIT) {
-      S.fresh = 1;
-      S.phase = PH_TRIAL;
-    } else {
-      double* y = I.yb[S.ycur];
-      for (int ii = 0; ii < m; ++ii) y[ii] = I.ycum[ii] / S.T;
-      restart_scalars(P, S);
-      S.restarts += 1;
-      S.fresh = 0;       // the KKT test of this iteration ran at the last iterate
-      S.phase = PH_TRIAL;
+  const int k0 = S.k, gcur0 = S.gcur, ycur0 = S.ycur;
+  // g at the pass point: g_i = 0.5 x'Q_i x + c_i'x + d_i, with the per-phase
+  // per-constraint work fused into the same loop
+  if (phase == PH_TRIAL && P.variant == RAPDB_YX) {
+    const double tau = S.tau;
+    const double sig = S.gamma * tau;
+    const double th = S.sigma_prev / sig;
+    const double* yt = I.yb[ycur0 ^ 1];
+    const double* y = I.yb[ycur0];
+    double acc[3] = {0.0, 0.0, 0.0};   // sum y~_i d'Q_i d, |dg|^2, |dy|^2
+    for (int ii = tid; ii < m; ii += NT) {
+      const double* Di = D + (size_t)(ii + 1) * NDOT;
+      const double vw = __ldcg(&Di[D_VW]);
+      I.gnew[ii] = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+      acc[0] += yt[ii] * vw;
+      const double dgi = __ldcg(&Di[D_VUO]) + __ldcg(&Di[D_CV]) + 0.5 * vw;
+      acc[1] += dgi * dgi;
+      const double t = yt[ii] - y[ii];
+      acc[2] += t * t;
+    }
+    block_allsum<3>(acc, red);
+    const double an = P.c_alpha / sig;
+    const double t_acc = sig / (k0 == 0 ? sig : S.sigma0);
+    if (tid == 0) {
+      const double dQd = __ldcg(&D[D_VW]) + acc[0];
+      const double E = 0.5 * dQd - S.dd / (2.0 * tau) + acc[1] / (2.0 * an) - (1.0 / sig - th * S.alpha_k) * 0.5 * acc[2];
+      const bool ok = E <= -P.delta * S.dd / (2.0 * tau) - P.delta * acc[2] / (2.0 * sig);
+      S.trials_total += 1;
+      S.passes += 1;
+      s_dec = !(E == E) ? 2 : ((ok || !P.backtracking) ? 1 : 0);
+    }
+    __syncthreads();
+    const int dec = s_dec;
+    if (dec == 1) {
+      accept_vectors(I, k0, gcur0, ycur0, t_acc);
+      __syncthreads();
+      if (tid == 0) accept_scalars(I, S, sig, an, 0.0);
+    } else if (tid == 0) {
+      if (dec == 2) finish(S, ctrl, RAPDB_ERR_NUMERIC);
+      else reject_trial(I, S, ctrl);
     }
     return;
   }
+  if (phase == PH_TRIAL) {
+    // xy: dual ascent at the new primal point, then the a/b sweep
+    const double sig = S.gamma * S.tau;
+    const double* y = I.yb[ycur0];
+    double* yt = I.yb[ycur0 ^ 1];
+    for (int ii = tid; ii < m; ii += NT) {
+      const double* Di = D + (size_t)(ii + 1) * NDOT;
+      const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+      I.gnew[ii] = g;
+      yt[ii] = fmax(0.0, y[ii] + sig * g);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      S.passes += 1;
+      S.phase = PH_XY2;
+    }
+    return;
+  }
+  // INIT / AVGP / KKT32: g at the pass point
+  double* gd = I.gb[gcur0];
+  const double T0 = S.T;
+  for (int ii = tid; ii < m; ii += NT) {
+    const double* Di = D + (size_t)(ii + 1) * NDOT;
+    const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+    I.gnew[ii] = g;
+    if (phase != PH_KKT32) gd[ii] = g;
+    if (phase == PH_AVGP) I.yb[ycur0][ii] = I.ycum[ii] / T0;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  S.passes += 1;
   if (phase == PH_KKT32) {
     S.phase = PH_KKT32B;
     return;
   }
-  if (phase == PH_TRIAL) {
-    const double tau = S.tau;
-    const double sig = S.gamma * tau;
-    const double th = S.sigma_prev / sig;
-    if (P.variant == RAPDB_YX) {
-      const double* yt = I.yb[S.ycur ^ 1];
-      const double* y = I.yb[S.ycur];
-      double dQd = D[D_VW], dg2 = 0.0, dy2 = 0.0;
-      for (int ii = 1; ii <= m; ++ii) {
-        const double vw = D[ii * NDOT + D_VW];
-        dQd += yt[ii - 1] * vw;
-        const double dgi = D[ii * NDOT + D_VUO] + D[ii * NDOT + D_CV] + 0.5 * vw;
-        dg2 += dgi * dgi;
-        const double t = yt[ii - 1] - y[ii - 1];
-        dy2 += t * t;
-      }
-      const double an = P.c_alpha / sig;
-      const double E = 0.5 * dQd - S.dd / (2.0 * tau) + dg2 / (2.0 * an) -
-                       (1.0 / sig - th * S.alpha_k) * 0.5 * dy2;
-      const bool ok = E <= -P.delta * S.dd / (2.0 * tau) - P.delta * dy2 / (2.0 * sig);
-      S.trials_total += 1;
-      if (!(E == E)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
-      if (ok || !P.backtracking) accept_trial(I, S, sig, an, 0.0);
-      else reject_trial(I, S, ctrl);
-    } else {
-      // xy: dual ascent at the new primal point, then the a/b sweep
-      const double* y = I.yb[S.ycur];
-      double* yt = I.yb[S.ycur ^ 1];
-      for (int ii = 0; ii < m; ++ii) yt[ii] = fmax(0.0, y[ii] + sig * I.gnew[ii]);
-      (void)th;
-      S.phase = PH_XY2;
-    }
-    return;
+  S.xcur ^= 1;
+  S.ucur ^= 1;
+  S.obj = 0.5 * __ldcg(&D[D_XU]) + __ldcg(&D[D_CX]);
+  if (phase == PH_INIT) {
+    S.fresh = 1;
+    S.phase = PH_TRIAL;
+  } else {
+    restart_scalars(P, S);
+    S.restarts += 1;
+    S.fresh = 0;       // the KKT test of this iteration ran at the last iterate
+    S.phase = PH_TRIAL;
+  }
+}
+
+// ---- stand-alone coupling pass (no control) ------------------------------
+template <int ST, int RPW, int UNR, int NST, int CWB>
+__global__ void __launch_bounds__(NT) k_pass_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
+                                                   const float* __restrict__ v, const float* __restrict__ XS,
+                                                   const float* __restrict__ VS, const float* __restrict__ uold,
+                                                   float* __restrict__ U, float* __restrict__ W,
+                                                   double* __restrict__ part, int use32, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  __shared__ double red[NWARP * NDOT];
+  const Inst& I = insts[0];
+  const int s = blockIdx.x / I.nrb;
+  const int r = blockIdx.x - s * I.nrb;
+  const int i = s + I.s_off;
+  const int row0 = r * I.rb;
+  const int rows = min(I.rb, I.n - row0);
+  const int ldv = I.ldv;
+  double* out = part + (size_t)s * NDOT * I.nrb + r;
+  const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
+  const float* crow = I.c + (size_t)i * ldv;
+  if (use32 || ST == RAPDB_F32) {
+    const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
+    pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,
+                                             nullptr, nullptr, nullptr, uo, crow, U + (size_t)i * ldv,
+                                             W + (size_t)i * ldv, out, I.nrb, red, dsm, err);
+  } else {
+    constexpr int EB = Elt<ST>::B;
+    const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;
+    pass_tile<ST, RPW, UNR, NST, CWB>(Qb, I.ld, row0, rows, x, v, XS ? XS + (size_t)s * ldv : nullptr,
+                                      VS ? VS + (size_t)s * ldv : nullptr,
+                                      I.qscale ? I.qscale + (size_t)s * ldv : nullptr, uo, crow, U + (size_t)i * ldv,
+                                      W + (size_t)i * ldv, out, I.nrb, red, dsm, err);
   }
 }
 

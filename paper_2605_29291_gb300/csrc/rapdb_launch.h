@@ -1,0 +1,47 @@
+// Launchers of the storage-templated solver kernels.  Each storage type
+// (float32, bfloat16, FP8) is compiled in its own translation unit
+// (kern_f32.cu, kern_bf16.cu, kern_fp8.cu) so that the builds run in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace rapdb_dev {
+
+struct Inst;
+struct State;
+struct Ctrl;
+
+// Coupling-pass tile variants picked by the autotuner:
+//   RPW  rows streamed together by one warp,
+//   UNR  16-byte chunks in flight per row and lane (register streaming),
+//   NST  shared-memory slots per warp (bulk-copy staging; 0 = registers),
+//   CWB  bytes of each row per slot.
+constexpr int NVAR = 5;
+constexpr int kVarRPW[NVAR] = {4, 4, 4, 4, 2};
+constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0};
+constexpr int kVarNST[NVAR] = {0, 0, 4, 4, 8};
+constexpr int kVarCWB[NVAR] = {0, 0, 1024, 512, 1024};
+
+// dynamic shared memory of variant vi (8 warps): mbarrier area rounded up to
+// 128 bytes, then 8 * NST * RPW * CWB bytes of slots
+inline size_t var_smem(int vi) {
+  if (kVarNST[vi] == 0) return 0;
+  const size_t bars = ((size_t)8 * kVarNST[vi] * 8 + 127) / 128 * 128;
+  return bars + (size_t)8 * kVarNST[vi] * kVarRPW[vi] * kVarCWB[vi];
+}
+
+#define RAPDB_DECLARE_LAUNCHERS(SUF)                                                                              \
+  cudaError_t prepare_##SUF();                                                                                    \
+  void launch_vec_##SUF(dim3 g, size_t smem, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* vm,    \
+                        float* XS, float* VS);                                                                    \
+  void launch_pass_##SUF(int vi, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* pm,         \
+                         const float* XS, const float* VS);                                                       \
+  void launch_plain_##SUF(int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x, const float* v,          \
+                          const float* XS, const float* VS, const float* uold, float* U, float* W, double* part,  \
+                          int use32, int* err);
+
+RAPDB_DECLARE_LAUNCHERS(f32)
+RAPDB_DECLARE_LAUNCHERS(bf16)
+RAPDB_DECLARE_LAUNCHERS(fp8)
+
+}  // namespace rapdb_dev

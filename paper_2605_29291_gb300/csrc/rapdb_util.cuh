@@ -98,7 +98,8 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   if (b >= B) return;
   const Inst& I = insts[b];
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
-    const float x = I.xb[0][j];
+    const float x = I.xf[0][j];
+    I.xb[0][j] = (double)x;
     if (!(x >= I.lb[j] && x <= I.ub[j])) atomicOr(&flags[0], 1);
   }
   for (int i = threadIdx.x; i < I.m; i += blockDim.x)
@@ -113,39 +114,6 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   S.rel_kkt = S.r_stat = S.r_feas = NAN;
   S.rel_q = INFINITY;
   S.deadline_ns = time_limit_s > 0.0 ? (long long)(now + (unsigned long long)(time_limit_s * 1e9)) : 0;
-}
-
-// ---- stand-alone coupling pass (no control) ------------------------------
-template <int ST>
-__global__ void __launch_bounds__(NT) k_pass_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
-                                                   const float* __restrict__ v, const float* __restrict__ XS,
-                                                   const float* __restrict__ VS, const float* __restrict__ uold,
-                                                   float* __restrict__ U, float* __restrict__ W,
-                                                   double* __restrict__ part, int use32) {
-  __shared__ double red[NWARP * NDOT];
-  const Inst& I = insts[0];
-  const int s = blockIdx.x / I.nrb;
-  const int r = blockIdx.x - s * I.nrb;
-  const int i = s + I.s_off;
-  const int row0 = r * I.rb;
-  const int rows = min(I.rb, I.n - row0);
-  const int ldv = I.ldv;
-  double* out = part + (size_t)s * NDOT * I.nrb + r;
-  const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
-  const float* crow = I.c + (size_t)i * ldv;
-  if (use32 || ST == RAPDB_F32) {
-    const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
-    const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
-    pass_block<RAPDB_F32, 4, 2>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v, nullptr,
-                                nullptr, nullptr, uo, crow, U + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb,
-                                red);
-  } else {
-    constexpr int EB = Elt<ST>::B;
-    const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;
-    pass_block<ST, 4, 2>(Qb, I.ld, row0, rows, x, v, XS ? XS + (size_t)s * ldv : nullptr,
-                         VS ? VS + (size_t)s * ldv : nullptr, I.qscale ? I.qscale + (size_t)s * ldv : nullptr,
-                         uo, crow, U + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb, red);
-  }
 }
 
 // Q_0 row of a stand-alone pass when Q_0 is diagonal or zero, plus the FP8
@@ -245,8 +213,15 @@ __global__ void k_kkt_final(const Inst* __restrict__ insts, const double* __rest
   for (int bq = 0; bq < I.ncb; ++bq)
     for (int q = 0; q < 3; ++q) p[q] += vpart[(size_t)bq * 3 + q];
   for (int i = 1; i <= I.m; ++i) g[i - 1] = 0.5 * dots[i * NDOT + D_XU] + dots[i * NDOT + D_CX] + I.dcon[i - 1];
+  double rf2 = 0.0, gd2 = 0.0;
+  for (int i = 0; i < I.m; ++i) {
+    const double ri = (y[i] > 0.0) ? fabs(g[i]) : fmax(g[i], 0.0);
+    rf2 += ri * ri;
+    const double t = g[i] - I.dcon[i];
+    gd2 += t * t;
+  }
   double rel, rs, rf;
-  kkt_from_partials(I, g, y, p[0], p[1], p[2], rel, rs, rf);
+  kkt_finish(I, p[0], p[1], p[2], rf2, gd2, rel, rs, rf);
   out[0] = rel;
   out[1] = rs;
   out[2] = rf;

@@ -32,7 +32,7 @@ class CParams(C.Structure):
         ("storage", C.c_int32), ("refine", C.c_int32), ("stall_ratio", C.c_double),
         ("max_iter", C.c_int32), ("max_trials", C.c_int32), ("kkt_every", C.c_int32), ("use_graph", C.c_int32),
         ("tol", C.c_double), ("time_limit_s", C.c_double),
-        ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32),
+        ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32), ("pass_variant", C.c_int32),
     ]
 
 
@@ -58,7 +58,7 @@ def _load():
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
         "rapdb_coupling_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
-        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp]),
+        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp]),
         "rapdb_create_batched": (C.c_int, [ctxpp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                            C.POINTER(vp), P, vp]),
@@ -66,7 +66,8 @@ def _load():
         "rapdb_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
         "rapdb_set_state": (C.c_int, [vp, vp, C.c_size_t]),
         "rapdb_resume": (C.c_int, [vp, vp, vp, I]),
-        "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32)]),
         "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rapdb_last_error": (C.c_char_p, [vp]),
         "rapdb_destroy": (None, [vp]),
@@ -118,6 +119,7 @@ class Params:
     time_limit_s: float = 0.0
     rows_per_block: int = 0
     gap_inner_max: int = 200
+    pass_variant: int = 0
 
     @classmethod
     def default(cls, variant: int = YX, **kw) -> "Params":
@@ -225,7 +227,7 @@ class Solver:
         import torch
         dev = self.device
         if capacity <= 0:
-            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None), self.ctx)
+            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None, None), self.ctx)
             self._log = None
             return
         tau = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
@@ -233,8 +235,9 @@ class Solver:
         xl = torch.full((capacity, self.n), float("nan"), dtype=torch.float32, device=dev) if iterates else None
         yl = (torch.full((capacity, max(self.m, 1)), float("nan"), dtype=torch.float32, device=dev)
               if iterates else None)
-        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl)), self.ctx)
-        self._log = dict(tau=tau, trials=tr, x=xl, y=yl)
+        kk = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
+        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl), _ptr(kk)), self.ctx)
+        self._log = dict(tau=tau, trials=tr, x=xl, y=yl, kkt=kk)
 
     @property
     def log(self):
@@ -257,10 +260,11 @@ class Solver:
         _check(lib.rapdb_time_pass(self.ctx, reps, C.byref(ms), C.byref(b)), self.ctx)
         return ms.value, b.value
 
-    def tile(self):
-        rb, ctas = C.c_int32(), C.c_int32()
-        lib.rapdb_get_tile(self.ctx, C.byref(rb), C.byref(ctas))
-        return rb.value, ctas.value
+    def tile(self) -> dict:
+        rb, ctas, rpw, unr = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        lib.rapdb_get_tile(self.ctx, C.byref(rb), C.byref(ctas), C.byref(rpw), C.byref(unr))
+        return {"rows_per_block": rb.value, "ctas": ctas.value, "rows_per_warp": rpw.value,
+                "chunks_in_flight": unr.value}
 
 
 class BatchedSolver:

@@ -40,7 +40,7 @@ def test_binding_loads_and_mirrors_defaults():
     assert yx.xi == gp["xi"]["value"] and yx.q == gp["q"]["value"]
     assert yx.gap_first == gp["gap_first"]["yx"] and xy.gap_first == gp["gap_first"]["xy"]
     # struct layout: the ctypes mirror must match the C struct size
-    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4
+    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8
 
 
 def test_create_rejects_bad_sizes_without_touching_the_gpu():
