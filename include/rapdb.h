@@ -229,6 +229,33 @@ rapdb_status rapdb_resume(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
 rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32_t *ctas,
                             int32_t *rows_per_warp, int32_t *chunks_in_flight);
 
+/* The coupling pass of rapdb_coupling_pass for callers that cannot allocate
+ * device memory (no context; the paper has no counterpart to this call).
+ * Creating a context calls cudaMalloc; callers working inside another
+ * framework's memory pool or a fixed, pre-planned memory budget, real-time
+ * loops that must not enter the allocator, and code recording a CUDA graph
+ * cannot do that.  This call allocates nothing: its only scratch, the
+ * per-block float64 partial dots, lives in a fixed array of 131072 doubles
+ * (1 MiB) that the library reserves on every GPU that loads it, until the
+ * process exits.
+ *   Q     device, (m+1, n, n) float32, Q_0 first, symmetric, 16-byte aligned
+ *   c     device, (m+1, n);  x, v: device, n floats, 16-byte aligned
+ *   uold  device, (m+1, n) or NULL (then the third dot is zero)
+ *   U, W  device outputs, (m+1, n): U[i] = Q_i x, W[i] = Q_i v
+ *   dots  device output, (m+1, 5) doubles as in rapdb_coupling_pass
+ * Limits: n % 4 == 0 and (m+1) * 5 * ceil(n/32) <= 131072 (e.g. n = 4096 with
+ * m up to 203); otherwise RAPDB_ERR_INVALID and nothing runs.  The call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = default stream).  The
+ * first call on each device finds the scratch array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array, so calls whose work
+ * overlaps on the GPU (different streams without ordering, or several host
+ * threads) race and give wrong results: order them on one stream.  Each call
+ * overwrites every scratch slot it reads, so no clearing is needed. */
+rapdb_status rapdb_coupling_pass_noalloc(int64_t n, int64_t m, const float *Q, const float *c,
+                                         const float *x, const float *v, const float *uold,
+                                         float *U, float *W, double *dots, void *stream);
+
 const char *rapdb_last_error(const rapdb_ctx *ctx);
 void rapdb_destroy(rapdb_ctx *ctx);
 

@@ -69,6 +69,7 @@ def _load():
         "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]),
         "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rapdb_coupling_pass_noalloc": (C.c_int, [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "rapdb_last_error": (C.c_char_p, [vp]),
         "rapdb_destroy": (None, [vp]),
     }
@@ -265,6 +266,25 @@ class Solver:
         lib.rapdb_get_tile(self.ctx, C.byref(rb), C.byref(ctas), C.byref(rpw), C.byref(unr))
         return {"rows_per_block": rb.value, "ctas": ctas.value, "rows_per_warp": rpw.value,
                 "chunks_in_flight": unr.value}
+
+
+def coupling_pass_noalloc(Q, c, x, v, uold=None, U=None, W=None, dots=None):
+    """The context-free coupling pass that allocates no device memory in the
+    library (see rapdb_coupling_pass_noalloc in include/rapdb.h).  Q is the
+    (m+1, n, n) float32 stack; the outputs may be passed in preallocated."""
+    import torch
+    M, n = int(Q.shape[0]), int(Q.shape[1])
+    if U is None:
+        U = torch.empty((M, n), dtype=torch.float32, device=Q.device)
+    if W is None:
+        W = torch.empty((M, n), dtype=torch.float32, device=Q.device)
+    if dots is None:
+        dots = torch.empty((M, 5), dtype=torch.float64, device=Q.device)
+    st = lib.rapdb_coupling_pass_noalloc(n, M - 1, _ptr(Q), _ptr(c), _ptr(x), _ptr(v), _ptr(uold), _ptr(U),
+                                         _ptr(W), _ptr(dots), _stream_handle(Q.device))
+    if st != OK:
+        raise RapdbError(st, "rapdb_coupling_pass_noalloc rejected the call (sizes, alignment or scratch limit)")
+    return U, W, dots
 
 
 class BatchedSolver:
