@@ -10,19 +10,21 @@ namespace rapdb_dev {
 
 static_assert(NWARP == 8, "var_smem assumes 8 warps per CTA");
 static_assert(tma_smem_bytes<4, 4, 1024>() == 256 + 8 * 4 * 4 * 1024, "smem layout");
-static_assert(tma_smem_bytes<8, 2, 1024>() == 512 + 8 * 8 * 2 * 1024, "smem layout");
+static_assert(tma_smem_bytes<3, 0, 32768>() == 128 + 1024 + 3 * 32768, "smem layout");
 
 // Opt every bulk-copy variant in to its dynamic shared memory size.
 cudaError_t RAPDB_CAT(prepare_, RAPDB_SUF)() {
   cudaError_t e = cudaSuccess;
 #define RAPDB_ATTR(K, B)                                                                       \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(B));
-  RAPDB_ATTR((k_pass<RAPDB_ST, 4, 0, 4, 1024>), (tma_smem_bytes<4, 4, 1024>()))
   RAPDB_ATTR((k_pass<RAPDB_ST, 4, 0, 4, 512>), (tma_smem_bytes<4, 4, 512>()))
-  RAPDB_ATTR((k_pass<RAPDB_ST, 2, 0, 8, 1024>), (tma_smem_bytes<8, 2, 1024>()))
-  RAPDB_ATTR((k_pass_plain<RAPDB_ST, 4, 0, 4, 1024>), (tma_smem_bytes<4, 4, 1024>()))
+  RAPDB_ATTR((k_pass<RAPDB_ST, 0, 0, 3, 32768>), (tma_smem_bytes<3, 0, 32768>()))
+  RAPDB_ATTR((k_pass<RAPDB_ST, 0, 0, 4, 16384>), (tma_smem_bytes<4, 0, 16384>()))
+  RAPDB_ATTR((k_pass<RAPDB_ST, 0, 0, 3, 65536>), (tma_smem_bytes<3, 0, 65536>()))
   RAPDB_ATTR((k_pass_plain<RAPDB_ST, 4, 0, 4, 512>), (tma_smem_bytes<4, 4, 512>()))
-  RAPDB_ATTR((k_pass_plain<RAPDB_ST, 2, 0, 8, 1024>), (tma_smem_bytes<8, 2, 1024>()))
+  RAPDB_ATTR((k_pass_plain<RAPDB_ST, 0, 0, 3, 32768>), (tma_smem_bytes<3, 0, 32768>()))
+  RAPDB_ATTR((k_pass_plain<RAPDB_ST, 0, 0, 4, 16384>), (tma_smem_bytes<4, 0, 16384>()))
+  RAPDB_ATTR((k_pass_plain<RAPDB_ST, 0, 0, 3, 65536>), (tma_smem_bytes<3, 0, 65536>()))
 #undef RAPDB_ATTR
   return e;
 }
@@ -37,9 +39,10 @@ void RAPDB_CAT(launch_pass_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const In
                                         const int* pm, const float* XS, const float* VS) {
   switch (vi) {
     case 1: k_pass<RAPDB_ST, 4, 4, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
-    case 2: k_pass<RAPDB_ST, 4, 0, 4, 1024><<<g, NT, var_smem(2), s>>>(I, S, C, pm, XS, VS); break;
-    case 3: k_pass<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(3), s>>>(I, S, C, pm, XS, VS); break;
-    case 4: k_pass<RAPDB_ST, 2, 0, 8, 1024><<<g, NT, var_smem(4), s>>>(I, S, C, pm, XS, VS); break;
+    case 2: k_pass<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(2), s>>>(I, S, C, pm, XS, VS); break;
+    case 3: k_pass<RAPDB_ST, 0, 0, 3, 32768><<<g, NT, var_smem(3), s>>>(I, S, C, pm, XS, VS); break;
+    case 4: k_pass<RAPDB_ST, 0, 0, 4, 16384><<<g, NT, var_smem(4), s>>>(I, S, C, pm, XS, VS); break;
+    case 5: k_pass<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, S, C, pm, XS, VS); break;
     default: k_pass<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
   }
 }
@@ -49,9 +52,10 @@ void RAPDB_CAT(launch_plain_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const I
                                          float* U, float* W, double* part, int use32, int* err) {
   switch (vi) {
     case 1: k_pass_plain<RAPDB_ST, 4, 4, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 2: k_pass_plain<RAPDB_ST, 4, 0, 4, 1024><<<g, NT, var_smem(2), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 3: k_pass_plain<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(3), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 4: k_pass_plain<RAPDB_ST, 2, 0, 8, 1024><<<g, NT, var_smem(4), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
+    case 2: k_pass_plain<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(2), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
+    case 3: k_pass_plain<RAPDB_ST, 0, 0, 3, 32768><<<g, NT, var_smem(3), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
+    case 4: k_pass_plain<RAPDB_ST, 0, 0, 4, 16384><<<g, NT, var_smem(4), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
+    case 5: k_pass_plain<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
     default: k_pass_plain<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
   }
 }

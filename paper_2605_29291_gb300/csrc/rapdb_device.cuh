@@ -646,4 +646,177 @@ __device__ __forceinline__ void pass_block_tma(const uint8_t* __restrict__ Qm, i
   __syncthreads();
 }
 
+
+// The fused coupling pass with whole rows staged through shared memory.
+// The CTA's row block [row0, row0+rows) of one matrix is contiguous in HBM; it
+// is streamed in stages of SR = SB / rowbytes rows (one bulk copy per stage,
+// NST slots in flight).  Thread t owns the 16-byte pieces t, t+NT, ... of
+// every row, so its x/v slices serve all SR rows of a stage; each stage ends
+// with a fixed-order CTA reduction of the rows' partial sums (warp shuffles,
+// then the 8 warps in order).  Requires rowbytes <= SB (checked by the caller).
+// `dsm` = [NST mbarriers | 2 x NWARP x SRMAX x 2 floats | NST x SB slots].
+constexpr int SRMAX = 8;
+template <int SB, int NST>
+__host__ __device__ constexpr size_t rows_smem_bytes() {
+  return (size_t)128 + (size_t)2 * NWARP * SRMAX * 2 * 4 + (size_t)NST * SB;
+}
+
+template <int ST, int SB, int NST>
+__device__ __forceinline__ void pass_block_rows(const uint8_t* __restrict__ Qm, int ld, int row0, int rows,
+                                                const float* __restrict__ x, const float* __restrict__ v,
+                                                const float* __restrict__ xs, const float* __restrict__ vs,
+                                                const float* __restrict__ scale,
+                                                const float* __restrict__ uold,
+                                                const float* __restrict__ crow,
+                                                float* __restrict__ Uo, float* __restrict__ Wo,
+                                                double* __restrict__ out, int ostride, double* smem,
+                                                uint8_t* dsm, int* err) {
+  constexpr int E = Elt<ST>::E;
+  constexpr int EB = Elt<ST>::B;
+  constexpr bool COMP = (ST == RAPDB_F32);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* xa = (ST == RAPDB_FP8) ? xs : x;
+  const float* va = (ST == RAPDB_FP8) ? vs : v;
+  const uint32_t rowbytes = (uint32_t)ld * EB;
+  const int npc = (int)(rowbytes / 16);                   // pieces per row
+  const int SR = min(SRMAX, max(1, (int)(SB / rowbytes)));
+  const int T = (rows + SR - 1) / SR;
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
+  float* red2 = reinterpret_cast<float*>(dsm + 128);      // [2][NWARP][SRMAX][2]
+  uint8_t* sbuf = dsm + 128 + (size_t)2 * NWARP * SRMAX * 2 * 4;
+  if (tid == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(&full[k], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {   // thread 0: stage t -> slot t % NST
+    const int r = row0 + t * SR;
+    const int nr = min(SR, row0 + rows - r);
+    const int slot = t % NST;
+    mbar_expect_tx(&full[slot], (uint32_t)nr * rowbytes);
+    bulk_g2s(sbuf + (size_t)slot * SB, Qm + (size_t)r * rowbytes, (uint32_t)nr * rowbytes, &full[slot]);
+  };
+  if (tid == 0)
+    for (int t = 0; t < NST && t < T; ++t) issue(t);
+
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int t = 0; t < T; ++t) {
+    const int slot = t % NST;
+    const bool got = mbar_wait_bounded(&full[slot], (uint32_t)((t / NST) & 1), err);
+    if (!__syncthreads_and(got)) {
+      // give up: drain the copies still in flight, then leave
+      if (tid == 0)
+        for (int t2 = t; t2 < T && t2 < t + NST; ++t2)
+          mbar_wait_bounded(&full[t2 % NST], (uint32_t)((t2 / NST) & 1), err);
+      __syncthreads();
+      break;
+    }
+    const int r = row0 + t * SR;
+    const int nr = min(SR, row0 + rows - r);
+    const uint8_t* sb = sbuf + (size_t)slot * SB;
+    float acc[SRMAX][2], cmp[SRMAX][2];
+#pragma unroll
+    for (int q = 0; q < SRMAX; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; cmp[q][0] = 0.f; cmp[q][1] = 0.f; }
+    for (int pc = tid; pc < npc; pc += NT) {
+      const int col = pc * E;
+      float xv[E], vv[E];
+#pragma unroll
+      for (int e = 0; e < E; e += 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(xa + col + e));
+        float4 b = __ldg(reinterpret_cast<const float4*>(va + col + e));
+        xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+        vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+      }
+#pragma unroll
+      for (int q = 0; q < SRMAX; ++q) {
+        if (q < nr) {
+          const uint4 raw = *reinterpret_cast<const uint4*>(sb + (size_t)q * rowbytes + (size_t)pc * 16);
+          float qe[E];
+          Elt<ST>::cvt(raw, qe);
+          if (COMP) {
+            float px = qe[0] * xv[0], pv = qe[0] * vv[0];
+#pragma unroll
+            for (int e = 1; e < E; ++e) {
+              px = fmaf(qe[e], xv[e], px);
+              pv = fmaf(qe[e], vv[e], pv);
+            }
+            const float yx = px - cmp[q][0];
+            const float tx = acc[q][0] + yx;
+            cmp[q][0] = (tx - acc[q][0]) - yx;
+            acc[q][0] = tx;
+            const float yv = pv - cmp[q][1];
+            const float tv = acc[q][1] + yv;
+            cmp[q][1] = (tv - acc[q][1]) - yv;
+            acc[q][1] = tv;
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+              acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+            }
+          }
+        }
+      }
+    }
+    // warp sums of each row's partials -> red2[par][warp][q]
+    float* rw = red2 + (size_t)(t & 1) * NWARP * SRMAX * 2;
+#pragma unroll
+    for (int q = 0; q < SRMAX; ++q) {
+      if (q < nr) {
+        float a0 = warp_sumf(acc[q][0]), a1 = warp_sumf(acc[q][1]);
+        if (COMP) {
+          a0 -= warp_sumf(cmp[q][0]);
+          a1 -= warp_sumf(cmp[q][1]);
+        }
+        if (lane == 0) {
+          rw[(warp * SRMAX + q) * 2 + 0] = a0;
+          rw[(warp * SRMAX + q) * 2 + 1] = a1;
+        }
+      }
+    }
+    __syncthreads();   // the slot is consumed and the warp sums are visible
+    if (tid == 0 && t + NST < T) {
+      fence_proxy_async();
+      issue(t + NST);
+    }
+    if (tid < nr) {
+      const int q = tid;
+      float u = 0.f, w = 0.f;
+      for (int wq = 0; wq < NWARP; ++wq) {
+        u += rw[(wq * SRMAX + q) * 2 + 0];
+        w += rw[(wq * SRMAX + q) * 2 + 1];
+      }
+      const int j = r + q;
+      if (ST == RAPDB_FP8) {
+        const float sj = scale[j];
+        u *= sj;
+        w *= sj;
+      }
+      Uo[j] = u;
+      Wo[j] = w;
+      const double xj = x[j], vj = v[j], cj = crow[j];
+      dsum[0] = fma(xj, (double)u, dsum[0]);
+      dsum[1] = fma(vj, (double)w, dsum[1]);
+      if (uold) dsum[2] = fma(vj, (double)uold[j], dsum[2]);
+      dsum[3] = fma(cj, xj, dsum[3]);
+      dsum[4] = fma(cj, vj, dsum[4]);
+    }
+  }
+  // fixed-order sum of the row-finishing threads' dots (threads 0..SRMAX-1 of warp 0)
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) {
+#pragma unroll
+    for (int o = 1; o < SRMAX; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+  }
+  if (tid < NDOT) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q)
+      if (q == tid) s = dsum[q];
+    out[tid * ostride] = s;
+  }
+  __syncthreads();
+  (void)smem;
+}
+
 }  // namespace rapdb_dev

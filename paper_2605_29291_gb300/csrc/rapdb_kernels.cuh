@@ -363,10 +363,15 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   if (!arrive_last(&S.arrive_vec, (unsigned)I.ncb)) return;
 
   // ---- last CTA of this instance: fixed-order reduction + control ----
-  if (tid < NVP) {
-    double s = 0.0;
-    for (int bq = 0; bq < I.ncb; ++bq) s += __ldcg(&I.vpart[(size_t)bq * NVP + tid]);
-    vfin[tid] = s;
+  // (one warp per partial slot, lanes striding over the column blocks)
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int q = warp; q < NVP; q += NWARP) {
+      double s = 0.0;
+      for (int bq = lane; bq < I.ncb; bq += 32) s += __ldcg(&I.vpart[(size_t)bq * NVP + q]);
+      s = warp_sum(s);
+      if (lane == 0) vfin[q] = s;
+    }
   }
   __syncthreads();
 
@@ -493,7 +498,8 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
 // ---------------------------------------------------------------------------
 // Tile variant of the coupling pass: NST == 0 streams Q through registers
 // (RPW rows x UNR 16-byte chunks in flight per lane); NST > 0 stages Q through
-// shared memory with bulk copies (NST slots of CWB bytes per row and warp).
+// shared memory with bulk copies: per warp (NST slots of CWB bytes per row,
+// RPW > 0), or per CTA in whole-row stages of CWB bytes (RPW == 0).
 // ---------------------------------------------------------------------------
 // dynamic shared memory of a bulk-copy variant: the warps' mbarriers (8 bytes
 // each, area rounded up to 128 bytes) followed by the slot buffers
@@ -503,7 +509,7 @@ __host__ __device__ constexpr size_t tma_bar_bytes() {
 }
 template <int NST, int RPW, int CWB>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-  return NST == 0 ? 0 : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB;
+  return NST == 0 ? 0 : (RPW == 0 ? rows_smem_bytes<CWB, NST>() : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB);
 }
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
@@ -513,6 +519,13 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
                                           int ostride, double* red, uint8_t* dsm, int* err) {
   if constexpr (NST == 0) {
     pass_block<ST, RPW, UNR>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red);
+  } else if constexpr (RPW == 0) {
+    // whole-row stages of CWB bytes; rows longer than a stage stream through registers
+    if ((size_t)ld * Elt<ST>::B <= (size_t)CWB)
+      pass_block_rows<ST, CWB, NST>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red,
+                                    dsm, err);
+    else
+      pass_block<ST, 4, 4>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red);
   } else {
     uint64_t* bars = reinterpret_cast<uint64_t*>(dsm);
     uint8_t* sbuf = dsm + tma_bar_bytes<NST>();

@@ -12,20 +12,22 @@ struct State;
 struct Ctrl;
 
 // Coupling-pass tile variants picked by the autotuner:
-//   RPW  rows streamed together by one warp,
+//   RPW  rows streamed together by one warp (0: whole-row CTA stages),
 //   UNR  16-byte chunks in flight per row and lane (register streaming),
-//   NST  shared-memory slots per warp (bulk-copy staging; 0 = registers),
-//   CWB  bytes of each row per slot.
-constexpr int NVAR = 5;
-constexpr int kVarRPW[NVAR] = {4, 4, 4, 4, 2};
-constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0};
-constexpr int kVarNST[NVAR] = {0, 0, 4, 4, 8};
-constexpr int kVarCWB[NVAR] = {0, 0, 1024, 512, 1024};
+//   NST  shared-memory slots (bulk-copy staging; 0 = registers),
+//   CWB  bytes of each row per warp slot, or bytes per CTA stage (RPW = 0).
+constexpr int NVAR = 6;
+constexpr int kVarRPW[NVAR] = {4, 4, 4, 0, 0, 0};
+constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0, 0};
+constexpr int kVarNST[NVAR] = {0, 0, 4, 3, 4, 3};
+constexpr int kVarCWB[NVAR] = {0, 0, 512, 32768, 16384, 65536};
 
-// dynamic shared memory of variant vi (8 warps): mbarrier area rounded up to
-// 128 bytes, then 8 * NST * RPW * CWB bytes of slots
+// dynamic shared memory of variant vi (8 warps).  Warp stages: mbarrier area
+// rounded up to 128 bytes, then 8 * NST * RPW * CWB bytes of slots.  CTA
+// stages: 128 bytes of mbarriers, 1 KB of row sums, NST * CWB bytes of slots.
 inline size_t var_smem(int vi) {
   if (kVarNST[vi] == 0) return 0;
+  if (kVarRPW[vi] == 0) return (size_t)128 + 1024 + (size_t)kVarNST[vi] * kVarCWB[vi];
   const size_t bars = ((size_t)8 * kVarNST[vi] * 8 + 127) / 128 * 128;
   return bars + (size_t)8 * kVarNST[vi] * kVarRPW[vi] * kVarCWB[vi];
 }
