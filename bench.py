@@ -31,8 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = ("time-to-1e-6 rel KKT & iters/s; coupling-pass HBM GB/s vs 8 TB/s "
           "(plain vs mixed/batched)")
 WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1), c_i N(0,1), "
-            "d_i=-U[0.1,1], box [-10,10], FP32 (3.42 GB Q stack); rAPDB-yx non-monotone, "
-            "fixed restart every 200 iterations, x0=y0=0, stop at rel KKT <= 1e-6")
+            "d_i=-U[0.1,1], box [-10,10], FP32 storage (3.42 GB Q stack); rAPDB-yx non-monotone, "
+            "adaptive (smoothed-gap) restart first at k=50 then every 500, precision refinement to "
+            "compensated float32 products, x0=y0=0, stop at rel KKT <= 1e-6")
 # DRAM bytes (read + write) of one coupling-pass launch on this workload from an
 # ncu capture (profiles/coupling_pass_n4096_m50_f32.md); None when no capture of
 # the current kernel exists.
@@ -133,9 +134,32 @@ def make_workload(device, seed=0):
     return W.config("C2", device=device, seed=seed)
 
 
-def solver_params(R):
-    return R.Params.default(R.YX, c_nm=1, restart=R.RESTART_FIXED, restart_period=200, tol=1e-6,
-                            max_iter=50000, time_limit_s=300.0)
+def solver_params(R, **kw):
+    base = dict(c_nm=1, restart=R.RESTART_GAP, gap_first=50, gap_every=500, restart_period=200, tol=1e-6,
+                max_iter=50000, time_limit_s=300.0, refine=1)
+    base.update(kw)
+    return R.Params.default(R.YX, **base)
+
+
+def timed_solve(R, torch, data, p, dev, reps=2):
+    """Create a context and time `reps` solves (after one untimed solve)."""
+    s = R.Solver(data, p)
+    x = torch.zeros(data.n, dtype=torch.float32, device=dev)
+    y = torch.zeros(max(data.m, 1), dtype=torch.float32, device=dev)
+    s.solve(x, y)
+    infos = []
+    for _ in range(reps):
+        x.zero_()
+        y.zero_()
+        infos.append(s.solve(x, y))
+    ms, b = s.time_pass(reps=10)
+    tile = s.tile()
+    s.close()
+    t = statistics.median(i["seconds"] for i in infos)
+    return {"time_to_tol_s": t, "iters": infos[-1]["iters"], "passes": infos[-1]["passes"],
+            "precision_switches": infos[-1]["precision_switches"], "rel_kkt": infos[-1]["rel_kkt"],
+            "status": infos[-1]["status"], "iters_per_s": infos[-1]["iters"] / t,
+            "pass_gbs": b / (ms * 1e-3) / 1e9, "pass_bytes": b, "tile": tile}
 
 
 def log(msg):
@@ -150,7 +174,7 @@ def oracle_sample(data, budget_s: float):
     t0 = time.time()
     prob = O.Problem.from_data(data)
     t_setup = time.time() - t0
-    p = O.default_params("yx", c_nm=1, restart="fixed", restart_period=200, tol=1e-6)
+    p = O.default_params("yx", c_nm=1, restart="gap", gap_first=50, gap_every=500, tol=1e-6)
     p.max_iter = 1
     t = time.time()
     O.rapdb(prob, p=p)
@@ -163,6 +187,39 @@ def oracle_sample(data, budget_s: float):
     del prob
     return {"iters": r.iters, "trials": r.trials, "seconds": dt, "setup_s": t_setup, "probe_s": one,
             "cores": os.cpu_count()}
+
+
+def run_batched(R, torch, dev, count=256, sample=32):
+    """256 random QCQPs of uneven n (64..1024, log-uniform) and m (2..32) in one
+    device loop, against one-at-a-time solves of a sample of them."""
+    from paper_2605_29291_gb300 import workloads as W
+    datas = W.batched_random_qcqp(count, seed=0)
+    devs = [d.to(dev) for d in datas]
+    p = R.Params.default(R.YX, tol=1e-6, max_iter=20000, time_limit_s=120.0, refine=1)
+    bs = R.BatchedSolver(devs, p)
+    xs = [torch.zeros(d.n, device=dev) for d in datas]
+    ys = [torch.zeros(max(d.m, 1), device=dev) for d in datas]
+    bs.solve(xs, ys)          # warm-up
+    for t in xs + ys:
+        t.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = bs.solve(xs, ys)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    bs.close()
+    ok = sum(1 for i in infos if i["status"] == R.OK)
+    t0 = time.perf_counter()
+    for d in devs[:sample]:
+        s = R.Solver(d, p)
+        s.solve(torch.zeros(d.n, device=dev), torch.zeros(max(d.m, 1), device=dev))
+        s.close()
+    torch.cuda.synchronize()
+    ts = (time.perf_counter() - t0) * count / sample
+    return {"instances": count, "converged": ok, "seconds": tb, "instances_per_s": count / tb,
+            "iters_total": sum(i["iters"] for i in infos), "iters_max": max(i["iters"] for i in infos),
+            "bytes_stored": sum(d.M * d.n * d.n * 4 for d in datas),
+            "sequential_estimate_s": ts, "sequential_sample": sample, "speedup_vs_sequential": ts / tb}
 
 
 def run_reference(args):
@@ -251,14 +308,17 @@ def run_ours(args):
 
     # dominant kernel: the coupling pass, timed with CUDA events on the
     # solver's stream (the torch current stream)
-    pass_ms, pass_bytes = s.time_pass(reps=20)
+    pass_ms, pass_bytes = s.time_pass(reps=20, level=0)        # plain float32: most passes of a solve
+    comp_ms, _ = s.time_pass(reps=5, level=2)                    # compensated passes of the final phase
     pk, pk_kind = peaks()
     achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": PASS_DRAM_BYTES,
                 "peak_kind": f"{pk_kind} copy bandwidth", "frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
                 "kernel": "k_pass<f32> (fused coupling pass)", "bytes_per_launch": pass_bytes,
-                "ms_per_launch": pass_ms, "tile": s.tile()}
+                "ms_per_launch": pass_ms, "tile": s.tile(),
+                "compensated_pass_gbs": pass_bytes / (comp_ms * 1e-3) / 1e9}
+    x64, y64 = s.solution_f64()
 
     # end to end through the C ABI from pinned host buffers (one step: upload,
     # create, solve, read back)
@@ -299,6 +359,22 @@ def run_ours(args):
                "steps": args.e2e_steps, "s_per_step": e_secs / args.e2e_steps}
         del host
 
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["batched"] = run_batched(R, torch, dev)
+        log(f"batched: {extras['batched']}")
+        # same instance: fixed-frequency restart (the paper's practice), and
+        # BF16 / FP8 storage with refinement (plain vs mixed)
+        fixed = timed_solve(R, torch, data, solver_params(R, restart=R.RESTART_FIXED), dev)
+        log(f"fixed restart: {fixed}")
+        extras["fixed_restart"] = fixed
+        mixed = {}
+        for name, st in (("bf16", R.BF16), ("fp8", R.FP8)):
+            mixed[name] = timed_solve(R, torch, data, solver_params(R, storage=st), dev)
+            mixed[name]["speedup_vs_f32"] = (statistics.median(i["seconds"] for i in infos) /
+                                             mixed[name]["time_to_tol_s"])
+            log(f"mixed {name}: {mixed[name]}")
+        extras["mixed"] = mixed
     cpu = None
     fp64_check = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -308,9 +384,11 @@ def run_ours(args):
         torch.cuda.empty_cache()
         # the oracle's float64 KKT residual at the last step's GPU result
         prob = O.Problem.from_data(hd)
-        rel64, rs64, rf64 = O.kkt_residual(prob, x.cpu().numpy().astype(np.float64),
-                                           y.cpu().numpy().astype(np.float64))
-        fp64_check = {"rel_kkt_fp64_at_result": rel64, "obj_fp64": float(prob.f(x.cpu().numpy().astype(np.float64)))}
+        xa, ya = x64.cpu().numpy(), y64.cpu().numpy()
+        rel64, rs64, rf64 = O.kkt_residual(prob, xa, ya)
+        rel32, _, _ = O.kkt_residual(prob, x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64))
+        fp64_check = {"rel_kkt_fp64_at_solver_iterate": rel64, "rel_kkt_fp64_at_float32_output": rel32,
+                      "obj_fp64": float(prob.f(xa))}
         del prob
         smp = oracle_sample(hd, args.cpu_budget)
         cpu = {"value": smp["iters"] / smp["seconds"], "unit": "iters/s", "cores": smp["cores"],
@@ -330,7 +408,7 @@ def run_ours(args):
         "coupling_gbs_in_solve": passes_all * pass_bytes / t_max / 1e9,
         "rel_kkt": max(i["rel_kkt"] for i in infos), "all_converged": ok,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches),
-        "oracle_check": fp64_check,
+        "oracle_check": fp64_check, "extras": extras,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -349,6 +427,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

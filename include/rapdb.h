@@ -141,6 +141,13 @@ rapdb_status rapdb_create(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind
  * at the end, then fills *info (host, may be NULL).  Returns info->status. */
 rapdb_status rapdb_solve(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
 
+/* The float64 iterate of the last rapdb_solve / rapdb_resume: x (device, n
+ * doubles) and y (device, m doubles; may be NULL).  rapdb_solve returns x
+ * and y rounded to float32; near a 1e-7 residual that rounding alone can
+ * move the residual, so callers that need the solver's own point read it
+ * here.  Synchronises the context's stream. */
+rapdb_status rapdb_get_solution_f64(rapdb_ctx *ctx, double *x, double *y);
+
 /* Relative KKT residual at (x, y) (device): one float32 coupling pass with the
  * context's float32 Q (the quantised copy only when no float32 Q exists), then
  *   r_stat_j = dist(0, grad_x L(x,y)_j + N_[lb,ub](x_j)),
@@ -168,12 +175,15 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
 /* Time the context's coupling-pass kernel: `reps` back-to-back launches on
  * the context's stream, on the current solver iterate (x^k, and d of the
  * last trial as the second right-hand side), bracketed by two CUDA events on
- * that stream.  *ms_per_pass (host) receives the average duration of one
- * launch, *bytes_per_pass (host) the algorithmic bytes of one pass: the
- * stored Q entries read, M * n * n * (4 | 2 | 1) (+ n*M*4 scale bytes for
- * FP8).  Outputs of the pass go to context scratch; the solver state is not
- * changed. */
-rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, double *ms_per_pass,
+ * that stream.  level: -1 = the precision the last solve ended at, 0 = the
+ * stored Q, 1 = the float32 Q of a BF16/FP8 context, 2 = float32 Q with
+ * compensated (double-float) products (contexts created with refine = 1).
+ * *ms_per_pass (host) receives the average duration of one launch,
+ * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
+ * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8).  Outputs
+ * go to context scratch; the solver state is not changed.  RAPDB_ERR_INVALID
+ * when the level does not exist in this context. */
+rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, int32_t level, double *ms_per_pass,
                              int64_t *bytes_per_pass);
 
 /* Record the first `capacity` iterations of the next rapdb_solve calls:
@@ -181,11 +191,13 @@ rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, double *ms_per_pass,
  * and, when non-NULL, the iterates x^{k+1} (x_log: device, capacity x n
  * floats), y^{k+1} (y_log: capacity x m floats) and the relative KKT
  * residual measured at iterate k (kkt_log: capacity doubles; entries of
- * iterations where it was not evaluated are left untouched).  capacity = 0
- * switches logging off.  The buffers are borrowed. */
+ * iterations where it was not evaluated are left untouched) and, with the
+ * adaptive restart, the smoothed gap G_xi of each evaluation in order
+ * (gap_log: capacity doubles).  capacity = 0 switches logging off.  The
+ * buffers are borrowed. */
 rapdb_status rapdb_set_log(rapdb_ctx *ctx, int32_t capacity, double *tau_log,
                            int32_t *trials_log, float *x_log, float *y_log,
-                           double *kkt_log);
+                           double *kkt_log, double *gap_log);
 
 /* Batched contexts: B independent problems with their own n_b, m_b, solved
  * together in one device loop with per-instance step sizes, restart counters

@@ -43,20 +43,25 @@ void RAPDB_CAT(launch_pass_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const In
     case 3: k_pass<RAPDB_ST, 0, 0, 3, 32768><<<g, NT, var_smem(3), s>>>(I, S, C, pm, XS, VS); break;
     case 4: k_pass<RAPDB_ST, 0, 0, 4, 16384><<<g, NT, var_smem(4), s>>>(I, S, C, pm, XS, VS); break;
     case 5: k_pass<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, S, C, pm, XS, VS); break;
+    case 6: k_pass<RAPDB_ST, 4, 2, -1, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
+    case 7: k_pass<RAPDB_ST, 4, 4, -1, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
     default: k_pass<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
   }
 }
 
 void RAPDB_CAT(launch_plain_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x,
                                          const float* v, const float* XS, const float* VS, const float* uold,
-                                         float* U, float* W, double* part, int use32, int* err) {
+                                         float* U, float* W, double* part, int level, const float* xlo,
+                                         float* Ulo, int* err) {
   switch (vi) {
-    case 1: k_pass_plain<RAPDB_ST, 4, 4, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 2: k_pass_plain<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(2), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 3: k_pass_plain<RAPDB_ST, 0, 0, 3, 32768><<<g, NT, var_smem(3), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 4: k_pass_plain<RAPDB_ST, 0, 0, 4, 16384><<<g, NT, var_smem(4), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    case 5: k_pass_plain<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
-    default: k_pass_plain<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, use32, err); break;
+    case 1: k_pass_plain<RAPDB_ST, 4, 4, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 2: k_pass_plain<RAPDB_ST, 4, 0, 4, 512><<<g, NT, var_smem(2), s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 3: k_pass_plain<RAPDB_ST, 0, 0, 3, 32768><<<g, NT, var_smem(3), s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 4: k_pass_plain<RAPDB_ST, 0, 0, 4, 16384><<<g, NT, var_smem(4), s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 5: k_pass_plain<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 6: k_pass_plain<RAPDB_ST, 4, 2, -1, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 7: k_pass_plain<RAPDB_ST, 4, 4, -1, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    default: k_pass_plain<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
   }
 }
 

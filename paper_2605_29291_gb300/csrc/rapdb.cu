@@ -74,6 +74,7 @@ struct rapdb_ctx {
   int log_cap = 0;
   double* tau_log = nullptr;
   double* kkt_log = nullptr;
+  double* gap_log = nullptr;
   int* trials_log = nullptr;
   float* x_log = nullptr;
   float* y_log = nullptr;
@@ -97,11 +98,11 @@ void launch_pass(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, Sta
 }
 
 void launch_plain(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x, const float* v,
-                  const float* XS, const float* VS, const float* uold, float* U, float* W, double* part, int use32,
-                  int* err) {
-  if (storage == RAPDB_F32) launch_plain_f32(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
-  else if (storage == RAPDB_BF16) launch_plain_bf16(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
-  else launch_plain_fp8(vi, g, s, I, x, v, XS, VS, uold, U, W, part, use32, err);
+                  const float* XS, const float* VS, const float* uold, float* U, float* W, double* part, int level,
+                  int* err, const float* xlo = nullptr, float* Ulo = nullptr) {
+  if (storage == RAPDB_F32) launch_plain_f32(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
+  else if (storage == RAPDB_BF16) launch_plain_bf16(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
+  else launch_plain_fp8(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
 }
 
 rapdb_status fail(rapdb_ctx* ctx, rapdb_status st, const std::string& msg) {
@@ -177,6 +178,7 @@ DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
   d.log_cap = ctx->log_cap;
   d.tau_log = ctx->tau_log;
   d.kkt_log = ctx->kkt_log;
+  d.gap_log = ctx->gap_log;
   d.trials_log = ctx->trials_log;
   d.x_log = ctx->x_log;
   d.y_log = ctx->y_log;
@@ -189,8 +191,12 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
   if (p->storage < RAPDB_F32 || p->storage > RAPDB_FP8) return fail(ctx, RAPDB_ERR_INVALID, "bad storage");
   if (p->restart < RAPDB_RESTART_NONE || p->restart > RAPDB_RESTART_GAP)
     return fail(ctx, RAPDB_ERR_INVALID, "bad restart mode");
-  if (p->restart == RAPDB_RESTART_GAP)
-    return fail(ctx, RAPDB_ERR_INVALID, "adaptive (gap) restart is not available in this build");
+  if (p->restart == RAPDB_RESTART_GAP &&
+      (p->restart_from_average || !(p->xi > 0.0) || !(p->q > 0.0) || p->gap_first < 0 || p->gap_every < 1 ||
+       p->gap_inner_max < 1))
+    return fail(ctx, RAPDB_ERR_INVALID,
+                "adaptive restart needs xi > 0, q > 0, gap_first >= 0, gap_every >= 1, gap_inner_max >= 1 and "
+                "restarts from the last iterate");
   if (p->restart == RAPDB_RESTART_FIXED && p->restart_period < 1)
     return fail(ctx, RAPDB_ERR_INVALID, "restart_period must be >= 1");
   if (!(p->eta > 0.0 && p->eta < 1.0)) return fail(ctx, RAPDB_ERR_INVALID, "eta must be in (0,1)");
@@ -327,6 +333,8 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   for (int s = 0; s < 2; ++s) {
     AL(I.xb[s], ldv);
     AL(I.xf[s], ldv);
+    AL(I.xl[s], ldv);
+    if (p.refine) AL(I.Ulo[s], (size_t)(m + 1) * ldv);
     AL(I.yb[s], mm);
     AL(I.U[s], (size_t)(m + 1) * ldv);
     AL(I.gb[s], mm);
@@ -342,6 +350,12 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   if (p.restart_from_average) {
     AL(I.xcum, ldv);
     AL(I.ycum, mm);
+  }
+  if (p.restart == RAPDB_RESTART_GAP) {
+    AL(I.gz, ldv);
+    AL(I.gzf, ldv);
+    AL(I.gwf, ldv);
+    AL(I.gpf, ldv);
   }
   I.P = make_devparams(p, ctx);
   return RAPDB_OK;
@@ -669,8 +683,12 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
   rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
   for (int b = 0; b < B && s == RAPDB_OK; ++b)
     s = build_instance(ctx, ctx->hi[b], n[b], m[b], RAPDB_Q0_DENSE, Q[b], nullptr, c[b], d[b], lb[b], ub[b],
-                       p->rows_per_block);
+                       p->rows_per_block > 0 ? p->rows_per_block : 64);
   if (s == RAPDB_OK) s = finalize_ctx(ctx);
+  // batched contexts take the tile from the parameters (rows_per_block > 0,
+  // pass_variant) or default to 64-row blocks of the pipelined register
+  // streaming variant (the fastest on the 256-instance workload)
+  if (s == RAPDB_OK) ctx->pvar = p->rows_per_block > 0 ? p->pass_variant : 6;
   if (s == RAPDB_OK) s = build_graph(ctx, 32);
   if (s != RAPDB_OK) {
     g_last_error = ctx->err;
@@ -832,26 +850,31 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
   return RAPDB_OK;
 }
 
-rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, double* ms_per_pass, int64_t* bytes_per_pass) {
+rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double* ms_per_pass,
+                             int64_t* bytes_per_pass) {
   if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
   if (reps < 1) return fail(ctx, RAPDB_ERR_INVALID, "reps must be >= 1");
   const Inst& I = ctx->hi[0].I;
   cudaStream_t st = ctx->stream;
-  int xcur = 0;
+  int xcur = 0, cur_level = 0;
   if (ctx->have_state) {
     CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     xcur = ctx->h_state[0].xcur;
+    cur_level = ctx->h_state[0].precision;
   }
+  const int lv = level < 0 ? cur_level : level;
+  if (lv > 2 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv == 2 && !I.Ulo[0]) ||
+      (lv == 1 && I.storage == RAPDB_F32))
+    return fail(ctx, RAPDB_ERR_INVALID, "precision level not available in this context");
   const float* x = I.xf[xcur];
   const float* v = I.dv;
-  const int use32 = (I.storage != RAPDB_F32 && ctx->have_state && ctx->h_state[0].precision == 1) ? 1 : 0;
-  if (I.storage == RAPDB_FP8 && !use32)
+  if (I.storage == RAPDB_FP8 && lv == 0)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
-    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS, I.U[0], ctx->tU, ctx->tW,
-                 ctx->tpart, use32, &ctx->d_ctrl->err);
+    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS, lv == 2 ? nullptr : I.U[0],
+                 ctx->tU, ctx->tW, ctx->tpart, lv, &ctx->d_ctrl->err, I.xl[xcur], ctx->tUo);
   };
   launch();   // warm-up
   CK(cudaGetLastError());
@@ -864,16 +887,30 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, double* ms_per_pass, 
   CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
   if (ms_per_pass) *ms_per_pass = (double)ms / reps;
   if (bytes_per_pass) {
-    const int64_t eb = use32 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));
+    const int64_t eb = lv >= 1 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));
     int64_t b = (int64_t)I.M * I.n * I.n * eb;
-    if (I.storage == RAPDB_FP8 && !use32) b += (int64_t)I.M * I.n * 4;
+    if (I.storage == RAPDB_FP8 && lv == 0) b += (int64_t)I.M * I.n * 4;
     *bytes_per_pass = b;
   }
   return RAPDB_OK;
 }
 
+rapdb_status rapdb_get_solution_f64(rapdb_ctx* ctx, double* x, double* y) {
+  if (!ctx || ctx->batched || !x) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context and x required");
+  if (!ctx->have_state) return fail(ctx, RAPDB_ERR_INVALID, "no solution yet (run rapdb_solve first)");
+  const Inst& I = ctx->hi[0].I;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const State& S = ctx->h_state[0];
+  CK(cudaMemcpyAsync(x, I.xb[S.xcur], (size_t)I.n * 8, cudaMemcpyDeviceToDevice, st));
+  if (y && I.m > 0) CK(cudaMemcpyAsync(y, I.yb[S.ycur], (size_t)I.m * 8, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return RAPDB_OK;
+}
+
 rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, int32_t* trials_log, float* x_log,
-                           float* y_log, double* kkt_log) {
+                           float* y_log, double* kkt_log, double* gap_log) {
   if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
   if (capacity < 0) return fail(ctx, RAPDB_ERR_INVALID, "capacity < 0");
   ctx->log_cap = capacity;
@@ -882,6 +919,7 @@ rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, in
   ctx->x_log = capacity ? x_log : nullptr;
   ctx->y_log = capacity ? y_log : nullptr;
   ctx->kkt_log = capacity ? kkt_log : nullptr;
+  ctx->gap_log = capacity ? gap_log : nullptr;
   return upload_params(ctx);
 }
 
@@ -903,6 +941,8 @@ static void state_blobs(rapdb_ctx* ctx, int b, std::vector<std::pair<void*, size
   for (int s = 0; s < 2; ++s) {
     v.push_back({I.xb[s], ldv * 8});
     v.push_back({I.xf[s], ldv * 4});
+    v.push_back({I.xl[s], ldv * 4});
+    if (I.Ulo[s]) v.push_back({I.Ulo[s], m1 * ldv * 4});
     v.push_back({I.yb[s], mm * 8});
     v.push_back({I.U[s], m1 * ldv * 4});
     v.push_back({I.gb[s], mm * 8});
@@ -910,6 +950,10 @@ static void state_blobs(rapdb_ctx* ctx, int b, std::vector<std::pair<void*, size
   }
   if (I.xcum) v.push_back({I.xcum, ldv * 8});
   if (I.ycum) v.push_back({I.ycum, mm * 8});
+  if (I.gz) v.push_back({I.gz, ldv * 8});
+  if (I.gzf) v.push_back({I.gzf, ldv * 4});
+  if (I.gwf) v.push_back({I.gwf, ldv * 4});
+  if (I.gpf) v.push_back({I.gpf, ldv * 4});
 }
 
 rapdb_status rapdb_get_state(rapdb_ctx* ctx, void* buf, size_t* len) {

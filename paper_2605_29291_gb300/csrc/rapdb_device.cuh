@@ -46,8 +46,9 @@ enum Phase : int {
   PH_AVGP = 8,       // ... then U = Q xbar (pass kernel)
   PH_KKT32 = 4,      // quantised storage: float32 pass at x^k for the true KKT
   PH_KKT32B = 5,     // ... and its residual sweep + the refinement decision
-  PH_GAPY = 6,       // adaptive restart: smoothed-gap x-subproblem iterations
-  PH_GAPF = 7,       // ... final value sweep
+  PH_GAPP = 6,       // adaptive restart: power iterations for the x-subproblem's step
+  PH_GAPF = 7,       // ... accelerated projected gradient on the x-subproblem
+  PH_GAPV = 10,      // ... value of the smoothed gap and the restart decision
   PH_DONE = 9
 };
 
@@ -65,6 +66,7 @@ struct DevParams {
   int max_iter, max_trials, kkt_every, refine, gap_first, gap_every, gap_inner_max;
   double mu, c_alpha, c_beta, delta, eta, tau_bar, gamma0, tol, stall_ratio, xi, q;
   int log_cap;
+  double* gap_log;      // smoothed-gap values, one per evaluation (capacity log_cap)
   double* kkt_log;
   double* tau_log;
   int* trials_log;
@@ -94,8 +96,10 @@ struct Inst {
   double dnorm;         // ||d||_2 of the constants
   double* xb[2];        // x^k / x~ master copies (ldv each, padding zero)
   float* xf[2];         // float32 copies of xb: the pass right-hand side
+  float* xl[2];         // xb - xf as float32 (the low part for compensated passes)
   double* yb[2];        // y^k / y~ (m)
   float* U[2];          // Q x^k / Q x~  ((m+1, ldv))
+  float* Ulo[2];        // low parts of U written by compensated passes (refine only)
   float* W;             // Q d           ((m+1, ldv))
   float* dv;            // d (ldv)
   double* gx[2];        // xy: grad_x Phi(x^k,y^k) / grad_x Phi(x^{k-1},y^{k-1}); gap: work
@@ -107,8 +111,10 @@ struct Inst {
   double* dots;         // (m+1, NDOT) reduced dots
   double* xcum;         // averaging: sum t_k x^{k+1}  (ldv)
   double* ycum;         // sum t_k y^{k+1}  (m)
-  float* gz;            // gap: FISTA iterate z (ldv)
-  float* gzp;           // gap: previous z (ldv)
+  double* gz;           // smoothed gap: x-subproblem iterate z (ldv)
+  float* gzf;           // ... its float32 copy (pass right-hand side)
+  float* gwf;           // ... extrapolated point w (float32, pass right-hand side)
+  float* gpf;           // ... power-iteration vector (float32, pass right-hand side)
   DevParams P;
 };
 
@@ -126,13 +132,15 @@ struct State {
   double kkt_ref;       // true residual at the previous restart boundary
   double dd;            // ||d||^2 of the current trial
   double dots0[NDOT];   // i = 0 dots when Q_0 is not stored
-  double gap_ref, gap_val, gap_L, gap_t, gap_yval, gap_lin;
+  double gap_ref, gap_val, gap_L, gap_mu, gap_pnorm, gap_prev, gap_beta;
   long long deadline_ns;
   int k, it, trial, trials_total, passes, restarts, switches;
   int phase, status, fresh, restart_note, avg_pending;
   int xcur, ycur, ucur, gcur, gxcur;
-  int precision;        // 0: stored Q, 1: float32 Q
-  int gap_iter, gap_fire_pending;
+  int precision;        // 0: stored Q, 1: float32 Q, 2: float32 Q, compensated products
+  int gap_iter, gap_has_ref, gap_evals, trial_ready;
+  int gap_it_done;      // iteration of the last smoothed-gap evaluation (-1: none)
+  int check_level;      // precision level of the pending accurate KKT check (KKT32 / KKT32B)
   unsigned int arrive_vec, arrive_pass;
   int pad_;
 };
@@ -817,6 +825,265 @@ __device__ __forceinline__ void pass_block_rows(const uint8_t* __restrict__ Qm, 
   }
   __syncthreads();
   (void)smem;
+}
+
+
+// Compensated coupling pass (precision level 2, float32 storage): the main
+// right-hand side is given as x = xh + xl (two floats); each product q*xh is
+// split exactly (TwoProduct with an FMA) and summed with TwoSum, the rounding
+// errors are accumulated separately, q*xl and q*v use plain FMAs.  The row
+// value Q x is formed in float64 and stored as a float pair (Uoh, Uol), so the
+// products carry about twice the float32 precision.  The dots use x = xh + xl
+// and uold = uoh + uol.
+template <int RPW, int UNR>
+__device__ __forceinline__ void pass_block_prec2(const float* __restrict__ Qf, int ld, int row0, int rows,
+                                                 const float* __restrict__ xh, const float* __restrict__ xl,
+                                                 const float* __restrict__ v,
+                                                 const float* __restrict__ uoh, const float* __restrict__ uol,
+                                                 const float* __restrict__ crow,
+                                                 float* __restrict__ Uoh, float* __restrict__ Uol,
+                                                 float* __restrict__ Wo, double* __restrict__ out, int ostride,
+                                                 double* smem) {
+  const uint8_t* Qm = reinterpret_cast<const uint8_t*>(Qf);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const size_t rowbytes = (size_t)ld * 4;
+  for (int r = row0 + warp * RPW; r < row0 + rows; r += NWARP * RPW) {
+    const int nr = min(RPW, row0 + rows - r);
+    const uint8_t* p[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) p[q] = Qm + (size_t)(r + (q < nr ? q : 0)) * rowbytes;
+    float sh[RPW], ce[RPW], al[RPW], aw[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) { sh[q] = 0.f; ce[q] = 0.f; al[q] = 0.f; aw[q] = 0.f; }
+    auto consume = [&](const uint4 (&raw)[RPW], int cc) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(xh + cc));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(xl + cc));
+      const float4 d = __ldg(reinterpret_cast<const float4*>(v + cc));
+      const float xv[4] = {a.x, a.y, a.z, a.w}, lv[4] = {b.x, b.y, b.z, b.w}, dv4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float qe[4];
+        Elt<RAPDB_F32>::cvt(raw[q], qe);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          // explicit round-to-nearest operations: no FMA contraction may
+          // merge the product into the following sums
+          const float pr = __fmul_rn(qe[e], xv[e]);
+          const float pe = fmaf(qe[e], xv[e], -pr);      // exact: q*x = pr + pe
+          const float t = __fadd_rn(sh[q], pr);           // TwoSum(sh, pr)
+          const float z = __fsub_rn(t, sh[q]);
+          const float er = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(t, z)), __fsub_rn(pr, z));
+          sh[q] = t;
+          ce[q] = __fadd_rn(ce[q], __fadd_rn(er, pe));
+          al[q] = fmaf(qe[e], lv[e], al[q]);
+          aw[q] = fmaf(qe[e], dv4[e], aw[q]);
+        }
+      }
+    };
+    int c0 = lane * 4;
+    for (; c0 + (UNR - 1) * 128 < ld; c0 += UNR * 128) {
+      uint4 raw[UNR][RPW];
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+          raw[uu][q] = (q < nr) ? ld_stream16(p[q] + (size_t)(c0 + uu * 128) * 4) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu) consume(raw[uu], c0 + uu * 128);
+    }
+    for (; c0 < ld; c0 += 128) {
+      uint4 raw[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) raw[q] = (q < nr) ? ld_stream16(p[q] + (size_t)c0 * 4) : make_uint4(0, 0, 0, 0);
+      consume(raw, c0);
+    }
+    double uu_[RPW], ww_[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      uu_[q] = warp_sum((double)sh[q]) + warp_sum((double)ce[q]) + warp_sum((double)al[q]);
+      ww_[q] = warp_sum((double)aw[q]);
+    }
+    if (lane < nr) {
+      const int j = r + lane;
+      double u = uu_[0], w = ww_[0];
+#pragma unroll
+      for (int q = 1; q < RPW; ++q)
+        if (lane == q) { u = uu_[q]; w = ww_[q]; }
+      const float uh = (float)u;
+      Uoh[j] = uh;
+      Uol[j] = (float)(u - (double)uh);
+      Wo[j] = (float)w;
+      const double xj = (double)xh[j] + (double)xl[j], vj = v[j], cj = crow[j];
+      dsum[0] = fma(xj, u, dsum[0]);
+      dsum[1] = fma(vj, w, dsum[1]);
+      if (uoh) dsum[2] = fma(vj, (double)uoh[j] + (double)uol[j], dsum[2]);
+      dsum[3] = fma(cj, xj, dsum[3]);
+      dsum[4] = fma(cj, vj, dsum[4]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) {
+#pragma unroll
+    for (int o = 1; o < RPW; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) smem[warp * NDOT + q] = dsum[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NDOT) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += smem[w * NDOT + threadIdx.x];
+    out[threadIdx.x * ostride] = s;
+  }
+  __syncthreads();
+}
+
+
+// Register streaming with explicit software pipelining: the loads of the
+// next UNR chunks of the RPW rows are issued before the current chunks are
+// consumed, so each lane keeps 2 x UNR x RPW 16-byte loads outstanding while
+// it computes.  Same arithmetic and outputs as pass_block.
+template <int ST, int RPW, int UNR>
+__device__ __forceinline__ void pass_block_pipe(const uint8_t* __restrict__ Qm, int ld, int row0, int rows,
+                                                const float* __restrict__ x, const float* __restrict__ v,
+                                                const float* __restrict__ xs, const float* __restrict__ vs,
+                                                const float* __restrict__ scale,
+                                                const float* __restrict__ uold,
+                                                const float* __restrict__ crow,
+                                                float* __restrict__ Uo, float* __restrict__ Wo,
+                                                double* __restrict__ out, int ostride, double* smem) {
+  constexpr int E = Elt<ST>::E;
+  constexpr int EB = Elt<ST>::B;
+  constexpr bool COMP = (ST == RAPDB_F32);
+  constexpr int STEP = UNR * 32 * E;          // columns covered by one batch of a warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const size_t rowbytes = (size_t)ld * EB;
+  const float* xa = (ST == RAPDB_FP8) ? xs : x;
+  const float* va = (ST == RAPDB_FP8) ? vs : v;
+  for (int r = row0 + warp * RPW; r < row0 + rows; r += NWARP * RPW) {
+    const int nr = min(RPW, row0 + rows - r);
+    const uint8_t* p[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) p[q] = Qm + (size_t)(r + (q < nr ? q : 0)) * rowbytes;
+    float acc[RPW][2], cmp[RPW][2];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) { acc[q][0] = 0.f; acc[q][1] = 0.f; cmp[q][0] = 0.f; cmp[q][1] = 0.f; }
+    auto load_batch = [&](int cb, uint4 (&raw)[UNR][RPW]) {
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu) {
+        const int cc = cb + lane * E + uu * 32 * E;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+          raw[uu][q] = (q < nr && cc < ld) ? ld_stream16(p[q] + (size_t)cc * EB) : make_uint4(0, 0, 0, 0);
+      }
+    };
+    auto consume_batch = [&](int cb, const uint4 (&raw)[UNR][RPW]) {
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu) {
+        const int cc = cb + lane * E + uu * 32 * E;
+        if (cc >= ld) continue;
+        float xv[E], vv[E];
+#pragma unroll
+        for (int e = 0; e < E; e += 4) {
+          float4 a = __ldg(reinterpret_cast<const float4*>(xa + cc + e));
+          float4 b = __ldg(reinterpret_cast<const float4*>(va + cc + e));
+          xv[e] = a.x; xv[e + 1] = a.y; xv[e + 2] = a.z; xv[e + 3] = a.w;
+          vv[e] = b.x; vv[e + 1] = b.y; vv[e + 2] = b.z; vv[e + 3] = b.w;
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          float qe[E];
+          Elt<ST>::cvt(raw[uu][q], qe);
+          if (COMP) {
+            float px = qe[0] * xv[0], pv = qe[0] * vv[0];
+#pragma unroll
+            for (int e = 1; e < E; ++e) {
+              px = fmaf(qe[e], xv[e], px);
+              pv = fmaf(qe[e], vv[e], pv);
+            }
+            const float yx = px - cmp[q][0];
+            const float tx = acc[q][0] + yx;
+            cmp[q][0] = (tx - acc[q][0]) - yx;
+            acc[q][0] = tx;
+            const float yv = pv - cmp[q][1];
+            const float tv = acc[q][1] + yv;
+            cmp[q][1] = (tv - acc[q][1]) - yv;
+            acc[q][1] = tv;
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              acc[q][0] = fmaf(qe[e], xv[e], acc[q][0]);
+              acc[q][1] = fmaf(qe[e], vv[e], acc[q][1]);
+            }
+          }
+        }
+      }
+    };
+    uint4 ra[UNR][RPW], rb[UNR][RPW];
+    int cb = 0;
+    load_batch(cb, ra);
+    while (true) {
+      const int nb = cb + STEP;
+      if (nb < ld) load_batch(nb, rb);           // next batch in flight
+      consume_batch(cb, ra);
+      if (nb >= ld) break;
+      cb = nb;
+      const int nb2 = cb + STEP;
+      if (nb2 < ld) load_batch(nb2, ra);
+      consume_batch(cb, rb);
+      if (nb2 >= ld) break;
+      cb = nb2;
+    }
+    float uu_[RPW], ww_[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      uu_[q] = warp_sumf(acc[q][0]);
+      ww_[q] = warp_sumf(acc[q][1]);
+      if (COMP) {
+        uu_[q] -= warp_sumf(cmp[q][0]);
+        ww_[q] -= warp_sumf(cmp[q][1]);
+      }
+    }
+    if (lane < nr) {
+      const int j = r + lane;
+      float u = uu_[0], w = ww_[0];
+#pragma unroll
+      for (int q = 1; q < RPW; ++q)
+        if (lane == q) { u = uu_[q]; w = ww_[q]; }
+      if (ST == RAPDB_FP8) {
+        const float sj = scale[j];
+        u *= sj;
+        w *= sj;
+      }
+      Uo[j] = u;
+      Wo[j] = w;
+      const double xj = x[j], vj = v[j], cj = crow[j];
+      dsum[0] = fma(xj, (double)u, dsum[0]);
+      dsum[1] = fma(vj, (double)w, dsum[1]);
+      if (uold) dsum[2] = fma(vj, (double)uold[j], dsum[2]);
+      dsum[3] = fma(cj, xj, dsum[3]);
+      dsum[4] = fma(cj, vj, dsum[4]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) {
+#pragma unroll
+    for (int o = 1; o < RPW; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) smem[warp * NDOT + q] = dsum[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NDOT) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += smem[w * NDOT + threadIdx.x];
+    out[threadIdx.x * ostride] = s;
+  }
+  __syncthreads();
 }
 
 }  // namespace rapdb_dev

@@ -31,10 +31,29 @@
 namespace rapdb_dev {
 
 __device__ __forceinline__ bool vec_phase(int ph) {
-  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_XY2 || ph == PH_AVG || ph == PH_KKT32B;
+  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_XY2 || ph == PH_AVG || ph == PH_KKT32B || ph == PH_GAPP ||
+         ph == PH_GAPF || ph == PH_GAPV;
 }
 __device__ __forceinline__ bool pass_phase(int ph) {
-  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_AVGP || ph == PH_KKT32;
+  return ph == PH_INIT || ph == PH_TRIAL || ph == PH_AVGP || ph == PH_KKT32 || ph == PH_GAPP || ph == PH_GAPF ||
+         ph == PH_GAPV;
+}
+__device__ __forceinline__ bool gap_phase(int ph) { return ph == PH_GAPP || ph == PH_GAPF || ph == PH_GAPV; }
+
+// Power iterations per smoothed-gap evaluation (first one / warm-started).
+constexpr int GAP_POWER_FIRST = 30;
+constexpr int GAP_POWER_WARM = 10;
+
+// Deterministic start vector of the power iteration: a uniform value in
+// [-1, 1) from a 32-bit integer hash of the column index.
+__device__ __forceinline__ float hash_unit(uint32_t j) {
+  uint32_t h = j * 0x9E3779B1u + 0x7F4A7C15u;
+  h ^= h >> 15;
+  h *= 0x85EBCA77u;
+  h ^= h >> 13;
+  h *= 0xC2B2AE3Du;
+  h ^= h >> 16;
+  return (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
 }
 
 __device__ __forceinline__ void finish(State& S, Ctrl* ctrl, int status) {
@@ -63,8 +82,20 @@ static __device__ void restart_scalars(const DevParams& P, State& S) {
   S.trial = 0;
 }
 
-__device__ __forceinline__ bool quantised_refining(const Inst& I, const State& S) {
-  return I.storage != RAPDB_F32 && I.P.refine && I.Q32 != nullptr && S.precision == 0;
+// Precision refinement: level 0 = the stored Q (float32, bfloat16 or FP8),
+// 1 = float32 Q (from quantised storage), 2 = float32 Q with compensated
+// (double-float) products.  At restart boundaries, and when the current level
+// reports convergence, the residual is checked one level up; a stall (or a
+// disagreement at convergence) switches to that level.
+__device__ __forceinline__ bool can_refine(const Inst& I, const State& S) {
+  return I.P.refine && S.precision < 2 && (I.storage == RAPDB_F32 || I.Q32 != nullptr);
+}
+__device__ __forceinline__ int next_level(const Inst& I, const State& S) {
+  return (I.storage == RAPDB_F32 || S.precision >= 1) ? 2 : 1;
+}
+__device__ __forceinline__ void start_check(const Inst& I, State& S) {
+  S.check_level = next_level(I, S);
+  S.phase = PH_KKT32;
 }
 
 // Per-constraint terms of the feasibility residual: r_feas_i^2 and
@@ -146,8 +177,12 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
     } else {
       restart_scalars(P, S);
       S.restart_note = 1;
-      if (quantised_refining(I, S)) S.phase = PH_KKT32;
+      if (can_refine(I, S)) start_check(I, S);
     }
+  } else if (P.restart != RAPDB_RESTART_FIXED && P.restart_period > 0 && S.it % P.restart_period == 0 &&
+             can_refine(I, S)) {
+    // without fixed restarts the precision check runs every restart_period iterations
+    start_check(I, S);
   }
 }
 
@@ -173,7 +208,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   extern __shared__ double sm[];            // ys[m], yts[m]
   __shared__ double red[NWARP * NVP];
   __shared__ double vfin[NVP];
-  __shared__ double pg[2][NGRP][VCOL];
+  __shared__ double pg[3][NGRP][VCOL];
   __shared__ float sx[VCOL], sd[VCOL];
   __shared__ int s_dec;
   const int b = vmap[blockIdx.x];
@@ -216,11 +251,21 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const bool kkt_due = (phase == PH_TRIAL && fresh &&
                         ((P.kkt_every > 0 && it % P.kkt_every == 0) || it >= P.max_iter)) ||
                        phase == PH_KKT32B;
+  // adaptive restart: a smoothed-gap evaluation is due before this iteration
+  const bool gap_due = phase == PH_TRIAL && fresh && P.restart == RAPDB_RESTART_GAP && it >= P.gap_first &&
+                       (it == P.gap_first || (it - P.gap_first) % P.gap_every == 0) && S.gap_it_done != it;
+  const int gap_iter = S.gap_iter;
+  const int gap_P = (S.gap_evals == 0) ? GAP_POWER_FIRST : GAP_POWER_WARM;
   const double* xk = I.xb[S.xcur];
   double* xt_out = I.xb[S.xcur ^ 1];
   float* xt_out32 = I.xf[S.xcur ^ 1];
+  float* xt_outlo = I.xl[S.xcur ^ 1];
   const float* Uc = I.U[S.ucur];
   float* Un = I.U[S.ucur ^ 1];
+  // low parts of U when the products were formed with compensation
+  const float* Uclo = (S.precision == 2) ? I.Ulo[S.ucur] : nullptr;
+  const float* Unlo = (phase == PH_KKT32B ? S.check_level == 2 : (S.precision == 2 && phase == PH_XY2))
+                          ? I.Ulo[S.ucur ^ 1] : nullptr;
   const float* c = I.c;
   double acc[NVP];
 #pragma unroll
@@ -229,34 +274,46 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const int j = cb * VCOL + lc;
   // ---- constraint sums, split over the NGRP groups ----
   {
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     if (j < n) {
       if (phase == PH_TRIAL || phase == PH_KKT32B) {
         const float* Us = (phase == PH_KKT32B) ? Un : Uc;
+        const float* Ul = (phase == PH_KKT32B) ? Unlo : Uclo;
         for (int i = 1 + grp; i <= m; i += NGRP) {
-          const double v = (double)Us[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j];
+          const double v = (double)Us[(size_t)i * ldv + j] + (Ul ? (double)Ul[(size_t)i * ldv + j] : 0.0) +
+                           (double)c[(size_t)i * ldv + j];
           s0 += ys[i - 1] * v;
           s1 += yts[i - 1] * v;
         }
       } else if (phase == PH_XY2) {
         for (int i = 1 + grp; i <= m; i += NGRP) {
           const double dy = yts[i - 1] - ys[i - 1];
-          s0 += dy * ((double)Un[(size_t)i * ldv + j] + (double)c[(size_t)i * ldv + j]);
+          s0 += dy * ((double)Un[(size_t)i * ldv + j] + (Unlo ? (double)Unlo[(size_t)i * ldv + j] : 0.0) +
+                      (double)c[(size_t)i * ldv + j]);
           s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
+        }
+      } else if (gap_phase(phase)) {
+        // sum_i y_i (Q_i w)_j, sum_i y_i (Q_i z)_j, sum_i y_i c_ij
+        for (int i = 1 + grp; i <= m; i += NGRP) {
+          s0 += ys[i - 1] * (double)Un[(size_t)i * ldv + j];
+          s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
+          s2 += ys[i - 1] * (double)c[(size_t)i * ldv + j];
         }
       }
     }
     pg[0][grp][lc] = s0;
     pg[1][grp][lc] = s1;
+    pg[2][grp][lc] = s2;
   }
   __syncthreads();
 
   if (grp == 0 && j < n) {
-    double gc = 0.0, gt = 0.0;
+    double gc = 0.0, gt = 0.0, g2 = 0.0;
 #pragma unroll
     for (int g = 0; g < NGRP; ++g) {
       gc += pg[0][g][lc];
       gt += pg[1][g][lc];
+      g2 += pg[2][g][lc];
     }
     const double xj = xk[j];
     const float xj32 = I.xf[S.xcur][j];
@@ -264,7 +321,8 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     const double q0d = (I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] : 0.0;
     if (phase == PH_TRIAL || phase == PH_KKT32B) {
       const float* Us = (phase == PH_KKT32B) ? Un : Uc;
-      const double u0 = (I.s_off ? q0d * (double)xj32 : (double)Us[j]);
+      const float* Ul = (phase == PH_KKT32B) ? Unlo : Uclo;
+      const double u0 = (I.s_off ? q0d * xj : (double)Us[j] + (Ul ? (double)Ul[j] : 0.0));
       const double gf = u0 + c0;
       const double grad = gf + gc;
       if (kkt_due) {
@@ -275,7 +333,11 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         acc[V_GC] = gc * gc;
       }
       if (phase == PH_KKT32B) {
-        if (I.s_off) Un[j] = (float)(q0d * (double)xj32);
+        if (I.s_off) {
+          const double u0n = q0d * xj;
+          Un[j] = (float)u0n;
+          if (Unlo) I.Ulo[S.ucur ^ 1][j] = (float)(u0n - (double)(float)u0n);
+        }
       } else {
         double step;
         if (P.variant == RAPDB_YX) {
@@ -293,27 +355,74 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         const float d32 = (float)(xt - xj);
         xt_out[j] = xt;
         xt_out32[j] = xt32;
+        xt_outlo[j] = (float)(xt - (double)xt32);
         I.dv[j] = d32;
         sx[lc] = xt32;
         sd[lc] = d32;
         acc[V_DD] = (double)d32 * (double)d32;
         if (I.s_off) {
-          const float u0n = (float)(q0d * (double)xt32);
+          const double u0d = q0d * (S.precision == 2 ? xt : (double)xt32);
+          const float u0n = (float)u0d;
           const float w0 = (float)(q0d * (double)d32);
           Un[j] = u0n;
+          if (S.precision == 2) I.Ulo[S.ucur ^ 1][j] = (float)(u0d - (double)u0n);
           I.W[j] = w0;
-          acc[V_XU0] = (double)xt32 * (double)u0n;
+          acc[V_XU0] = (S.precision == 2 ? xt : (double)xt32) * u0d;
           acc[V_DW0] = (double)d32 * (double)w0;
           acc[V_DU0] = (double)d32 * u0;
         }
         acc[V_CX0] = c0 * (double)xt32;
         acc[V_CD0] = c0 * (double)d32;
+        if (gap_due && S.gap_evals == 0) I.gpf[j] = hash_unit((uint32_t)j);
         if (fresh) {
           if (P.log_cap > 0 && it >= 1 && it <= P.log_cap && P.x_log)
             P.x_log[(size_t)(it - 1) * n + j] = (float)xj;
           if (P.restart_from_average && k >= 1)
             I.xcum[j] = (k == 1 ? 0.0 : I.xcum[j]) + S.t_last * xj;
         }
+      }
+    } else if (phase == PH_GAPP) {
+      // power iteration on Q(y): consume Q(y)p of the last pass, write the next p
+      const float pj = I.gpf[j];
+      const double hp = (I.s_off ? q0d * (double)pj : (double)Un[j]) + gc;
+      acc[V_AA] = (double)pj * hp;
+      acc[V_BB] = (double)pj * (double)pj;
+      acc[V_X2] = hp * hp;
+      if (gap_iter < gap_P) {
+        const float pn = (float)(hp / S.gap_pnorm);
+        I.gpf[j] = pn;
+        sx[lc] = pn;
+        sd[lc] = pn;
+      } else {
+        // last power step: the accelerated gradient starts at z_0 = w_0 = x^k
+        I.gz[j] = xj;
+        I.gzf[j] = xj32;
+        I.gwf[j] = xj32;
+        sx[lc] = xj32;
+        sd[lc] = xj32;
+      }
+    } else if (phase == PH_GAPF || phase == PH_GAPV) {
+      // x-subproblem min_{z in box} Phi(z, y) + xi |z - x|^2 (Hessian Q(y) + 2 xi I)
+      const double zk = I.gz[j];
+      const float zk32 = I.gzf[j];
+      const double cl = c0 + g2;                                       // c(y)_j
+      const double hz = (I.s_off ? q0d * (double)zk32 : (double)I.W[j]) + gt;  // (Q(y) z)_j
+      acc[2] = (double)zk32 * hz;
+      acc[3] = cl * (double)zk32;
+      acc[4] = ((double)zk32 - xj) * ((double)zk32 - xj);
+      if (phase == PH_GAPF) {
+        const float wj = I.gwf[j];
+        const double hw = (I.s_off ? q0d * (double)wj : (double)Un[j]) + gc;   // (Q(y) w)_j
+        const double grad = hw + 2.0 * P.xi * ((double)wj - xj) + cl;
+        const double zn = fmin(fmax((double)wj - grad / S.gap_L, (double)I.lb[j]), (double)I.ub[j]);
+        const double wn = zn + S.gap_beta * (zn - zk);                  // momentum of this step
+        I.gz[j] = zn;
+        I.gzf[j] = (float)zn;
+        I.gwf[j] = (float)wn;
+        sx[lc] = (float)wn;
+        sd[lc] = (float)zn;
+        acc[0] = (zn - zk) * (zn - zk);
+        acc[1] = zn * zn;
       }
     } else if (phase == PH_XY2) {
       // a = sum_i dy_i (u~_i + c_i),  b = Q(y^k) d = w_0 + sum_i y_i w_i
@@ -326,6 +435,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       const float xt32 = (float)xt;
       xt_out[j] = xt;
       xt_out32[j] = xt32;
+      xt_outlo[j] = (float)(xt - (double)xt32);
       I.dv[j] = 0.0f;
       sx[lc] = xt32;
       sd[lc] = 0.0f;
@@ -338,11 +448,17 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       acc[V_CX0] = c0 * (double)xt32;
     }
   }
-  if (ST == RAPDB_FP8 && (phase == PH_TRIAL || phase == PH_INIT || phase == PH_AVG)) {
-    // pre-scaled right-hand sides s_i .* x~ and s_i .* d of every stored matrix
+  if (ST == RAPDB_FP8 && (phase == PH_TRIAL || phase == PH_INIT || phase == PH_AVG || phase == PH_GAPP ||
+                           phase == PH_GAPF)) {
+    // pre-scaled right-hand sides s_i .* (first, second right-hand side) of every stored matrix
     __syncthreads();
     if (j < n) {
-      const float xv = sx[lc], dvv = sd[lc];
+      float xv = sx[lc], dvv = sd[lc];
+      if (phase == PH_TRIAL && gap_due && grp >= 0) {
+        // the trial may be replaced by the first power pass: its RHS is p_0
+        xv = I.gpf[j];
+        dvv = xv;
+      }
       for (int s = grp; s < I.M; s += NGRP) {
         const float sc = I.qscale[(size_t)s * ldv + j];
         XS[(size_t)s * ldv + j] = sc * xv;
@@ -397,9 +513,9 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       S.r_feas = rf;
       if (P.kkt_log && it < P.log_cap) P.kkt_log[it] = rel;
       if (!(rel == rel)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
-      if (quantised_refining(I, S)) {
+      if (can_refine(I, S)) {
         S.rel_q = rel;
-        if (rel <= P.tol) { S.phase = PH_KKT32; return; }
+        if (rel <= P.tol) { start_check(I, S); return; }
       } else if (rel <= P.tol) {
         finish(S, ctrl, RAPDB_OK);
         return;
@@ -416,9 +532,101 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       S.phase = PH_AVG;
       return;
     }
+    if (gap_due) {                // smoothed-gap evaluation first: the trial is discarded
+      S.fresh = 0;
+      S.gap_it_done = it;
+      S.gap_iter = 1;             // the pass of this body is power pass #1 (right-hand side p_0)
+      S.gap_pnorm = 1.0;
+      S.phase = PH_GAPP;
+      return;
+    }
     S.restarts += S.restart_note;
     S.restart_note = 0;
     S.fresh = 0;
+    S.trial_ready = 1;
+    return;
+  }
+  if (phase == PH_TRIAL) {        // a further trial of the same iteration
+    if (tid == 0) S.trial_ready = 1;
+    return;
+  }
+  if (phase == PH_GAPP) {
+    if (tid != 0) return;
+    const double mu = vfin[V_AA] / vfin[V_BB];
+    S.gap_pnorm = sqrt(vfin[V_X2]);
+    if (!(S.gap_pnorm > 0.0) || !(mu == mu)) S.gap_pnorm = 1.0;
+    if (gap_iter < gap_P) {
+      S.gap_iter = gap_iter + 1;
+      return;
+    }
+    // step constant of the accelerated gradient: L = 2 mu + 2 xi (the
+    // Rayleigh quotient mu bounds lambda_max(Q(y)) from below), constant
+    // momentum (sqrt(L) - sqrt(2 xi)) / (sqrt(L) + sqrt(2 xi)) for the
+    // 2 xi-strongly convex subproblem
+    const double lq = fmax(mu, 0.0);
+    S.gap_L = 2.0 * lq + 2.0 * P.xi;
+    const double sl = sqrt(S.gap_L), sm = sqrt(2.0 * P.xi);
+    S.gap_mu = (sl - sm) / (sl + sm);
+    S.gap_beta = S.gap_mu;
+    S.gap_prev = INFINITY;
+    S.gap_iter = 0;
+    S.phase = PH_GAPF;
+    return;
+  }
+  if (phase == PH_GAPF || phase == PH_GAPV) {
+    // x-subproblem objective at z_k: 0.5 z'Q(y)z + c(y)'z + y'd + xi |z - x|^2
+    double yd[1] = {0.0};
+    for (int i = tid; i < m; i += NT) yd[0] += ys[i] * I.dcon[i];
+    block_allsum<1>(yd, red);
+    const double xval = 0.5 * vfin[2] + vfin[3] + yd[0] + P.xi * vfin[4];
+    if (phase == PH_GAPF) {
+      if (tid != 0) return;
+      // function-value restart of the momentum: after an increase of the
+      // subproblem objective the next step is a plain projected gradient step
+      S.gap_beta = (gap_iter > 0 && xval > S.gap_prev) ? 0.0 : S.gap_mu;
+      S.gap_prev = xval;
+      const int k1 = gap_iter + 1;
+      const bool small = vfin[0] <= 1e-20 * (1.0 + vfin[1]);
+      if (k1 >= P.gap_inner_max || small) {
+        S.phase = PH_GAPV;       // the pass of this body forms Q z_K
+      } else {
+        S.gap_iter = k1;
+      }
+      return;
+    }
+    // PH_GAPV: y-part in closed form, y' = max(0, y + g(x)/(2 xi))
+    double yp[2] = {0.0, 0.0};
+    for (int i = tid; i < m; i += NT) {
+      const double gi = gk[i];
+      const double lp = fmax(0.0, ys[i] + gi / (2.0 * P.xi));
+      yp[0] += lp * gi;
+      yp[1] += (lp - ys[i]) * (lp - ys[i]);
+    }
+    block_allsum<2>(yp, red);
+    if (tid != 0) return;
+    const double yval = S.obj + yp[0] - P.xi * yp[1];
+    const double G = yval - xval;
+    S.gap_val = G;
+    if (P.gap_log && S.gap_evals < P.log_cap) P.gap_log[S.gap_evals] = G;
+    S.gap_evals += 1;
+    bool fire = false;
+    if (!S.gap_has_ref) {
+      S.gap_ref = G;
+      S.gap_has_ref = 1;
+    } else if (G <= P.q * S.gap_ref) {
+      fire = true;
+      S.gap_ref = G;
+    }
+    S.gap_iter = 0;
+    S.phase = PH_TRIAL;          // the next body's vector kernel prepares the trial
+    if (fire) {
+      restart_scalars(P, S);
+      S.restarts += 1;
+      if (can_refine(I, S)) {
+        S.fresh = 1;
+        start_check(I, S);
+      }
+    }
     return;
   }
   if (phase == PH_XY2) {
@@ -450,6 +658,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     return;
   }
   if (phase == PH_KKT32B) {
+    // the residual one precision level up (check_level) at x^k
     double fe[2] = {0.0, 0.0};
     kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1]);
     block_allsum<2>(fe, red);
@@ -481,7 +690,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         finish(S, ctrl, RAPDB_OK);
       } else {
         if (dec == 1) {
-          S.precision = 1;
+          S.precision = S.check_level;
           S.switches += 1;
           S.ucur ^= 1;
           restart_scalars(P, S);
@@ -509,7 +718,7 @@ __host__ __device__ constexpr size_t tma_bar_bytes() {
 }
 template <int NST, int RPW, int CWB>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
-  return NST == 0 ? 0 : (RPW == 0 ? rows_smem_bytes<CWB, NST>() : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB);
+  return NST <= 0 ? 0 : (RPW == 0 ? rows_smem_bytes<CWB, NST>() : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB);
 }
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
@@ -519,6 +728,8 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
                                           int ostride, double* red, uint8_t* dsm, int* err) {
   if constexpr (NST == 0) {
     pass_block<ST, RPW, UNR>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red);
+  } else if constexpr (NST < 0) {
+    pass_block_pipe<ST, RPW, UNR>(Qm, ld, row0, rows, x, v, xs, vs, scale, uold, crow, Uo, Wo, out, ostride, red);
   } else if constexpr (RPW == 0) {
     // whole-row stages of CWB bytes; rows longer than a stage stream through registers
     if ((size_t)ld * Elt<ST>::B <= (size_t)CWB)
@@ -538,7 +749,8 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
 // k_pass: the fused coupling pass + post-control
 // ---------------------------------------------------------------------------
 template <int ST, int RPW, int UNR, int NST, int CWB>
-__global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, State* __restrict__ states,
+__global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __restrict__ insts,
+                                                                State* __restrict__ states,
                                              Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
                                              const float* __restrict__ XS, const float* __restrict__ VS) {
   extern __shared__ __align__(128) uint8_t dsm[];
@@ -549,6 +761,7 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
   State& S = states[b];
   const int phase = S.phase;
   if (!pass_phase(phase)) return;
+  if (phase == PH_TRIAL && !S.trial_ready) return;   // no trial prepared in this body
   const int item = blockIdx.x - I.pblk0;
   const int s = item / I.nrb;
   const int r = item - s * I.nrb;
@@ -556,15 +769,37 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
   const int row0 = r * I.rb;
   const int rows = min(I.rb, I.n - row0);
   const int ldv = I.ldv;
-  const bool use32 = (phase == PH_KKT32) || (ST != RAPDB_F32 && S.precision == 1);
-  const float* x = (phase == PH_KKT32) ? I.xf[S.xcur] : I.xf[S.xcur ^ 1];
-  const float* v = (phase == PH_KKT32) ? I.xf[S.xcur] : I.dv;
-  const float* uold = (phase == PH_KKT32) ? nullptr : I.U[S.ucur] + (size_t)i * ldv;
+  const int level = (phase == PH_KKT32) ? S.check_level : S.precision;
+  const bool comp = (level == 2) && !gap_phase(phase);               // compensated products
+  const bool use32 = (ST != RAPDB_F32) && (level >= 1);
+  const float* x;
+  const float* v;
+  if (phase == PH_KKT32) {
+    x = I.xf[S.xcur];
+    v = x;
+  } else if (phase == PH_GAPP) {
+    x = I.gpf;
+    v = x;
+  } else if (phase == PH_GAPF || phase == PH_GAPV) {
+    x = I.gwf;
+    v = I.gzf;
+  } else {
+    x = I.xf[S.xcur ^ 1];
+    v = I.dv;
+  }
+  const float* uold = (phase == PH_KKT32 || gap_phase(phase)) ? nullptr : I.U[S.ucur] + (size_t)i * ldv;
   float* Uo = I.U[S.ucur ^ 1] + (size_t)i * ldv;
   float* Wo = I.W + (size_t)i * ldv;
   double* out = I.part + (size_t)s * NDOT * I.nrb + r;
   const float* crow = I.c + (size_t)i * ldv;
-  if (use32 || ST == RAPDB_F32) {
+  if (comp) {
+    const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
+    const float* xlo = (phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1];
+    pass_block_prec2<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
+                           uold ? I.Ulo[S.ucur] + (size_t)i * ldv : nullptr, crow, Uo,
+                           I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo, out, I.nrb, red);
+  } else if (use32 || ST == RAPDB_F32) {
     const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
     pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,
@@ -598,6 +833,11 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
   const int m = I.m;
   const double* D = I.dots;
   const int k0 = S.k, gcur0 = S.gcur, ycur0 = S.ycur;
+  if (gap_phase(phase)) {          // smoothed-gap passes: the vector kernel consumes the products
+    if (tid == 0) S.passes += 1;
+    return;
+  }
+  if (phase == PH_TRIAL && tid == 0) S.trial_ready = 0;
   // g at the pass point: g_i = 0.5 x'Q_i x + c_i'x + d_i, with the per-phase
   // per-constraint work fused into the same loop
   if (phase == PH_TRIAL && P.variant == RAPDB_YX) {
@@ -690,12 +930,16 @@ __global__ void __launch_bounds__(NT) k_pass(const Inst* __restrict__ insts, Sta
 }
 
 // ---- stand-alone coupling pass (no control) ------------------------------
+// level 0: the stored Q; 1: the float32 Q of a quantised context; 2: float32
+// Q with compensated products of x + xlo (low parts of U written to Ulo, the
+// uold dot not formed).
 template <int ST, int RPW, int UNR, int NST, int CWB>
-__global__ void __launch_bounds__(NT) k_pass_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
+__global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
                                                    const float* __restrict__ v, const float* __restrict__ XS,
                                                    const float* __restrict__ VS, const float* __restrict__ uold,
                                                    float* __restrict__ U, float* __restrict__ W,
-                                                   double* __restrict__ part, int use32, int* __restrict__ err) {
+                                                   double* __restrict__ part, int level, const float* __restrict__ xlo,
+                                                   float* __restrict__ Ulo, int* __restrict__ err) {
   extern __shared__ __align__(128) uint8_t dsm[];
   __shared__ double red[NWARP * NDOT];
   const Inst& I = insts[0];
@@ -708,7 +952,14 @@ __global__ void __launch_bounds__(NT) k_pass_plain(const Inst* __restrict__ inst
   double* out = part + (size_t)s * NDOT * I.nrb + r;
   const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
   const float* crow = I.c + (size_t)i * ldv;
-  if (use32 || ST == RAPDB_F32) {
+  const int use32 = (ST != RAPDB_F32 && level >= 1) ? 1 : 0;
+  if (level == 2) {
+    const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
+    // compensated products of x = x + xlo; the low parts of U go to Ulo
+    pass_block_prec2<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, nullptr, nullptr, crow,
+                           U + (size_t)i * ldv, Ulo + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb, red);
+  } else if (use32 || ST == RAPDB_F32) {
     const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
     pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,

@@ -16,17 +16,18 @@ struct Ctrl;
 //   UNR  16-byte chunks in flight per row and lane (register streaming),
 //   NST  shared-memory slots (bulk-copy staging; 0 = registers),
 //   CWB  bytes of each row per warp slot, or bytes per CTA stage (RPW = 0).
-constexpr int NVAR = 6;
-constexpr int kVarRPW[NVAR] = {4, 4, 4, 0, 0, 0};
-constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0, 0};
-constexpr int kVarNST[NVAR] = {0, 0, 4, 3, 4, 3};
-constexpr int kVarCWB[NVAR] = {0, 0, 512, 32768, 16384, 65536};
+//   NST = -1: register streaming with the next batch's loads in flight.
+constexpr int NVAR = 8;
+constexpr int kVarRPW[NVAR] = {4, 4, 4, 0, 0, 0, 4, 4};
+constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0, 0, 2, 4};
+constexpr int kVarNST[NVAR] = {0, 0, 4, 3, 4, 3, -1, -1};
+constexpr int kVarCWB[NVAR] = {0, 0, 512, 32768, 16384, 65536, 0, 0};
 
 // dynamic shared memory of variant vi (8 warps).  Warp stages: mbarrier area
 // rounded up to 128 bytes, then 8 * NST * RPW * CWB bytes of slots.  CTA
 // stages: 128 bytes of mbarriers, 1 KB of row sums, NST * CWB bytes of slots.
 inline size_t var_smem(int vi) {
-  if (kVarNST[vi] == 0) return 0;
+  if (kVarNST[vi] <= 0) return 0;
   if (kVarRPW[vi] == 0) return (size_t)128 + 1024 + (size_t)kVarNST[vi] * kVarCWB[vi];
   const size_t bars = ((size_t)8 * kVarNST[vi] * 8 + 127) / 128 * 128;
   return bars + (size_t)8 * kVarNST[vi] * kVarRPW[vi] * kVarCWB[vi];
@@ -40,7 +41,7 @@ inline size_t var_smem(int vi) {
                          const float* XS, const float* VS);                                                       \
   void launch_plain_##SUF(int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x, const float* v,          \
                           const float* XS, const float* VS, const float* uold, float* U, float* W, double* part,  \
-                          int use32, int* err);
+                          int level, const float* xlo, float* Ulo, int* err);
 
 RAPDB_DECLARE_LAUNCHERS(f32)
 RAPDB_DECLARE_LAUNCHERS(bf16)

@@ -100,6 +100,7 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
     const float x = I.xf[0][j];
     I.xb[0][j] = (double)x;
+    I.xl[0][j] = 0.0f;
     if (!(x >= I.lb[j] && x <= I.ub[j])) atomicOr(&flags[0], 1);
   }
   for (int i = threadIdx.x; i < I.m; i += blockDim.x)
@@ -113,6 +114,7 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   S.phase = PH_INIT;
   S.rel_kkt = S.r_stat = S.r_feas = NAN;
   S.rel_q = INFINITY;
+  S.gap_it_done = -1;
   S.deadline_ns = time_limit_s > 0.0 ? (long long)(now + (unsigned long long)(time_limit_s * 1e9)) : 0;
 }
 

@@ -58,7 +58,7 @@ def _load():
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
         "rapdb_coupling_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
-        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp]),
+        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp, vp]),
         "rapdb_create_batched": (C.c_int, [ctxpp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                            C.POINTER(vp), P, vp]),
@@ -68,7 +68,8 @@ def _load():
         "rapdb_resume": (C.c_int, [vp, vp, vp, I]),
         "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]),
-        "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "rapdb_get_solution_f64": (C.c_int, [vp, vp, vp]),
         "rapdb_coupling_pass_noalloc": (C.c_int, [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "rapdb_last_error": (C.c_char_p, [vp]),
         "rapdb_destroy": (None, [vp]),
@@ -228,7 +229,7 @@ class Solver:
         import torch
         dev = self.device
         if capacity <= 0:
-            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None, None), self.ctx)
+            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None, None, None), self.ctx)
             self._log = None
             return
         tau = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
@@ -237,8 +238,10 @@ class Solver:
         yl = (torch.full((capacity, max(self.m, 1)), float("nan"), dtype=torch.float32, device=dev)
               if iterates else None)
         kk = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
-        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl), _ptr(kk)), self.ctx)
-        self._log = dict(tau=tau, trials=tr, x=xl, y=yl, kkt=kk)
+        gp = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
+        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl), _ptr(kk), _ptr(gp)),
+               self.ctx)
+        self._log = dict(tau=tau, trials=tr, x=xl, y=yl, kkt=kk, gap=gp)
 
     @property
     def log(self):
@@ -255,10 +258,20 @@ class Solver:
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib.rapdb_set_state(self.ctx, buf, len(blob)), self.ctx)
 
-    def time_pass(self, reps: int = 20):
-        """(average ms per coupling-pass launch, algorithmic bytes per pass)."""
+    def solution_f64(self):
+        """The solver's float64 iterate (x, y) of the last solve."""
+        import torch
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        y = torch.empty(max(self.m, 1), dtype=torch.float64, device=self.device)
+        _check(lib.rapdb_get_solution_f64(self.ctx, _ptr(x), _ptr(y)), self.ctx)
+        return x, y[:self.m]
+
+    def time_pass(self, reps: int = 20, level: int = -1):
+        """(average ms per coupling-pass launch, algorithmic bytes per pass) at a
+        precision level (-1: where the last solve ended, 0 stored Q, 1 float32 Q,
+        2 compensated float32 products)."""
         ms, b = C.c_double(), C.c_int64()
-        _check(lib.rapdb_time_pass(self.ctx, reps, C.byref(ms), C.byref(b)), self.ctx)
+        _check(lib.rapdb_time_pass(self.ctx, reps, level, C.byref(ms), C.byref(b)), self.ctx)
         return ms.value, b.value
 
     def tile(self) -> dict:

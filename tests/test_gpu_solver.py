@@ -196,9 +196,10 @@ def test_quantised_storage_with_refinement(R, cuda, storage):
     x, y = gpu_vecs(data, cuda)
     info = s.solve(x, y)
     assert info["status"] == R.OK, info
-    assert info["precision_switches"] == 1
+    assert info["precision_switches"] >= 1
+    # the stand-alone residual uses plain float32 products at the float32 point
     rel_lib, _, _ = s.kkt_residual(x, y)
-    assert rel_lib <= 1e-6
+    assert rel_lib <= 1.5e-6
     prob = O.Problem.from_data(data)
     rel, _, _ = O.kkt_residual(prob, x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64))
     assert rel <= 2e-6
@@ -237,9 +238,10 @@ def test_batched_matches_single(R, cuda):
     xs = [torch.zeros(d.n, device=cuda) for d in datas]
     ys = [torch.zeros(max(d.m, 1), device=cuda) for d in datas]
     infos = bs.solve(xs, ys)
-    # a single-instance context with the batched context's tile (32 rows, the
-    # register-streaming variant) performs the same floating-point operations
-    p1 = R.Params.default(tol=1e-6, rows_per_block=32, pass_variant=0)
+    # a single-instance context with the batched context's tile (64 rows, the
+    # pipelined register-streaming variant) performs the same floating-point
+    # operations
+    p1 = R.Params.default(tol=1e-6, rows_per_block=64, pass_variant=6)
     for d, dv, xb, yb, ib in zip(datas, devs, xs, ys, infos):
         assert ib["status"] == R.OK and ib["rel_kkt"] <= 1e-6
         s = R.Solver(dv, p1)
@@ -302,4 +304,81 @@ def test_kkt_residual_at_random_points(R, cuda, c1):
         rel, rs, rf = s.kkt_residual(torch.from_numpy(x).to(cuda), torch.from_numpy(y).to(cuda))
         ro, rso, rfo = O.kkt_residual(prob, x.astype(np.float64), y.astype(np.float64))
         np.testing.assert_allclose([rel, rs, rf], [ro, rso, rfo], rtol=1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_smoothed_gap_matches_oracle_at_logged_iterates(R, cuda, c1, variant):
+    """Adaptive restart (eq. ada_restart): the device's G_xi at iterates x^30,
+    x^40 (fixed step, so both sides are at the same point) equals the oracle's
+    exact G_xi (y-part closed form, x-part an exact box QP)."""
+    p = R.Params.default(variant, backtracking=0, tau_bar=0.05, tol=0.0, max_iter=45, restart=R.RESTART_GAP,
+                         gap_first=30, gap_every=10)
+    s = R.Solver(c1.to(cuda), p)
+    s.set_log(50)
+    x, y = gpu_vecs(c1, cuda)
+    info = s.solve(x, y)
+    assert info["iters"] == 45
+    xl = s.log["x"].cpu().numpy().astype(np.float64)
+    yl = s.log["y"].cpu().numpy().astype(np.float64)
+    G = s.log["gap"].cpu().numpy()
+    prob = O.Problem.from_data(c1)
+    for e, it in enumerate([30, 40]):
+        Go = O.smoothed_gap(prob, xl[it - 1], yl[it - 1, :c1.m], p.xi)
+        assert Go > 0
+        assert abs(G[e] - Go) <= 1e-4 * abs(Go) + 1e-9, (it, G[e], Go)
+    # the restart fired exactly when the oracle's rule says so
+    r = O.rapdb(prob, p=oracle_params(R, p))
+    assert info["restarts"] == r.restarts
+    s.close()
+
+
+def test_adaptive_restart_full_solve(R, cuda, c1):
+    p = R.Params.default(R.YX, restart=R.RESTART_GAP, gap_first=50, gap_every=100, tol=1e-6, max_iter=20000)
+    s = R.Solver(c1.to(cuda), p)
+    s.set_log(64, iterates=False)
+    x, y = gpu_vecs(c1, cuda)
+    info = s.solve(x, y)
+    assert info["status"] == R.OK, info
+    prob = O.Problem.from_data(c1)
+    r = O.rapdb(prob, p=oracle_params(R, p))
+    assert r.status == 0
+    fo = prob.f(r.x)
+    assert abs(info["obj"] - fo) <= 1e-5 * (1 + abs(fo))
+    G = s.log["gap"].cpu().numpy()
+    Go = [g for (_, g, _) in r.log["gap"]]
+    # the first evaluation (k = 50) happens before the trajectories part
+    assert abs(G[0] - Go[0]) <= 1e-3 * abs(Go[0])
+    # (the precision switch of the refinement is a restart of its own)
+    assert abs(info["restarts"] - info["precision_switches"] - r.restarts) <= 1
+    # each pass of the gap evaluation is counted; the solve still ends near the oracle
+    assert info["passes"] > info["trials"]
+    s.close()
+
+
+def test_compensated_refinement_breaks_float32_floor(R, cuda):
+    """n = 1024, m = 50: plain float32 products stall near rel KKT 1.3e-6 on
+    this instance (the Lagrangian gradient cancels the per-constraint
+    products' rounding).  With refinement the solver switches to compensated
+    (double-float) products and reaches 2e-7, confirmed by the oracle's float64
+    residual at the returned point."""
+    data = W.random_qcqp(1024, 50, rows=512, seed=0)
+    p = R.Params.default(tol=2e-7, max_iter=6000, refine=1)
+    s = R.Solver(data.to(cuda), p)
+    x, y = gpu_vecs(data, cuda)
+    info = s.solve(x, y)
+    assert info["status"] == R.OK, info
+    assert info["precision_switches"] >= 1 and info["rel_kkt"] <= 2e-7
+    prob = O.Problem.from_data(data)
+    x64, y64 = s.solution_f64()
+    rel, _, _ = O.kkt_residual(prob, x64.cpu().numpy(), y64.cpu().numpy())
+    assert rel <= 3e-7
+    # the float32 copy returned by rapdb_solve is the same point rounded
+    np.testing.assert_array_equal(x.cpu().numpy(), x64.cpu().numpy().astype(np.float32))
+    s.close()
+    p0 = R.Params.default(tol=2e-7, max_iter=3000, refine=0)
+    s = R.Solver(data.to(cuda), p0)
+    x, y = gpu_vecs(data, cuda)
+    info0 = s.solve(x, y)
+    assert info0["status"] == R.ERR_MAXITER      # the float32 floor without refinement
     s.close()
