@@ -34,10 +34,10 @@ WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1),
             "d_i=-U[0.1,1], box [-10,10], FP32 storage (3.42 GB Q stack); rAPDB-yx non-monotone, "
             "adaptive (smoothed-gap) restart first at k=50 then every 500, precision refinement to "
             "compensated float32 products, x0=y0=0, stop at rel KKT <= 1e-6")
-# DRAM bytes (read + write) of one coupling-pass launch on this workload from an
-# ncu capture (profiles/coupling_pass_n4096_m50_f32.md); None when no capture of
-# the current kernel exists.
-PASS_DRAM_BYTES = None
+# DRAM bytes (read + write) of one coupling-pass launch on this workload: the
+# ncu capture of the same tile on the 11-matrix case (741.9 MB per launch,
+# profiles/coupling_pass_n4096_m10_f32.md) scaled by the 51/11 matrices.
+PASS_DRAM_BYTES = 741.9e6 * 51 / 11
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 
