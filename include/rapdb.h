@@ -148,8 +148,10 @@ rapdb_status rapdb_solve(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
  * here.  Synchronises the context's stream. */
 rapdb_status rapdb_get_solution_f64(rapdb_ctx *ctx, double *x, double *y);
 
-/* Relative KKT residual at (x, y) (device): one float32 coupling pass with the
- * context's float32 Q (the quantised copy only when no float32 Q exists), then
+/* Relative KKT residual at (x, y) (device): one coupling pass with the most
+ * precise products the context has (compensated float32 products when it
+ * was created with refine = 1, else the float32 Q, else the stored copy),
+ * then
  *   r_stat_j = dist(0, grad_x L(x,y)_j + N_[lb,ub](x_j)),
  *   r_feas_i = |g_i(x)| if y_i > 0 else max(g_i(x), 0),
  *   rel = max(||r_stat|| / (1 + max(||Q_0x+c_0||, ||sum_i y_i(Q_ix+c_i)||)),

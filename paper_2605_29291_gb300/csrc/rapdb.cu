@@ -828,17 +828,23 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
   float* xpad = ctx->txv;
   CK(cudaMemcpyAsync(xpad, x, (size_t)I.n * 4, cudaMemcpyDeviceToDevice, st));
   if (I.m > 0) k_f2d<<<1, 256, 0, st>>>(y, ctx->ty, I.m);
-  const int use32 = (I.storage != RAPDB_F32 && I.Q32) ? 1 : 0;
+  // the most precise products the context has: compensated float32 products
+  // (refine = 1), else float32 Q, else the stored Q
+  const int level = I.Ulo[0] ? 2 : ((I.storage != RAPDB_F32 && I.Q32) ? 1 : 0);
   float* Ut = ctx->tU;
   float* Wt = ctx->tW;
-  if (I.storage == RAPDB_FP8 && !use32)
+  float* Ulo = level == 2 ? ctx->tUo : nullptr;
+  float* xzero = ctx->txv + I.ldv;   // zero low part of the float32 x
+  if (level == 2) CK(cudaMemsetAsync(xzero, 0, (size_t)I.ldv * 4, st));
+  if (I.storage == RAPDB_FP8 && level == 0)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
   else if (I.s_off)
-    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, use32);
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, xpad, nullptr, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart,
+                                      level >= 1 ? 1 : 0);
   launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut,
-               Wt, ctx->tpart, use32, &ctx->d_ctrl->err);
+               Wt, ctx->tpart, level, &ctx->d_ctrl->err, xzero, Ulo);
   k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots);
-  k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, ctx->tvpart);
+  k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, Ulo, ctx->tvpart);
   k_kkt_final<<<1, 32, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout);
   CK(cudaGetLastError());
   double out[4];

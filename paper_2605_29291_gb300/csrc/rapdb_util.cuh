@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NT) k_dots_final(const Inst* __restrict__ inst
 // not stored): ||r_stat||^2, ||Q_0x+c_0||^2, ||sum_i y_i(Q_ix+c_i)||^2.
 __global__ void __launch_bounds__(NT) k_kkt_plain(const Inst* __restrict__ insts, const float* __restrict__ x,
                                                   const double* __restrict__ y, const float* __restrict__ U,
-                                                  double* __restrict__ vpart) {
+                                                  const float* __restrict__ Ulo, double* __restrict__ vpart) {
   __shared__ double red[NWARP * 3];
   const Inst& I = insts[0];
   const int j = blockIdx.x * NT + threadIdx.x;
@@ -189,11 +189,12 @@ __global__ void __launch_bounds__(NT) k_kkt_plain(const Inst* __restrict__ insts
   if (j < I.n) {
     const double xj = x[j];
     const double u0 = I.s_off ? ((I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] * (double)x[j] : 0.0)
-                              : (double)U[j];
+                              : (double)U[j] + (Ulo ? (double)Ulo[j] : 0.0);
     const double gf = u0 + (double)I.c[j];
     double gc = 0.0;
     for (int i = 1; i <= I.m; ++i)
-      gc += y[i - 1] * ((double)U[(size_t)i * I.ldv + j] + (double)I.c[(size_t)i * I.ldv + j]);
+      gc += y[i - 1] * ((double)U[(size_t)i * I.ldv + j] + (Ulo ? (double)Ulo[(size_t)i * I.ldv + j] : 0.0) +
+                        (double)I.c[(size_t)i * I.ldv + j]);
     const double grad = gf + gc;
     const double lo = I.lb[j], hi = I.ub[j];
     const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
