@@ -270,6 +270,22 @@ rapdb_status rapdb_coupling_pass_noalloc(int64_t n, int64_t m, const float *Q, c
                                          const float *x, const float *v, const float *uold,
                                          float *U, float *W, double *dots, void *stream);
 
+/* Self-test of the bounded wait that guards every bulk-copy stage of the
+ * coupling pass (the paper has no counterpart: it is failure detection).  One
+ * warp waits on an mbarrier phase with the pass's own wait routine under a
+ * limit of limit_us microseconds (1 .. 2,000,000).  complete = 1: a real
+ * 16-byte bulk copy completes the phase; the wait returns, *gave_up = 0 and
+ * *copied_sum = 10 (the sum of the four copied floats).  complete = 0: the
+ * barrier expects 16 bytes that no copy delivers; the wait gives up at the
+ * limit, *gave_up = 1 and *copied_sum = -1.  *waited_ms is the device time
+ * the wait took.  No copy is ever left in flight, so the device stays usable
+ * either way.  Runs synchronously on the current device (default stream);
+ * allocates and frees one small device buffer.  Outputs may be NULL.
+ * Returns RAPDB_ERR_INVALID for a bad limit or flag, RAPDB_ERR_CUDA if a
+ * CUDA call fails. */
+rapdb_status rapdb_wait_selftest(int32_t complete, int64_t limit_us, int32_t *gave_up, double *waited_ms,
+                                 float *copied_sum);
+
 const char *rapdb_last_error(const rapdb_ctx *ctx);
 void rapdb_destroy(rapdb_ctx *ctx);
 

@@ -104,3 +104,23 @@ def fp8_dequantize(codes: np.ndarray, s: np.ndarray) -> np.ndarray:
     """float64 Q~ = diag(s) dec(codes) diag(s)."""
     s64 = np.asarray(s, np.float64)
     return s64[:, None] * _TABLE[codes] * s64[None, :]
+
+
+def jacobi_factors(diag: np.ndarray):
+    """(r, s') of the symmetric Jacobi-scaled storage from the float32 diagonal:
+    r_j = 1/sqrt(Q_jj), s'_j = sqrt(Q_jj)/16 (r_j = 1, s'_j = 1/16 when Q_jj <= 0)."""
+    dg = np.asarray(diag, dtype=np.float32)
+    pos = dg > 0
+    sq = np.where(pos, np.sqrt(np.where(pos, dg, np.float32(1))), np.float32(1)).astype(np.float32)
+    r = (np.float32(1) / sq).astype(np.float32)
+    return r, (sq * np.float32(1.0 / 16.0)).astype(np.float32)
+
+
+def fp8_jacobi_codes(q: np.ndarray, r_row: np.ndarray, r_col: np.ndarray) -> np.ndarray:
+    """E4M3 codes of single entries Q_jk of the Jacobi-scaled storage, given
+    r_j and r_k (broadcast against q): E4M3(((Q_jk * r_j) * r_k) * 256), each
+    product rounded to float32 as in fp8_jacobi_quantize.  Lets a few rows or
+    columns of a matrix too large to quantise here be checked on their own."""
+    q = np.asarray(q, dtype=np.float32)
+    C = ((q * np.asarray(r_row, np.float32)).astype(np.float32) * np.asarray(r_col, np.float32)).astype(np.float32)
+    return e4m3_encode((C * np.float32(256.0)).astype(np.float32))

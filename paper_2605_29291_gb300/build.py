@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librapdb.so")
-SOURCES = ["rapdb.cu", "kern_f32.cu", "kern_bf16.cu", "kern_fp8.cu", "rapdb_noalloc.cu"]
+SOURCES = ["rapdb.cu", "kern_f32.cu", "kern_bf16.cu", "kern_fp8.cu", "rapdb_noalloc.cu", "rapdb_selftest.cu"]
 DEPS = SOURCES + ["rapdb_device.cuh", "rapdb_kernels.cuh", "rapdb_util.cuh", "rapdb_launch.h", "kern_impl.cuh"]
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -71,6 +71,8 @@ def _load():
         "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rapdb_get_solution_f64": (C.c_int, [vp, vp, vp]),
         "rapdb_coupling_pass_noalloc": (C.c_int, [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "rapdb_wait_selftest": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_float)]),
         "rapdb_last_error": (C.c_char_p, [vp]),
         "rapdb_destroy": (None, [vp]),
     }
@@ -298,6 +300,17 @@ def coupling_pass_noalloc(Q, c, x, v, uold=None, U=None, W=None, dots=None):
     if st != OK:
         raise RapdbError(st, "rapdb_coupling_pass_noalloc rejected the call (sizes, alignment or scratch limit)")
     return U, W, dots
+
+
+def wait_selftest(complete: bool, limit_us: int = 50000) -> dict:
+    """Run the bounded-wait self-test on the current device (see
+    rapdb_wait_selftest in include/rapdb.h): returns whether the wait gave
+    up, how long it waited (ms) and the sum of the copied floats."""
+    g, ms, sm = C.c_int32(0), C.c_double(0.0), C.c_float(0.0)
+    st = lib.rapdb_wait_selftest(1 if complete else 0, int(limit_us), C.byref(g), C.byref(ms), C.byref(sm))
+    if st != OK:
+        raise RapdbError(st, "rapdb_wait_selftest failed")
+    return {"gave_up": bool(g.value), "waited_ms": ms.value, "copied_sum": sm.value}
 
 
 class BatchedSolver:

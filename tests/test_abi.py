@@ -54,3 +54,9 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu():
     st = R.lib.rapdb_create(ctypes.byref(ctx), 10, 3, 0, None, None, None, None, None, None,
                             ctypes.byref(p), None)
     assert st == R.ERR_INVALID and b"NULL" in R.lib.rapdb_last_error(None)
+
+
+def test_wait_selftest_rejects_bad_arguments_without_touching_the_gpu():
+    from paper_2605_29291_gb300 import rapdb as R
+    for complete, limit in ((0, 0), (1, -5), (0, 2000001), (2, 1000)):
+        assert R.lib.rapdb_wait_selftest(complete, limit, None, None, None) == R.ERR_INVALID

@@ -66,3 +66,23 @@ def test_fp8_jacobi_is_symmetric_and_close(seed):
     d = np.sqrt(np.diag(Q).astype(np.float64))
     err = np.abs(Qt - Q) / np.outer(d, d)
     assert err.max() <= 2.0 ** -4 + 2.0 ** -9
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fp8_entrywise_codes_equal_the_whole_matrix_quantiser(seed):
+    """Codes of sampled rows and of single columns, computed entry by entry,
+    are the whole-matrix quantiser's codes; a zero-diagonal coordinate (the
+    epigraph variable of the kernel-learning form) takes r = 1, s' = 1/16."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((30, 50))
+    Q = np.zeros((51, 51), np.float32)
+    Q[:50, :50] = A.T @ A / 50
+    Q = ((Q + Q.T) * np.float32(0.5)).astype(np.float32)
+    codes, s = O.fp8_jacobi_quantize(Q)
+    r, s2 = QZ.jacobi_factors(np.diagonal(Q))
+    np.testing.assert_array_equal(s2, s)
+    assert r[50] == 1.0 and s2[50] == np.float32(1.0 / 16.0)
+    rows = np.array([0, 7, 49, 50])
+    np.testing.assert_array_equal(QZ.fp8_jacobi_codes(Q[rows], r[rows][:, None], r[None, :]), codes[rows])
+    for k in (0, 13, 50):
+        np.testing.assert_array_equal(QZ.fp8_jacobi_codes(Q[:, k], r, r[k]), codes[:, k])
