@@ -82,13 +82,14 @@ typedef struct {
   int32_t refine;             /* quantised storage: switch to float32 Q on a KKT stall*/
   double stall_ratio;         /* stall: rel KKT fell by less than this factor per run */
   int32_t max_iter, max_trials, kkt_every;
-  int32_t use_graph;          /* 1: device loop as a CUDA graph with a conditional    */
-                              /*    WHILE node; 0: host relaunches kernel chunks      */
+  int32_t use_graph;          /* 1: loop bodies captured in a CUDA graph of 32 bodies */
+                              /*    (two launches kept in flight); 0: host launches    */
+                              /*    the kernels of 16 bodies at a time                */
   double tol;                 /* stop when rel KKT <= tol (checked every kkt_every)  */
   double time_limit_s;        /* <= 0: none                                           */
   int32_t rows_per_block;     /* coupling pass tile height; 0 = autotune at create   */
   int32_t gap_inner_max;      /* inner iterations of the smoothed-gap box QP          */
-  int32_t pass_variant;       /* tile variant when rows_per_block > 0 (0..4, see     */
+  int32_t pass_variant;       /* tile variant when rows_per_block > 0 (0..9, see     */
                               /* rapdb_get_tile); ignored when autotuning           */
 } rapdb_params;
 
@@ -232,7 +233,9 @@ rapdb_status rapdb_set_state(rapdb_ctx *ctx, const void *buf, size_t len);
  * may come from a context created with a larger max_iter).  x, y (device, n
  * and m floats) receive the final iterate; info as for rapdb_solve.  Because
  * every reduction runs in a fixed order, a solve split by a checkpoint ends
- * bit for bit where the uninterrupted solve ends. */
+ * bit for bit where the uninterrupted solve ends, provided both contexts use
+ * the same coupling-pass tile (fix rows_per_block and pass_variant: tiles
+ * with different rows per warp add the products in different orders). */
 rapdb_status rapdb_resume(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
 
 /* Coupling-pass tile of the context: rows per CTA, CTAs per pass, rows each

@@ -45,6 +45,8 @@ void RAPDB_CAT(launch_pass_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const In
     case 5: k_pass<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, S, C, pm, XS, VS); break;
     case 6: k_pass<RAPDB_ST, 4, 2, -1, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
     case 7: k_pass<RAPDB_ST, 4, 4, -1, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
+    case 8: k_pass<RAPDB_ST, 8, 2, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
+    case 9: k_pass<RAPDB_ST, 8, 1, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
     default: k_pass<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS); break;
   }
 }
@@ -61,6 +63,8 @@ void RAPDB_CAT(launch_plain_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const I
     case 5: k_pass_plain<RAPDB_ST, 0, 0, 3, 65536><<<g, NT, var_smem(5), s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
     case 6: k_pass_plain<RAPDB_ST, 4, 2, -1, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
     case 7: k_pass_plain<RAPDB_ST, 4, 4, -1, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 8: k_pass_plain<RAPDB_ST, 8, 2, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
+    case 9: k_pass_plain<RAPDB_ST, 8, 1, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
     default: k_pass_plain<RAPDB_ST, 4, 2, 0, 0><<<g, NT, 0, s>>>(I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err); break;
   }
 }

@@ -317,6 +317,12 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
     for (int i = 0; i < m; ++i) dn += (double)hd[i] * (double)hd[i];
   }
   I.c = cc;
+  {
+    double* cdp = nullptr;
+    AL(cdp, (size_t)(m + 1) * ldv);
+    k_f2d<<<std::min<int64_t>(((int64_t)(m + 1) * ldv + 255) / 256, 4096), 256, 0, st>>>(cc, cdp, (int)((m + 1) * ldv));
+    I.cd = cdp;
+  }
   I.lb = lbp;
   I.ub = ubp;
   I.q0diag = q0d;

@@ -30,7 +30,7 @@ namespace rapdb_dev {
 
 constexpr int NT = 256;            // threads per CTA, all solver kernels
 constexpr int NWARP = NT / 32;
-constexpr int VCOL = 64;           // vector kernel: columns per CTA
+constexpr int VCOL = 32;           // vector kernel: columns per CTA
 constexpr int NGRP = NT / VCOL;    // ... and constraint groups per column
 constexpr int NDOT = 5;            // dots per (matrix, row block)
 constexpr int NVP = 12;            // vector-kernel partials per column block
@@ -90,6 +90,7 @@ struct Inst {
   const float* qscale;  // FP8: (M, ldv) symmetric scales s
   const float* q0diag;  // (ldv) diagonal of Q_0 when DIAG
   const float* c;       // (m+1, ldv)
+  const double* cd;     // (m+1, ldv): c in float64 (the vector kernel's constraint sums)
   const double* dcon;   // (m)
   const float* lb;      // (ldv)
   const float* ub;      // (ldv)
@@ -142,7 +143,7 @@ struct State {
   int gap_it_done;      // iteration of the last smoothed-gap evaluation (-1: none)
   int check_level;      // precision level of the pending accurate KKT check (KKT32 / KKT32B)
   unsigned int arrive_vec, arrive_pass;
-  int pad_;
+  int anchor_age;       // level 2: accepted iterations since U was last formed by a direct product
 };
 
 struct Ctrl {
@@ -919,6 +920,106 @@ __device__ __forceinline__ void pass_block_prec2(const float* __restrict__ Qf, i
       dsum[0] = fma(xj, u, dsum[0]);
       dsum[1] = fma(vj, w, dsum[1]);
       if (uoh) dsum[2] = fma(vj, (double)uoh[j] + (double)uol[j], dsum[2]);
+      dsum[3] = fma(cj, xj, dsum[3]);
+      dsum[4] = fma(cj, vj, dsum[4]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) {
+#pragma unroll
+    for (int o = 1; o < RPW; o <<= 1) dsum[q] += __shfl_xor_sync(0xffffffffu, dsum[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) smem[warp * NDOT + q] = dsum[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NDOT) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += smem[w * NDOT + threadIdx.x];
+    out[threadIdx.x * ostride] = s;
+  }
+  __syncthreads();
+}
+
+
+// Incremental form of the compensated pass (precision level 2, float32
+// storage), for trial points x~ = x^k + d: U' = U^k + Q d, with U^k the
+// double-float products at x^k (uoh + uol) and Q d formed in float32 (one
+// right-hand side).  Algebraically U' = Q x~; the float32 rounding of Q d is
+// of the order of eps_32 |Q||d|, so it vanishes with the step, and the
+// caller re-forms U by a direct compensated product every ANCHOR_EVERY
+// accepted iterations so that these roundings cannot add up.  Outputs and
+// dots as in pass_block_prec2.
+constexpr int ANCHOR_EVERY = 64;
+template <int RPW, int UNR>
+__device__ __forceinline__ void pass_block_incr(const float* __restrict__ Qf, int ld, int row0, int rows,
+                                                const float* __restrict__ xh, const float* __restrict__ xl,
+                                                const float* __restrict__ v,
+                                                const float* __restrict__ uoh, const float* __restrict__ uol,
+                                                const float* __restrict__ crow,
+                                                float* __restrict__ Uoh, float* __restrict__ Uol,
+                                                float* __restrict__ Wo, double* __restrict__ out, int ostride,
+                                                double* smem) {
+  const uint8_t* Qm = reinterpret_cast<const uint8_t*>(Qf);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const size_t rowbytes = (size_t)ld * 4;
+  for (int r = row0 + warp * RPW; r < row0 + rows; r += NWARP * RPW) {
+    const int nr = min(RPW, row0 + rows - r);
+    const uint8_t* p[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) p[q] = Qm + (size_t)(r + (q < nr ? q : 0)) * rowbytes;
+    float aw[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) aw[q] = 0.f;
+    auto consume = [&](const uint4 (&raw)[RPW], int cc) {
+      const float4 d = __ldg(reinterpret_cast<const float4*>(v + cc));
+      const float dv4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float qe[4];
+        Elt<RAPDB_F32>::cvt(raw[q], qe);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) aw[q] = fmaf(qe[e], dv4[e], aw[q]);
+      }
+    };
+    int c0 = lane * 4;
+    for (; c0 + (UNR - 1) * 128 < ld; c0 += UNR * 128) {
+      uint4 raw[UNR][RPW];
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+          raw[uu][q] = (q < nr) ? ld_stream16(p[q] + (size_t)(c0 + uu * 128) * 4) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int uu = 0; uu < UNR; ++uu) consume(raw[uu], c0 + uu * 128);
+    }
+    for (; c0 < ld; c0 += 128) {
+      uint4 raw[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) raw[q] = (q < nr) ? ld_stream16(p[q] + (size_t)c0 * 4) : make_uint4(0, 0, 0, 0);
+      consume(raw, c0);
+    }
+    double ww_[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) ww_[q] = warp_sum((double)aw[q]);
+    if (lane < nr) {
+      const int j = r + lane;
+      double w = ww_[0];
+#pragma unroll
+      for (int q = 1; q < RPW; ++q)
+        if (lane == q) w = ww_[q];
+      const double uo = (double)uoh[j] + (double)uol[j];
+      const double u = uo + w;
+      const float uh = (float)u;
+      Uoh[j] = uh;
+      Uol[j] = (float)(u - (double)uh);
+      Wo[j] = (float)w;
+      const double xj = (double)xh[j] + (double)xl[j], vj = v[j], cj = crow[j];
+      dsum[0] = fma(xj, u, dsum[0]);
+      dsum[1] = fma(vj, w, dsum[1]);
+      dsum[2] = fma(vj, uo, dsum[2]);
       dsum[3] = fma(cj, xj, dsum[3]);
       dsum[4] = fma(cj, vj, dsum[4]);
     }

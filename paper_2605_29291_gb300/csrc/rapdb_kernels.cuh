@@ -154,6 +154,9 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
     if (P.tau_log) P.tau_log[S.it] = tau;
     if (P.trials_log) P.trials_log[S.it] = trials_this;
   }
+  // level 2: the accepted products came from U^k + Q d while anchor_age <
+  // ANCHOR_EVERY, else from a direct compensated product
+  if (S.precision == 2) S.anchor_age = (S.anchor_age < ANCHOR_EVERY) ? S.anchor_age + 1 : 0;
   S.tau_prev = tau;
   S.sigma_prev = sigma;
   S.alpha_k = alpha_next;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const float* Unlo = (phase == PH_KKT32B ? S.check_level == 2 : (S.precision == 2 && phase == PH_XY2))
                           ? I.Ulo[S.ucur ^ 1] : nullptr;
   const float* c = I.c;
+  const double* cdb = I.cd;
   double acc[NVP];
 #pragma unroll
   for (int q = 0; q < NVP; ++q) acc[q] = 0.0;
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         const float* Ul = (phase == PH_KKT32B) ? Unlo : Uclo;
         for (int i = 1 + grp; i <= m; i += NGRP) {
           const double v = (double)Us[(size_t)i * ldv + j] + (Ul ? (double)Ul[(size_t)i * ldv + j] : 0.0) +
-                           (double)c[(size_t)i * ldv + j];
+                           cdb[(size_t)i * ldv + j];
           s0 += ys[i - 1] * v;
           s1 += yts[i - 1] * v;
         }
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         for (int i = 1 + grp; i <= m; i += NGRP) {
           const double dy = yts[i - 1] - ys[i - 1];
           s0 += dy * ((double)Un[(size_t)i * ldv + j] + (Unlo ? (double)Unlo[(size_t)i * ldv + j] : 0.0) +
-                      (double)c[(size_t)i * ldv + j]);
+                      cdb[(size_t)i * ldv + j]);
           s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
         }
       } else if (gap_phase(phase)) {
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         for (int i = 1 + grp; i <= m; i += NGRP) {
           s0 += ys[i - 1] * (double)Un[(size_t)i * ldv + j];
           s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
-          s2 += ys[i - 1] * (double)c[(size_t)i * ldv + j];
+          s2 += ys[i - 1] * cdb[(size_t)i * ldv + j];
         }
       }
     }
@@ -704,6 +708,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
           S.precision = S.check_level;
           S.switches += 1;
           S.ucur ^= 1;
+          S.anchor_age = 0;       // the check pass formed U directly
           restart_scalars(P, S);
           S.restart_note = 1;
         }
@@ -731,6 +736,11 @@ template <int NST, int RPW, int CWB>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
   return NST <= 0 ? 0 : (RPW == 0 ? rows_smem_bytes<CWB, NST>() : tma_bar_bytes<NST>() + (size_t)NWARP * NST * RPW * CWB);
 }
+
+// Rows per warp of the float32 products inside a kernel of storage ST: the
+// float32 refinement copy of a quantised matrix keeps four rows per warp.
+template <int ST, int RPW>
+constexpr int F32_RPW = (ST == RAPDB_F32 || RPW <= 4) ? RPW : 4;
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
 __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, int rows, const float* x,
@@ -807,15 +817,20 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
     const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
     const float* xlo = (phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1];
-    pass_block_prec2<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
-                           uold ? I.Ulo[S.ucur] + (size_t)i * ldv : nullptr, crow, Uo,
-                           I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo, out, I.nrb, red);
+    if (phase == PH_TRIAL && S.anchor_age < ANCHOR_EVERY)   // U' = U^k + Q d
+      pass_block_incr<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
+                            I.Ulo[S.ucur] + (size_t)i * ldv, crow, Uo, I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo,
+                            out, I.nrb, red);
+    else
+      pass_block_prec2<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
+                             uold ? I.Ulo[S.ucur] + (size_t)i * ldv : nullptr, crow, Uo,
+                             I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo, out, I.nrb, red);
   } else if (use32 || ST == RAPDB_F32) {
     const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
-    pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,
-                                             nullptr, nullptr, nullptr, uold, crow, Uo, Wo, out, I.nrb, red, dsm,
-                                             &ctrl->err);
+    pass_tile<RAPDB_F32, F32_RPW<ST, RPW>, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0,
+                                                         rows, x, v, nullptr, nullptr, nullptr, uold, crow, Uo, Wo,
+                                                         out, I.nrb, red, dsm, &ctrl->err);
   } else {
     constexpr int EB = Elt<ST>::B;
     const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;
@@ -928,6 +943,7 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
   }
   S.xcur ^= 1;
   S.ucur ^= 1;
+  S.anchor_age = 0;         // INIT / AVGP form U directly
   S.obj = 0.5 * __ldcg(&D[D_XU]) + __ldcg(&D[D_CX]);
   if (phase == PH_INIT) {
     S.fresh = 1;
@@ -973,9 +989,10 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass_plain(const Ins
   } else if (use32 || ST == RAPDB_F32) {
     const float* Qb = (ST == RAPDB_F32 && !use32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32 && !use32) ? I.ld : I.ld32;
-    pass_tile<RAPDB_F32, RPW, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0, rows, x, v,
-                                             nullptr, nullptr, nullptr, uo, crow, U + (size_t)i * ldv,
-                                             W + (size_t)i * ldv, out, I.nrb, red, dsm, err);
+    pass_tile<RAPDB_F32, F32_RPW<ST, RPW>, UNR, NST, CWB>((const uint8_t*)(Qb + (size_t)s * I.n * ldq), ldq, row0,
+                                                         rows, x, v, nullptr, nullptr, nullptr, uo, crow,
+                                                         U + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb, red,
+                                                         dsm, err);
   } else {
     constexpr int EB = Elt<ST>::B;
     const uint8_t* Qb = (const uint8_t*)I.Q + (size_t)s * I.n * I.ld * EB;

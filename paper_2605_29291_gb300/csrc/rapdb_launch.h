@@ -17,11 +17,14 @@ struct Ctrl;
 //   NST  shared-memory slots (bulk-copy staging; 0 = registers),
 //   CWB  bytes of each row per warp slot, or bytes per CTA stage (RPW = 0).
 //   NST = -1: register streaming with the next batch's loads in flight.
-constexpr int NVAR = 8;
-constexpr int kVarRPW[NVAR] = {4, 4, 4, 0, 0, 0, 4, 4};
-constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0, 0, 2, 4};
-constexpr int kVarNST[NVAR] = {0, 0, 4, 3, 4, 3, -1, -1};
-constexpr int kVarCWB[NVAR] = {0, 0, 512, 32768, 16384, 65536, 0, 0};
+//   RPW = 8 shares each 16-byte slice of x and v between eight rows, which
+//   matters for FP8 (sixteen elements per slice); the float32 products of a
+//   quantised matrix's refinement copy keep four rows per warp.
+constexpr int NVAR = 10;
+constexpr int kVarRPW[NVAR] = {4, 4, 4, 0, 0, 0, 4, 4, 8, 8};
+constexpr int kVarUNR[NVAR] = {2, 4, 0, 0, 0, 0, 2, 4, 2, 1};
+constexpr int kVarNST[NVAR] = {0, 0, 4, 3, 4, 3, -1, -1, 0, 0};
+constexpr int kVarCWB[NVAR] = {0, 0, 512, 32768, 16384, 65536, 0, 0, 0, 0};
 
 // dynamic shared memory of variant vi (8 warps).  Warp stages: mbarrier area
 // rounded up to 128 bytes, then 8 * NST * RPW * CWB bytes of slots.  CTA

@@ -116,7 +116,7 @@ def test_pass_is_deterministic(R, cuda):
     s.close()
 
 
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 @pytest.mark.parametrize("storage", [0, 1, 2])
 @pytest.mark.parametrize("n,m,q0_kind", [(203, 3, W.Q0_DENSE), (1000, 2, W.Q0_DIAG), (37, 1, W.Q0_DENSE)])
 def test_every_tile_variant(R, cuda, variant, storage, n, m, q0_kind):
@@ -146,7 +146,7 @@ def test_every_tile_variant(R, cuda, variant, storage, n, m, q0_kind):
     s.close()
 
 
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 def test_every_tile_variant_solves(R, cuda, variant):
     """The full device loop with each tile variant reaches the oracle's
     objective on a ragged instance."""

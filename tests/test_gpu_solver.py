@@ -213,11 +213,14 @@ def test_quantised_storage_with_refinement(R, cuda, storage):
 
 
 def test_checkpoint_resume_is_bit_identical(R, cuda, c1):
-    full = R.Params.default(max_iter=300, tol=1e-9)
+    # one tile for all three contexts: tiles with different rows per warp
+    # combine the products in different (each fixed) orders
+    tile = dict(rows_per_block=64, pass_variant=0)
+    full = R.Params.default(max_iter=300, tol=1e-9, **tile)
     s_full = R.Solver(c1.to(cuda), full)
     xf, yf = gpu_vecs(c1, cuda)
     i_full = s_full.solve(xf, yf)
-    part = R.Params.default(max_iter=137, tol=1e-9)
+    part = R.Params.default(max_iter=137, tol=1e-9, **tile)
     s_a = R.Solver(c1.to(cuda), part)
     xa, ya = gpu_vecs(c1, cuda)
     ia = s_a.solve(xa, ya)
