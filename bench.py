@@ -32,12 +32,13 @@ METRIC = ("time-to-1e-6 rel KKT & iters/s; coupling-pass HBM GB/s vs 8 TB/s "
           "(plain vs mixed/batched)")
 WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1), c_i N(0,1), "
             "d_i=-U[0.1,1], box [-10,10], FP32 storage (3.42 GB Q stack); rAPDB-yx non-monotone, "
-            "adaptive (smoothed-gap) restart first at k=50 then every 500, precision refinement to "
-            "compensated float32 products, x0=y0=0, stop at rel KKT <= 1e-6")
-# DRAM bytes (read + write) of one coupling-pass launch on this workload: the
-# ncu capture of the same tile on the 11-matrix case (741.9 MB per launch,
-# profiles/coupling_pass_n4096_m10_f32.md) scaled by the 51/11 matrices.
-PASS_DRAM_BYTES = 741.9e6 * 51 / 11
+            "adaptive (smoothed-gap) restart first at k=50 then every 500, refinement on: compensated "
+            "(double-float) products throughout, trial passes incremental, x0=y0=0, stop at rel KKT <= 1e-6")
+# DRAM bytes (read + write) of one incremental trial-pass launch on this
+# workload: the ncu capture of the same kernel on the 11-matrix case (742.1 MB
+# per launch against 738.2 MB algorithmic; profiles/coupling_pass_n4096_m10_f32.md)
+# scaled by the 51/11 matrices.
+PASS_DRAM_BYTES = 742.1e6 * 51 / 11
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 
@@ -308,16 +309,21 @@ def run_ours(args):
 
     # dominant kernel: the coupling pass, timed with CUDA events on the
     # solver's stream (the torch current stream)
-    pass_ms, pass_bytes = s.time_pass(reps=20, level=0)        # plain float32: most passes of a solve
-    comp_ms, _ = s.time_pass(reps=5, level=2)                    # compensated passes of the final phase
+    # float32 storage with refinement runs every trial pass in the incremental
+    # compensated form (level 3: U^k + Q d); a direct compensated pass (level
+    # 2) re-anchors U every 64 iterations
+    pass_ms, pass_bytes = s.time_pass(reps=20, level=3)
+    plain_ms, _ = s.time_pass(reps=10, level=0)
+    comp_ms, _ = s.time_pass(reps=5, level=2)
     pk, pk_kind = peaks()
     achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": PASS_DRAM_BYTES,
                 "peak_kind": f"{pk_kind} copy bandwidth", "frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
-                "kernel": "k_pass<f32> (fused coupling pass)", "bytes_per_launch": pass_bytes,
-                "ms_per_launch": pass_ms, "tile": s.tile(),
-                "compensated_pass_gbs": pass_bytes / (comp_ms * 1e-3) / 1e9}
+                "kernel": "k_pass<f32>, incremental compensated trial pass (U^k + Q d)",
+                "bytes_per_launch": pass_bytes, "ms_per_launch": pass_ms, "tile": s.tile(),
+                "plain_float32_pass_gbs": pass_bytes / (plain_ms * 1e-3) / 1e9,
+                "direct_compensated_pass_gbs": pass_bytes / (comp_ms * 1e-3) / 1e9}
     x64, y64 = s.solution_f64()
 
     # end to end through the C ABI from pinned host buffers (one step: upload,

@@ -180,7 +180,10 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
  * last trial as the second right-hand side), bracketed by two CUDA events on
  * that stream.  level: -1 = the precision the last solve ended at, 0 = the
  * stored Q, 1 = the float32 Q of a BF16/FP8 context, 2 = float32 Q with
- * compensated (double-float) products (contexts created with refine = 1).
+ * compensated (double-float) products (contexts created with refine = 1),
+ * 3 = the incremental form of level 2 that the solver's trial passes use
+ * (U = U^k + Q d: one float32 right-hand side added to the double-float
+ * products at x^k).
  * *ms_per_pass (host) receives the average duration of one launch,
  * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
  * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8).  Outputs

@@ -528,9 +528,16 @@ rapdb_status autotune(rapdb_ctx* ctx) {
     const int grid = ctx->npblk;
     for (int vi = 0; vi < NVAR; ++vi) {
       const Inst& I = ctx->hi[0].I;
+      // time the pass the solver's trials run: float32 storage with
+      // refinement runs the incremental compensated pass (level 3) throughout
+      const bool inc = I.storage == RAPDB_F32 && I.P.refine && I.Ulo[0] != nullptr;
       auto go = [&]() {
-        launch_plain(I.storage, vi, dim3(grid), st, ctx->d_inst, I.xf[0], I.dv, ctx->XS, ctx->VS, nullptr, ctx->tU,
-                     ctx->tW, ctx->tpart, 0, &ctx->d_ctrl->err);
+        if (inc)
+          launch_plain(I.storage, vi, dim3(grid), st, ctx->d_inst, I.xf[0], I.dv, ctx->XS, ctx->VS, I.U[0], ctx->tU,
+                       ctx->tW, ctx->tpart, 3, &ctx->d_ctrl->err, I.xl[0], ctx->tUo);
+        else
+          launch_plain(I.storage, vi, dim3(grid), st, ctx->d_inst, I.xf[0], I.dv, ctx->XS, ctx->VS, nullptr, ctx->tU,
+                       ctx->tW, ctx->tpart, 0, &ctx->d_ctrl->err);
       };
       go();
       CK(cudaGetLastError());
@@ -876,7 +883,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     cur_level = ctx->h_state[0].precision;
   }
   const int lv = level < 0 ? cur_level : level;
-  if (lv > 2 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv == 2 && !I.Ulo[0]) ||
+  if (lv > 3 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
       (lv == 1 && I.storage == RAPDB_F32))
     return fail(ctx, RAPDB_ERR_INVALID, "precision level not available in this context");
   const float* x = I.xf[xcur];
@@ -885,7 +892,8 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
-    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS, lv == 2 ? nullptr : I.U[0],
+    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS,
+                 lv == 2 ? nullptr : I.U[0],
                  ctx->tU, ctx->tW, ctx->tpart, lv, &ctx->d_ctrl->err, I.xl[xcur], ctx->tUo);
   };
   launch();   // warm-up

@@ -144,6 +144,7 @@ struct State {
   int check_level;      // precision level of the pending accurate KKT check (KKT32 / KKT32B)
   unsigned int arrive_vec, arrive_pass;
   int anchor_age;       // level 2: accepted iterations since U was last formed by a direct product
+  int check_due;        // a precision check runs at the next iteration's KKT test
 };
 
 struct Ctrl {

@@ -90,8 +90,13 @@ static __device__ void restart_scalars(const DevParams& P, State& S) {
 __device__ __forceinline__ bool can_refine(const Inst& I, const State& S) {
   return I.P.refine && S.precision < 2 && (I.storage == RAPDB_F32 || I.Q32 != nullptr);
 }
+// The next level is always the compensated one: its trial products are
+// incremental (U^k + Q d, one float32 right-hand side), so they cost what a
+// plain float32 pass costs, and float32 products alone leave a KKT floor.
 __device__ __forceinline__ int next_level(const Inst& I, const State& S) {
-  return (I.storage == RAPDB_F32 || S.precision >= 1) ? 2 : 1;
+  (void)I;
+  (void)S;
+  return 2;
 }
 __device__ __forceinline__ void start_check(const Inst& I, State& S) {
   S.check_level = next_level(I, S);
@@ -180,12 +185,11 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
     } else {
       restart_scalars(P, S);
       S.restart_note = 1;
-      if (can_refine(I, S)) start_check(I, S);
+      if (can_refine(I, S)) S.check_due = 1;
     }
-  } else if (P.restart != RAPDB_RESTART_FIXED && P.restart_period > 0 && S.it % P.restart_period == 0 &&
-             can_refine(I, S)) {
-    // without fixed restarts the precision check runs every restart_period iterations
-    start_check(I, S);
+  } else if (can_refine(I, S) && P.restart_period > 0 && S.it % max(1, P.restart_period / 4) == 0) {
+    // the precision check also runs every restart_period / 4 iterations
+    S.check_due = 1;
   }
 }
 
@@ -520,7 +524,13 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       if (!(rel == rel)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
       if (can_refine(I, S)) {
         S.rel_q = rel;
-        if (rel <= P.tol) { start_check(I, S); return; }
+        // the check runs at this x^k, after the stored level's residual at
+        // the same point (rel_q) has been formed
+        if (rel <= P.tol || S.check_due) {
+          S.check_due = 0;
+          start_check(I, S);
+          return;
+        }
       } else if (rel <= P.tol) {
         finish(S, ctrl, RAPDB_OK);
         return;
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       S.restarts += 1;
       if (can_refine(I, S)) {
         S.fresh = 1;
-        start_check(I, S);
+        S.check_due = 1;
       }
     }
     return;
@@ -689,7 +699,10 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       } else {
         const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
         S.kkt_ref = rel;
-        if (stalled || S.rel_q <= P.tol) dec = 1;
+        // switch when the true residual stalls, when the stored matrices'
+        // problem is solved, or when the storage error already dominates
+        // (the true residual is more than twice the stored level's)
+        if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) dec = 1;
       }
       s_dec = dec;
     }
@@ -705,12 +718,13 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         finish(S, ctrl, RAPDB_OK);
       } else {
         if (dec == 1) {
+          // the products' precision changes, the iteration's state does not:
+          // step sizes, momentum and the counter carry on from x^k (a check
+          // at a restart boundary follows the restart that happened there)
           S.precision = S.check_level;
           S.switches += 1;
           S.ucur ^= 1;
           S.anchor_age = 0;       // the check pass formed U directly
-          restart_scalars(P, S);
-          S.restart_note = 1;
         }
         S.fresh = 1;
         S.phase = PH_TRIAL;
@@ -741,6 +755,12 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
 // float32 refinement copy of a quantised matrix keeps four rows per warp.
 template <int ST, int RPW>
 constexpr int F32_RPW = (ST == RAPDB_F32 || RPW <= 4) ? RPW : 4;
+// Rows per warp and chunks in flight of the incremental compensated pass
+// (register streaming): the tile's own where it streams through registers.
+template <int ST, int RPW>
+constexpr int INC_RPW = (RPW == 0) ? 4 : F32_RPW<ST, RPW>;
+template <int UNR>
+constexpr int INC_UNR = (UNR == 0) ? 2 : UNR;
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
 __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, int rows, const float* x,
@@ -818,9 +838,9 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
     const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
     const float* xlo = (phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1];
     if (phase == PH_TRIAL && S.anchor_age < ANCHOR_EVERY)   // U' = U^k + Q d
-      pass_block_incr<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
-                            I.Ulo[S.ucur] + (size_t)i * ldv, crow, Uo, I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo,
-                            out, I.nrb, red);
+      pass_block_incr<INC_RPW<ST, RPW>, INC_UNR<UNR>>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
+                                                     I.Ulo[S.ucur] + (size_t)i * ldv, crow, Uo,
+                                                     I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo, out, I.nrb, red);
     else
       pass_block_prec2<4, 2>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
                              uold ? I.Ulo[S.ucur] + (size_t)i * ldv : nullptr, crow, Uo,
@@ -980,7 +1000,15 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass_plain(const Ins
   const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
   const float* crow = I.c + (size_t)i * ldv;
   const int use32 = (ST != RAPDB_F32 && level >= 1) ? 1 : 0;
-  if (level == 2) {
+  if (level == 3) {
+    // the incremental form of level 2: U = uold + Q v with uold + Ulo_cur the
+    // double-float products at the current iterate
+    const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
+    pass_block_incr<INC_RPW<ST, RPW>, INC_UNR<UNR>>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uo,
+                                                   I.Ulo[0] + (size_t)i * ldv, crow, U + (size_t)i * ldv,
+                                                   Ulo + (size_t)i * ldv, W + (size_t)i * ldv, out, I.nrb, red);
+  } else if (level == 2) {
     const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
     // compensated products of x = x + xlo; the low parts of U go to Ulo

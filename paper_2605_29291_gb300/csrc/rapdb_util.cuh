@@ -112,6 +112,8 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   restart_scalars(I.P, S);
   S.sigma0 = S.sigma_prev;
   S.phase = PH_INIT;
+  // float32 storage with refinement runs the compensated level from the start
+  if (I.P.refine && I.storage == RAPDB_F32 && I.Ulo[0]) S.precision = 2;
   S.rel_kkt = S.r_stat = S.r_feas = NAN;
   S.rel_q = INFINITY;
   S.gap_it_done = -1;
