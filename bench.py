@@ -35,10 +35,10 @@ WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1),
             "adaptive (smoothed-gap) restart first at k=50 then every 500, refinement on: compensated "
             "(double-float) products throughout, trial passes incremental, x0=y0=0, stop at rel KKT <= 1e-6")
 # DRAM bytes (read + write) of one incremental trial-pass launch on this
-# workload: the ncu capture of the same kernel on the 11-matrix case (742.1 MB
-# per launch against 738.2 MB algorithmic; profiles/coupling_pass_n4096_m10_f32.md)
-# scaled by the 51/11 matrices.
-PASS_DRAM_BYTES = 742.1e6 * 51 / 11
+# workload: the ncu capture of the same kernel and tile on the 11-matrix case
+# (742.3 MB per launch against 738.2 MB algorithmic;
+# profiles/coupling_pass_n4096_m10_f32.md) scaled by the 51/11 matrices.
+PASS_DRAM_BYTES = 742.3e6 * 51 / 11
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 
