@@ -31,6 +31,7 @@ struct InstHost {
 struct rapdb_ctx {
   int B = 1;
   bool batched = false;
+  int mapped = 0;              // instances that have CTAs in the current block maps
   rapdb_params p{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;  // private stream used for graph capture
@@ -383,6 +384,7 @@ rapdb_status finalize_ctx(rapdb_ctx* ctx) {
   }
   ctx->nvblk = (int)vmap.size();
   ctx->npblk = (int)pmap.size();
+  ctx->mapped = B;
   ctx->smem_vec = (size_t)2 * mmax * sizeof(double);
   if (ctx->smem_vec > 200 * 1024) return fail(ctx, RAPDB_ERR_INVALID, "too many constraints (m > 12800)");
   AL(ctx->d_vmap, vmap.size());
@@ -459,6 +461,38 @@ rapdb_status build_graph(rapdb_ctx* ctx, int bodies) {
   return RAPDB_OK;
 }
 
+// Block maps over the instances still running (a batched context drops the
+// finished ones, so that their CTAs are no longer launched only to exit);
+// `run[b]` selects instance b.  Rebuilds the loop graph for the new grids.
+// The caller has synchronised the stream.
+rapdb_status set_block_maps(rapdb_ctx* ctx, const std::vector<char>& run) {
+  cudaStream_t st = ctx->stream;
+  std::vector<int> vmap, pmap;
+  int nact = 0;
+  for (int b = 0; b < ctx->B; ++b) {
+    if (!run[b]) continue;
+    Inst& I = ctx->hi[b].I;
+    ++nact;
+    I.vblk0 = (int)vmap.size();
+    for (int k = 0; k < I.ncb; ++k) vmap.push_back(b);
+    I.pblk0 = (int)pmap.size();
+    for (int k = 0; k < I.M * I.nrb; ++k) pmap.push_back(b);
+  }
+  if (!vmap.empty())
+    CK(cudaMemcpyAsync(ctx->d_vmap, vmap.data(), vmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!pmap.empty())
+    CK(cudaMemcpyAsync(ctx->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<Inst> tmp(ctx->B);
+  for (int b = 0; b < ctx->B; ++b) tmp[b] = ctx->hi[b].I;
+  CK(cudaMemcpyAsync(ctx->d_inst, tmp.data(), ctx->B * sizeof(Inst), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->nvblk = (int)vmap.size();
+  ctx->npblk = (int)pmap.size();
+  ctx->mapped = nact;
+  if (ctx->p.use_graph && nact > 0) return build_graph(ctx, 32);
+  return RAPDB_OK;
+}
+
 // Run the device loop until every instance is done.  The host never waits
 // per trial: it keeps two graph launches (each `g_bodies` bodies) in flight
 // and reads the 'active' counter of the older one.
@@ -488,7 +522,20 @@ rapdb_status run_loop(rapdb_ctx* ctx, int64_t max_bodies) {
       const int old = slot ^ 1;
       CK(cudaEventSynchronize(ctx->ev[old]));
       pending = 1;
-      if (ctx->h_ctrl[old].active <= 0) done = true;
+      const int act = ctx->h_ctrl[old].active;
+      if (act <= 0) {
+        done = true;
+      } else if (ctx->batched && 2 * act <= ctx->mapped && ctx->npblk > 4 * 152) {
+        // half of the mapped instances have finished: launch CTAs for the
+        // running ones only (each instance's arithmetic is unchanged)
+        CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpy(ctx->h_state, ctx->d_state, sizeof(State) * ctx->B, cudaMemcpyDeviceToHost));
+        std::vector<char> run(ctx->B);
+        for (int b = 0; b < ctx->B; ++b) run[b] = ctx->h_state[b].phase != PH_DONE;
+        rapdb_status s = set_block_maps(ctx, run);
+        if (s != RAPDB_OK) return s;
+        pending = 0;
+      }
     }
     slot ^= 1;
   }
@@ -736,6 +783,12 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
     CK(cudaStreamSynchronize(st));
     if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "x0 outside the box");
     if (flags[1]) return fail(ctx, RAPDB_ERR_INVALID, "y0 has a negative (or NaN) entry");
+  }
+  if (ctx->batched && ctx->mapped != B) {
+    // a previous solve dropped finished instances from the block maps
+    CK(cudaStreamSynchronize(st));
+    rapdb_status s = set_block_maps(ctx, std::vector<char>(B, 1));
+    if (s != RAPDB_OK) return s;
   }
   Ctrl c0{};
   c0.active = B;

@@ -25,13 +25,15 @@ pytestmark = pytest.mark.gpu
 N_SAMPLE = 40
 
 
-def bench_params(R, **kw):
+def bench_params(R, variant=None, **kw):
     """The benchmark's solver parameters: yx, non-monotone steps, adaptive
-    restart (first gap evaluation at k = 50, then every 500), refinement on."""
-    base = dict(c_nm=1, restart=R.RESTART_GAP, gap_first=50, gap_every=500, restart_period=200, tol=1e-6,
-                max_iter=50000, time_limit_s=300.0, refine=1)
+    restart (first gap evaluation at k = 50, then every 500), refinement on.
+    The xy variant takes its own defaults (first gap evaluation at k = 100)."""
+    variant = R.YX if variant is None else variant
+    base = dict(c_nm=1, restart=R.RESTART_GAP, gap_first=50 if variant == R.YX else 100, gap_every=500,
+                restart_period=200, tol=1e-6, max_iter=50000, time_limit_s=300.0, refine=1)
     base.update(kw)
-    return R.Params.default(R.YX, **base)
+    return R.Params.default(variant, **base)
 
 
 def sample_rows(n, seed):
@@ -164,6 +166,25 @@ def test_dense_4096x50_solve_meets_tolerance_in_the_oracle_kkt(R, cuda, c2):
     assert abs(info["obj"] - prob.f(x64)) <= 1e-6 * (1 + abs(prob.f(x64)))
 
 
+@pytest.mark.parametrize("variant,storage", [(0, 1), (0, 2), (1, 0)])
+def test_dense_4096x50_other_forms_meet_tolerance(R, cuda, c2, variant, storage):
+    """BF16 and FP8 storage with refinement (yx), and the xy variant with
+    float32 storage, on the full workload: each ends at rel KKT 1e-6 by its
+    own test, confirmed by the oracle's float64 residual at its iterate."""
+    s = R.Solver(c2, bench_params(R, storage=storage, variant=variant))
+    x = torch.zeros(c2.n, device=cuda)
+    y = torch.zeros(c2.m, device=cuda)
+    info = s.solve(x, y)
+    x64, y64 = s.solution_f64()
+    s.close()
+    assert info["status"] == R.OK and info["rel_kkt"] <= 1e-6, info
+    if storage != 0:
+        assert info["precision_switches"] == 1, info
+    prob = oracle_problem(c2)
+    rel, _, _ = O.kkt_residual(prob, x64.cpu().numpy(), y64.cpu().numpy())
+    assert rel <= 1e-6, rel
+
+
 # ---------------------------------------------------------------------------
 # Kernel-learning epigraph QCQP, n = 5000 samples, m = 8 kernels, bfloat16
 # ---------------------------------------------------------------------------
@@ -234,6 +255,20 @@ def test_batched_256_sampled_instances(R, cuda):
         assert np.all(xb >= prob.lb) and np.all(xb <= prob.ub) and np.all(yb >= 0)
         rel, _, _ = O.kkt_residual(prob, xb, yb)
         assert rel <= 1e-5, (b, datas[b].n, datas[b].m, rel)
+    # the batched loop drops finished instances from its launch grids as they
+    # finish; each instance's arithmetic is unchanged, so a single-instance
+    # context with the batched tile (64 rows, pipelined register streaming)
+    # ends on the same bits
+    for b in (order[0], order[len(order) // 2], order[-1]):
+        ps = R.Params.default(R.YX, tol=1e-6, max_iter=20000, time_limit_s=120.0, refine=1, rows_per_block=64,
+                              pass_variant=6)
+        s1 = R.Solver(devs[b], ps)
+        x1 = torch.zeros(datas[b].n, device=cuda)
+        y1 = torch.zeros(max(datas[b].m, 1), device=cuda)
+        i1 = s1.solve(x1, y1)
+        s1.close()
+        assert i1["iters"] == infos[b]["iters"], (b, i1["iters"], infos[b]["iters"])
+        assert torch.equal(x1, xs[b]) and torch.equal(y1, ys[b]), b
     del devs
     torch.cuda.empty_cache()
 
