@@ -199,11 +199,16 @@ rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, int32_t level, double
  * residual measured at iterate k (kkt_log: capacity doubles; entries of
  * iterations where it was not evaluated are left untouched) and, with the
  * adaptive restart, the smoothed gap G_xi of each evaluation in order
- * (gap_log: capacity doubles).  capacity = 0 switches logging off.  The
- * buffers are borrowed. */
+ * (gap_log: capacity doubles); obj_log and infeas_log (capacity doubles
+ * each, optional) receive f(x^{k+1}) and mean_i max(g_i(x^{k+1}), 0) of each
+ * accepted iteration k, the two terms of the paper's termination measure for
+ * random QCQPs (Sec. 5.1).  capacity = 0 switches logging off.  The buffers
+ * are borrowed.  Single-instance contexts only (RAPDB_ERR_INVALID on a
+ * batched context). */
 rapdb_status rapdb_set_log(rapdb_ctx *ctx, int32_t capacity, double *tau_log,
                            int32_t *trials_log, float *x_log, float *y_log,
-                           double *kkt_log, double *gap_log);
+                           double *kkt_log, double *gap_log, double *obj_log,
+                           double *infeas_log);
 
 /* Batched contexts: B independent problems with their own n_b, m_b, solved
  * together in one device loop with per-instance step sizes, restart counters

@@ -76,6 +76,8 @@ struct rapdb_ctx {
   double* tau_log = nullptr;
   double* kkt_log = nullptr;
   double* gap_log = nullptr;
+  double* obj_log = nullptr;
+  double* infeas_log = nullptr;
   int* trials_log = nullptr;
   float* x_log = nullptr;
   float* y_log = nullptr;
@@ -180,6 +182,8 @@ DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
   d.tau_log = ctx->tau_log;
   d.kkt_log = ctx->kkt_log;
   d.gap_log = ctx->gap_log;
+  d.obj_log = ctx->obj_log;
+  d.infeas_log = ctx->infeas_log;
   d.trials_log = ctx->trials_log;
   d.x_log = ctx->x_log;
   d.y_log = ctx->y_log;
@@ -983,9 +987,11 @@ rapdb_status rapdb_get_solution_f64(rapdb_ctx* ctx, double* x, double* y) {
 }
 
 rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, int32_t* trials_log, float* x_log,
-                           float* y_log, double* kkt_log, double* gap_log) {
+                           float* y_log, double* kkt_log, double* gap_log, double* obj_log, double* infeas_log) {
   if (!ctx) return fail(nullptr, RAPDB_ERR_INVALID, "ctx is NULL");
   if (capacity < 0) return fail(ctx, RAPDB_ERR_INVALID, "capacity < 0");
+  if (capacity > 0 && ctx->batched)
+    return fail(ctx, RAPDB_ERR_INVALID, "logging needs a single-instance context");
   ctx->log_cap = capacity;
   ctx->tau_log = capacity ? tau_log : nullptr;
   ctx->trials_log = capacity ? trials_log : nullptr;
@@ -993,6 +999,8 @@ rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, in
   ctx->y_log = capacity ? y_log : nullptr;
   ctx->kkt_log = capacity ? kkt_log : nullptr;
   ctx->gap_log = capacity ? gap_log : nullptr;
+  ctx->obj_log = capacity ? obj_log : nullptr;
+  ctx->infeas_log = capacity ? infeas_log : nullptr;
   return upload_params(ctx);
 }
 

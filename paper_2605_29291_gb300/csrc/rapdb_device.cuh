@@ -72,6 +72,8 @@ struct DevParams {
   int* trials_log;
   float* x_log;
   float* y_log;
+  double* obj_log;      // f(x^{k+1}) of each accepted iteration k
+  double* infeas_log;   // mean_i max(g_i(x^{k+1}), 0) of each accepted iteration k
 };
 
 // Immutable description of one instance (device memory).

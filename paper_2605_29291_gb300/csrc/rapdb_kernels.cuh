@@ -178,6 +178,14 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
   S.trial = 0;
   S.fresh = 1;
   S.obj = 0.5 * __ldcg(&I.dots[D_XU]) + __ldcg(&I.dots[D_CX]);
+  if (S.it - 1 < P.log_cap) {
+    if (P.obj_log) P.obj_log[S.it - 1] = S.obj;
+    if (P.infeas_log) {
+      double v = 0.0;
+      for (int i = 0; i < I.m; ++i) v += fmax(__ldcg(&I.gnew[i]), 0.0);
+      P.infeas_log[S.it - 1] = I.m > 0 ? v / I.m : 0.0;
+    }
+  }
   S.phase = PH_TRIAL;
   if (P.restart == RAPDB_RESTART_FIXED && S.k == P.restart_period) {
     if (P.restart_from_average) {

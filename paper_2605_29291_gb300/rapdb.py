@@ -58,7 +58,7 @@ def _load():
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
         "rapdb_coupling_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
-        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp, vp]),
+        "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "rapdb_create_batched": (C.c_int, [ctxpp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                            C.POINTER(vp), P, vp]),
@@ -227,11 +227,13 @@ class Solver:
         return U, W, dots
 
     def set_log(self, capacity: int, iterates: bool = True):
-        """Record tau_k, trials and (optionally) the first `capacity` iterates."""
+        """Record tau_k, trials, KKT residuals, smoothed gaps, f(x^{k+1}) and
+        the mean constraint violation of the first `capacity` iterations, and
+        (optionally) the iterates."""
         import torch
         dev = self.device
         if capacity <= 0:
-            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None, None, None), self.ctx)
+            _check(lib.rapdb_set_log(self.ctx, 0, None, None, None, None, None, None, None, None), self.ctx)
             self._log = None
             return
         tau = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
@@ -241,9 +243,11 @@ class Solver:
               if iterates else None)
         kk = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
         gp = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
-        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl), _ptr(kk), _ptr(gp)),
-               self.ctx)
-        self._log = dict(tau=tau, trials=tr, x=xl, y=yl, kkt=kk, gap=gp)
+        ob = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
+        inf = torch.full((capacity,), float("nan"), dtype=torch.float64, device=dev)
+        _check(lib.rapdb_set_log(self.ctx, capacity, _ptr(tau), _ptr(tr), _ptr(xl), _ptr(yl), _ptr(kk), _ptr(gp),
+                                 _ptr(ob), _ptr(inf)), self.ctx)
+        self._log = dict(tau=tau, trials=tr, x=xl, y=yl, kkt=kk, gap=gp, obj=ob, infeas=inf)
 
     @property
     def log(self):

@@ -169,6 +169,34 @@ def test_ragged_sizes_match_oracle(R, cuda, n, m):
     s.close()
 
 
+def test_objective_and_infeasibility_logs(R, cuda):
+    """The logged f(x^{k+1}) and mean_i max(g_i(x^{k+1}), 0) -- the paper's
+    termination measure for random QCQPs -- equal the oracle's f and g at the
+    logged iterates (float32 copies of the float64 iterates, hence the
+    tolerance scaled by |x| |grad|)."""
+    data = W.paper_random_qcqp(200, 5, seed=3)
+    p = R.Params.default(R.YX, tol=1e-12, max_iter=60, restart=R.RESTART_FIXED, restart_period=400)
+    s = R.Solver(data.to(cuda), p)
+    s.set_log(60)
+    x, y = gpu_vecs(data, cuda)
+    info = s.solve(x, y, check=False)
+    assert info["iters"] == 60
+    xl = s.log["x"].cpu().numpy().astype(np.float64)
+    ob = s.log["obj"].cpu().numpy()
+    inf = s.log["infeas"].cpu().numpy()
+    s.close()
+    prob = O.Problem.from_data(data)
+    for e in range(60):
+        xe = xl[e]
+        g = prob.g(xe)
+        f = prob.f(xe)
+        sc_f = 1.0 + np.linalg.norm(xe) * (np.linalg.norm(prob.Q[0] @ xe) + np.linalg.norm(prob.c[0]))
+        assert abs(ob[e] - f) <= 1e-6 * sc_f, (e, ob[e], f)
+        sc_g = 1.0 + max(np.linalg.norm(xe) * (np.linalg.norm(prob.Q[i] @ xe) + np.linalg.norm(prob.c[i]))
+                         for i in range(1, prob.m + 1))
+        assert abs(inf[e] - np.mean(np.maximum(g, 0.0))) <= 1e-6 * sc_g, e
+
+
 def test_kml_diag_q0_matches_oracle(R, cuda):
     data = W.kml_qcqp(120, 5, 8, seed=2)
     p = R.Params.default(tol=1e-6, restart_period=200)
