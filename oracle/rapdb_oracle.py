@@ -25,8 +25,14 @@ Sources (arXiv 2605.29291):
   * KKT residual: the residual r(x, v, lambda) of Thm. (metric
     subregularity sufficient conditions) with the map G(z) of its proof; the
     normalisation into a relative residual is a reading (the paper is silent).
+  * Dual on a simplex (the kernel-learning min-max problem of Sec. 5.2, eq.
+    min-max-KML: y in {y >= 0, sum y = r}): the projection onto the simplex
+    by the sort-and-threshold method of Held, Wolfe and Crowder (1974), the
+    simplex normal cone in the KKT residual, and the simplex projection in
+    the y-part of G_xi.
 
-Parity pins (see tests/test_oracle_pins.py): closed forms (ball constraint,
+Parity pins (see tests/test_oracle_pins.py, tests/test_oracle_simplex_pins.py):
+closed forms (ball constraint,
 interior PD QP, one-step iterate), weak-duality certificates from an exact box
 QP by exhaustive active-set enumeration, the ergodic bounds (Lemmas with eqs.
 4.16apd / 3.3apd) at random points, step-size invariants (monotone identity of
@@ -99,10 +105,53 @@ class BacktrackError(RuntimeError):
 # ---------------------------------------------------------------------------
 
 
-class Problem:
-    """Float64 copy of the canonical float32 data.  Q[0] is Q_0."""
+def proj_simplex(v, r: float = 1.0):
+    """Euclidean projection of v onto {y >= 0, sum y = r} (Held, Wolfe and
+    Crowder, 1974): sort v in decreasing order, take the largest k with
+    u_k > (sum_{j<=k} u_j - r) / k, then y = max(v - theta, 0) with theta =
+    (sum_{j<=k} u_j - r) / k."""
+    v = np.asarray(v, np.float64)
+    u = np.sort(v)[::-1]
+    css = np.cumsum(u) - r
+    k = np.arange(1, v.size + 1)
+    rho = int(np.nonzero(u - css / k > 0)[0][-1]) + 1
+    theta = css[rho - 1] / rho
+    return np.maximum(v - theta, 0.0)
 
-    def __init__(self, Q, c, d, lb, ub):
+
+def simplex_cone_distance(g, lam):
+    """dist(g, N_Delta(lam)) for the simplex Delta = {y >= 0, sum y = r}:
+    N_Delta(lam) = {t 1 - nu : nu >= 0, nu_i = 0 where lam_i > 0}, so the
+    distance is min over t of sqrt(sum_{lam_i>0} (g_i - t)^2 +
+    sum_{lam_i=0} max(g_i - t, 0)^2).  The function of t is convex and
+    piecewise quadratic with breakpoints at the off-support g_i; on each
+    piece its minimiser is the mean of g over the support and the off-support
+    entries above the piece.  Returns (distance, the minimising t)."""
+    g = np.asarray(g, np.float64)
+    on = np.asarray(lam, np.float64) > 0.0
+    off = np.sort(g[~on])
+    best = (math.inf, 0.0)
+    # pieces: t in (-inf, off_0], (off_0, off_1], ..., (off_last, +inf)
+    edges = [-math.inf] + list(off) + [math.inf]
+    for p in range(len(edges) - 1):
+        lo, hi = edges[p], edges[p + 1]
+        active = np.concatenate([g[on], off[p:]])     # off-support entries above the piece
+        if active.size == 0:
+            continue
+        t = min(max(float(np.mean(active)), lo), hi)      # the piece's minimiser
+        val = float(np.sum((g[on] - t) ** 2) + np.sum(np.maximum(g[~on] - t, 0.0) ** 2))
+        if val < best[0]:
+            best = (val, t)
+    return math.sqrt(best[0]), best[1]
+
+
+class Problem:
+    """Float64 copy of the canonical float32 data.  Q[0] is Q_0.  With
+    dual_radius set, the dual set is the simplex {y >= 0, sum y = dual_radius}
+    instead of the nonnegative orthant."""
+
+    def __init__(self, Q, c, d, lb, ub, dual_radius=None):
+        self.dual_radius = None if dual_radius is None else float(dual_radius)
         self.Q = np.asarray(Q, dtype=np.float64)
         self.c = np.asarray(c, dtype=np.float64)
         self.r = np.asarray(d, dtype=np.float64)
@@ -113,9 +162,11 @@ class Problem:
         assert self.c.shape == (self.m + 1, self.n) and self.r.shape == (self.m,)
 
     @classmethod
-    def from_data(cls, data) -> "Problem":
+    def from_data(cls, data, dual_radius=None) -> "Problem":
         h = data.numpy()
-        return cls(data.dense_q(), h.c, h.d, h.lb, h.ub)
+        if dual_radius is None:
+            dual_radius = (data.meta or {}).get("dual_radius")
+        return cls(data.dense_q(), h.c, h.d, h.lb, h.ub, dual_radius)
 
     # objective and constraints --------------------------------------------
     def f(self, x):
@@ -149,9 +200,16 @@ class Problem:
     def proj_x(self, x):
         return np.minimum(np.maximum(x, self.lb), self.ub)
 
-    @staticmethod
-    def proj_y(lam):
+    def proj_y(self, lam):
+        if self.dual_radius is not None:
+            return proj_simplex(lam, self.dual_radius)
         return np.maximum(lam, 0.0)
+
+    def default_lam0(self):
+        """A dual start in Y: 0, or the simplex's centre."""
+        if self.dual_radius is not None:
+            return np.full(self.m, self.dual_radius / max(self.m, 1))
+        return np.zeros(self.m)
 
 
 def Dp(x, xk):
@@ -313,6 +371,7 @@ def kkt_residual(prob: Problem, x, lam):
 
       r_stat_j = dist(0, grad_x Phi(x, lam)_j + N_X(x)_j)   (box normal cone),
       r_feas_i = dist(0, -g_i(x) + N_{R+}(lam_i)),
+                 (simplex dual: ||r_feas|| = dist(g(x), N_Delta(lam))),
       rel_kkt = max(||r_stat|| / (1 + max(||Q_0x+q_0||, ||sum lam_i(Q_ix+q_i)||)),
                     ||r_feas|| / (1 + max(||r||, ||(g_i(x) - r_i)_i||))).
     """
@@ -326,9 +385,12 @@ def kkt_residual(prob: Problem, x, lam):
     rs = np.where(x <= prob.lb, np.maximum(-grad, 0.0),
                   np.where(x >= prob.ub, np.maximum(grad, 0.0), np.abs(grad)))
     g = prob.g(x)
-    rf = np.where(lam > 0.0, np.abs(g), np.maximum(g, 0.0))
     r_stat = float(np.linalg.norm(rs))
-    r_feas = float(np.linalg.norm(rf))
+    if prob.dual_radius is not None:
+        r_feas = simplex_cone_distance(g, lam)[0]      # dist(0, -g + N_Delta(lam))
+    else:
+        rf = np.where(lam > 0.0, np.abs(g), np.maximum(g, 0.0))
+        r_feas = float(np.linalg.norm(rf))
     den_s = 1.0 + max(float(np.linalg.norm(gf)), float(np.linalg.norm(gc)))
     den_f = 1.0 + max(float(np.linalg.norm(prob.r)), float(np.linalg.norm(g - prob.r)))
     return max(r_stat / den_s, r_feas / den_f), r_stat, r_feas
@@ -365,7 +427,8 @@ def smoothed_gap(prob: Problem, x, lam, xi):
     """Self-centred smoothed gap G_xi(z) =
     [max_{lam' >= 0} Phi(x, lam') - xi||lam' - lam||^2]
       - [min_{x' in X} Phi(x', lam) + xi||x' - x||^2].
-    The y-part is separable: lam' = max(0, lam + g(x) / (2 xi))."""
+    The y-part is a projection: lam' = proj_Y(lam + g(x) / (2 xi)) (max(0, .)
+    for the orthant, the simplex projection for a simplex dual)."""
     x = np.asarray(x, np.float64)
     lam = np.asarray(lam, np.float64)
     g = prob.g(x)
@@ -414,7 +477,7 @@ def rapdb(prob: Problem, x0=None, lam0=None, p: Params | None = None, keep_itera
     """
     p = p or default_params()
     x0 = np.zeros(prob.n) if x0 is None else np.asarray(x0, np.float64)
-    lam0 = np.zeros(prob.m) if lam0 is None else np.asarray(lam0, np.float64)
+    lam0 = prob.default_lam0() if lam0 is None else np.asarray(lam0, np.float64)
     st = start_routine(prob, x0, lam0, p)
     log: dict = {}
     it = trials = restarts = 0

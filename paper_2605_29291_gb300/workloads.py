@@ -174,8 +174,11 @@ def kml_features(n: int, dfeat: int, seed: int):
 
 
 def kml_kernel_specs(m: int) -> list:
-    """Kernel list: the 8-kernel set (RBF 0.1,0.5,1,2,5; poly 2,3; linear) for
-    m=8, otherwise m-4 log-spaced RBF widths in [0.05, 10], poly 2..4, linear."""
+    """Kernel list: the paper's three kernels (poly 2, RBF 0.1, linear) for
+    m=3, the 8-kernel set (RBF 0.1,0.5,1,2,5; poly 2,3; linear) for m=8,
+    otherwise m-4 log-spaced RBF widths in [0.05, 10], poly 2..4, linear."""
+    if m == 3:
+        return [("poly", 2), ("rbf", 0.1), ("linear", None)]
     if m == 8:
         return [("rbf", w) for w in (0.1, 0.5, 1.0, 2.0, 5.0)] + \
                [("poly", 2), ("poly", 3), ("linear", None)]
@@ -183,6 +186,25 @@ def kml_kernel_specs(m: int) -> list:
     widths = np.exp(np.linspace(math.log(0.05), math.log(10.0), nr)) if nr > 1 else [1.0]
     return [("rbf", float(w)) for w in widths] + [("poly", 2), ("poly", 3), ("poly", 4),
                                                  ("linear", None)]
+
+
+def _kml_h(A, B, kind, par, use_torch):
+    """H(K) = diag(b) K diag(b) of one kernel, K normalised to a unit
+    diagonal (float64)."""
+    ip = A @ A.T
+    if kind == "rbf":
+        sq = (A * A).sum(1)
+        dist2 = sq[:, None] + sq[None, :] - 2.0 * ip
+        dist2 = dist2.clamp(min=0.0) if use_torch else np.maximum(dist2, 0.0)
+        K = (-0.5 * dist2 / par).exp() if use_torch else np.exp(-0.5 * dist2 / par)
+    elif kind == "poly":
+        K = (1.0 + ip) ** par
+    else:
+        K = ip
+    dg = K.diagonal().clone() if use_torch else K.diagonal().copy()
+    dg = dg.clamp(min=1e-300) if use_torch else np.maximum(dg, 1e-300)
+    s = dg.rsqrt() if use_torch else 1.0 / np.sqrt(dg)
+    return K * (s * B)[:, None] * (s * B)[None, :]
 
 
 def kml_qcqp(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0,
@@ -209,27 +231,14 @@ def kml_qcqp(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0,
         Q = np.zeros((m, N, N), np.float32)
     smax = 0.0
     for i, (kind, par) in enumerate(specs):
-        ip = A @ A.T
-        if kind == "rbf":
-            sq = (A * A).sum(1)
-            dist2 = sq[:, None] + sq[None, :] - 2.0 * ip
-            dist2 = dist2.clamp(min=0.0) if use_torch else np.maximum(dist2, 0.0)
-            K = (-0.5 * dist2 / par).exp() if use_torch else np.exp(-0.5 * dist2 / par)
-        elif kind == "poly":
-            K = (1.0 + ip) ** par
-        else:
-            K = ip
-        dg = K.diagonal().clone() if use_torch else K.diagonal().copy()
-        dg = dg.clamp(min=1e-300) if use_torch else np.maximum(dg, 1e-300)
-        s = dg.rsqrt() if use_torch else 1.0 / np.sqrt(dg)
-        H = K * (s * B)[:, None] * (s * B)[None, :]
+        H = _kml_h(A, B, kind, par, use_torch)
         smax = max(smax, float(H.abs().sum()) if use_torch else float(np.abs(H).sum()))
         if use_torch:
             h32 = (2.0 * H).to(torch.float32)
             Q[i, :n, :n] = (h32 + h32.T) * 0.5
         else:
             Q[i, :n, :n] = _sym32(2.0 * H)
-        del K, H, ip
+        del H
     c = np.zeros((m + 1, N), np.float32)
     c[0, :n] = -2.0
     c[0, n] = float(m)
@@ -245,6 +254,53 @@ def kml_qcqp(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0,
         t = lambda v: torch.from_numpy(v).to(device)
         return QCQPData(N, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name)
     return QCQPData(N, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name)
+
+
+def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: float = 1.0,
+               device=None) -> QCQPData:
+    """The kernel-learning min-max problem as the paper states it (Sec. 5.2,
+    eq. min-max-KML), with the dual on the simplex:
+
+        min_{0 <= x <= C} max_{y in Delta_m}  lam ||x||^2 - 2 1'x
+                                              + sum_i (c / r_i) y_i x'H(K_i)x,
+
+    r_i = trace(K_i) = n (unit-diagonal kernels), c = sum_i r_i, so
+    c / r_i = m.  As QCQP data: Q_0 = 2 lam I (diagonal), c_0 = -2 1,
+    Q_i = 2 m H(K_i), c_i = 0, d_i = 0; meta['dual_radius'] = 1.  The
+    equality b'x = 0 of the paper's form is left out (no equalities on
+    this path).  Same features and kernels as kml_qcqp."""
+    a, b = kml_features(n, dfeat, seed)
+    specs = kml_kernel_specs(m)
+    assert len(specs) == m
+    use_torch = device is not None
+    if use_torch:
+        import torch
+        A = torch.from_numpy(a).to(device)
+        B = torch.from_numpy(b).to(device)
+        Q = torch.zeros((m, n, n), dtype=torch.float32, device=device)
+    else:
+        A, B = a, b
+        Q = np.zeros((m, n, n), np.float32)
+    for i, (kind, par) in enumerate(specs):
+        H = _kml_h(A, B, kind, par, use_torch)
+        if use_torch:
+            h32 = (2.0 * m * H).to(torch.float32)
+            Q[i] = (h32 + h32.T) * 0.5
+        else:
+            Q[i] = _sym32(2.0 * m * H)
+        del H
+    c = np.zeros((m + 1, n), np.float32)
+    c[0] = -2.0
+    d = np.zeros(m, np.float32)
+    lb = np.zeros(n, np.float32)
+    ub = np.full(n, C, np.float32)
+    q0diag = np.full(n, 2.0 * lam, np.float32)
+    name = f"kml_minmax(n={n},d={dfeat},m={m},seed={seed})"
+    meta = {"dual_radius": 1.0}
+    if use_torch:
+        t = lambda v: torch.from_numpy(v).to(device)
+        return QCQPData(n, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name, meta)
+    return QCQPData(n, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name, meta)
 
 
 def ball_qcqp(cvec: np.ndarray, rho: float, box: float = 10.0) -> QCQPData:
@@ -284,6 +340,10 @@ def config(name: str, device=None, seed: int = 0) -> QCQPData:
         return kml_qcqp(5000, 20, 8, seed=seed, device=device)
     if name == "C5":
         return kml_qcqp(16000, 32, 20, seed=seed, device=device)
+    if name == "C3m":
+        return kml_minmax(5000, 20, 8, seed=seed, device=device)
+    if name == "C5m":
+        return kml_minmax(16000, 32, 20, seed=seed, device=device)
     if name == "P1":
         return paper_random_qcqp(1000, 10, seed=seed)
     raise KeyError(name)
