@@ -58,6 +58,14 @@ typedef enum { RAPDB_YX = 0, RAPDB_XY = 1 } rapdb_variant;
  * symmetrically Jacobi-scaled matrix, Q~ = S C S with S = diag(s),
  * s_j = sqrt(Q_jj)/16, C = e4m3(256 * Q_jk / sqrt(Q_jj Q_kk)). */
 typedef enum { RAPDB_F32 = 0, RAPDB_BF16 = 1, RAPDB_FP8 = 2 } rapdb_storage;
+
+/* Dual set Y.  RAPDB_DUAL_NONNEG: y >= 0, the multipliers of the QCQP
+ * 0.5x'Q_ix + c_i'x + d_i <= 0.  RAPDB_DUAL_SIMPLEX: y on the simplex
+ * {y >= 0, sum y = dual_radius}, which turns the problem into
+ * min_x f(x) + dual_radius * max_i g_i(x), the min-max form of the paper's
+ * kernel-learning experiment (Sec. 5.2, eq. min-max-KML); the dual start y0
+ * must lie on the simplex. */
+typedef enum { RAPDB_DUAL_NONNEG = 0, RAPDB_DUAL_SIMPLEX = 1 } rapdb_dual_set;
 typedef enum { RAPDB_Q0_DENSE = 0, RAPDB_Q0_DIAG = 1, RAPDB_Q0_ZERO = 2 } rapdb_q0_kind;
 typedef enum { RAPDB_RESTART_NONE = 0, RAPDB_RESTART_FIXED = 1, RAPDB_RESTART_GAP = 2 } rapdb_restart;
 
@@ -91,6 +99,10 @@ typedef struct {
   int32_t gap_inner_max;      /* inner iterations of the smoothed-gap box QP          */
   int32_t pass_variant;       /* tile variant when rows_per_block > 0 (0..9, see     */
                               /* rapdb_get_tile); ignored when autotuning           */
+  int32_t dual_set;           /* rapdb_dual_set: y >= 0 (the QCQP's multipliers) or  */
+                              /* y on the simplex {y >= 0, sum y = dual_radius} (the */
+                              /* min-max kernel-learning problem, Sec. 5.2)         */
+  double dual_radius;         /* the simplex's sum (> 0), used with RAPDB_DUAL_SIMPLEX */
 } rapdb_params;
 
 typedef struct {

@@ -167,6 +167,8 @@ DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
   d.gap_first = p.gap_first;
   d.gap_every = p.gap_every;
   d.gap_inner_max = p.gap_inner_max;
+  d.dual_simplex = p.dual_set == RAPDB_DUAL_SIMPLEX ? 1 : 0;
+  d.dual_r = p.dual_radius;
   d.mu = p.mu;
   d.c_alpha = p.c_alpha;
   d.c_beta = p.c_beta;
@@ -213,6 +215,10 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
     return fail(ctx, RAPDB_ERR_INVALID, "rows_per_block must be 0 (auto) or a multiple of 32");
   if (p->rows_per_block > 0 && (p->pass_variant < 0 || p->pass_variant >= NVAR))
     return fail(ctx, RAPDB_ERR_INVALID, "pass_variant out of range");
+  if (p->dual_set != RAPDB_DUAL_NONNEG && p->dual_set != RAPDB_DUAL_SIMPLEX)
+    return fail(ctx, RAPDB_ERR_INVALID, "dual_set must be RAPDB_DUAL_NONNEG or RAPDB_DUAL_SIMPLEX");
+  if (p->dual_set == RAPDB_DUAL_SIMPLEX && !(p->dual_radius > 0.0 && std::isfinite(p->dual_radius)))
+    return fail(ctx, RAPDB_ERR_INVALID, "dual_radius must be positive and finite");
   return RAPDB_OK;
 }
 
@@ -659,6 +665,8 @@ void rapdb_default_params(rapdb_params* p, int32_t variant) {
   p->rows_per_block = 0;
   p->gap_inner_max = 200;
   p->pass_variant = 0;
+  p->dual_set = RAPDB_DUAL_NONNEG;
+  p->dual_radius = 1.0;
 }
 
 rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
@@ -786,7 +794,8 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
     CK(cudaMemcpyAsync(flags, ctx->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "x0 outside the box");
-    if (flags[1]) return fail(ctx, RAPDB_ERR_INVALID, "y0 has a negative (or NaN) entry");
+    if (flags[1] & 1) return fail(ctx, RAPDB_ERR_INVALID, "y0 has a negative (or NaN) entry");
+    if (flags[1] & 2) return fail(ctx, RAPDB_ERR_INVALID, "y0 is not on the dual simplex");
   }
   if (ctx->batched && ctx->mapped != B) {
     // a previous solve dropped finished instances from the block maps

@@ -64,6 +64,8 @@ enum VSlot : int {
 struct DevParams {
   int variant, c_nm, backtracking, restart, restart_period, restart_from_average;
   int max_iter, max_trials, kkt_every, refine, gap_first, gap_every, gap_inner_max;
+  int dual_simplex;     // 1: y on the simplex {y >= 0, sum y = dual_r}; 0: y >= 0
+  double dual_r;
   double mu, c_alpha, c_beta, delta, eta, tau_bar, gamma0, tol, stall_ratio, xi, q;
   int log_cap;
   double* gap_log;      // smoothed-gap values, one per evaluation (capacity log_cap)
@@ -216,6 +218,74 @@ __device__ __forceinline__ void block_allsum(double (&v)[K], double* smem /* NWA
 #pragma unroll
   for (int q = 0; q < K; ++q) v[q] = smem[q];
   __syncthreads();
+}
+
+// Projection of v (m entries, shared or global memory) onto the simplex
+// {y >= 0, sum y = r}, in place, by all threads of the CTA.  The threshold
+// theta solves sum_i max(v_i - theta, 0) = r: starting from all entries,
+// theta is the mean excess (sum - r)/count of the entries above the previous
+// theta; it only rises, and it is exact once no entry above the previous
+// theta lies at or below the new one (Michelot's finite algorithm).
+__device__ __forceinline__ void proj_simplex_block(double* v, int m, double r, double* smem /* NWARP*2 */) {
+  double th = -INFINITY;
+  for (int pass = 0; pass <= m; ++pass) {
+    double s[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      if (v[i] > th) { s[0] += v[i]; s[1] += 1.0; }
+    block_allsum<2>(s, smem);
+    if (!(s[1] > 0.0)) break;
+    const double tn = (s[0] - r) / s[1];
+    double c[1] = {0.0};
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      if (v[i] > th && v[i] <= tn) c[0] += 1.0;
+    block_allsum<1>(c, smem);
+    th = tn;
+    if (c[0] == 0.0) break;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = fmax(v[i] - th, 0.0);
+  __syncthreads();
+}
+
+// Threshold t of dist(g, N_Delta(y)) for the simplex Delta: minimises
+// sum_{y_i>0} (g_i - t)^2 + sum_{y_i=0} max(g_i - t, 0)^2.  t is the mean of
+// g over the support and the off-support entries above t; starting from all
+// entries the mean only rises as off-support entries at or below it leave.
+// All threads of the CTA; the result is valid in every thread.
+__device__ __forceinline__ double simplex_cone_t_block(const double* g, const double* y, int m,
+                                                       double* smem /* NWARP*2 */) {
+  double t = -INFINITY;
+  for (int pass = 0; pass <= m; ++pass) {
+    double s[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      if (y[i] > 0.0 || g[i] > t) { s[0] += g[i]; s[1] += 1.0; }
+    block_allsum<2>(s, smem);
+    if (!(s[1] > 0.0)) break;
+    const double tn = s[0] / s[1];
+    double c[1] = {0.0};
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      if (!(y[i] > 0.0) && g[i] > t && g[i] <= tn) c[0] += 1.0;
+    block_allsum<1>(c, smem);
+    t = tn;
+    if (c[0] == 0.0) break;
+  }
+  return t;
+}
+// The same threshold, one thread.
+__device__ __forceinline__ double simplex_cone_t_serial(const double* g, const double* y, int m) {
+  double t = -INFINITY;
+  for (int pass = 0; pass <= m; ++pass) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < m; ++i)
+      if (y[i] > 0.0 || g[i] > t) { s0 += g[i]; s1 += 1.0; }
+    if (!(s1 > 0.0)) break;
+    const double tn = s0 / s1;
+    int c = 0;
+    for (int i = 0; i < m; ++i)
+      if (!(y[i] > 0.0) && g[i] > t && g[i] <= tn) ++c;
+    t = tn;
+    if (c == 0) break;
+  }
+  return t;
 }
 
 // Arrival on a per-instance counter after this CTA's partials are written.

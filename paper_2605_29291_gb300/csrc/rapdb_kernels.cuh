@@ -105,16 +105,22 @@ __device__ __forceinline__ void start_check(const Inst& I, State& S) {
 
 // Per-constraint terms of the feasibility residual: r_feas_i^2 and
 // (g_i - d_i)^2, summed over this thread's constraints.
+// All threads of the CTA (a simplex dual first finds the normal-cone
+// threshold t: r_feas = dist(g, N_Delta(y)) with components g_i - t on the
+// support of y and max(g_i - t, 0) off it).
 __device__ __forceinline__ void kkt_feas_terms(const Inst& I, const double* g, const double* y, double& rf2,
-                                               double& gd2) {
+                                               double& gd2, double* smem) {
   rf2 = 0.0;
   gd2 = 0.0;
+  const double t = I.P.dual_simplex ? simplex_cone_t_block(g, y, I.m, smem) : 0.0;
   for (int i = threadIdx.x; i < I.m; i += NT) {
     const double gi = g[i];
-    const double ri = (y[i] > 0.0) ? fabs(gi) : fmax(gi, 0.0);
+    double ri;
+    if (I.P.dual_simplex) ri = (y[i] > 0.0) ? gi - t : fmax(gi - t, 0.0);
+    else ri = (y[i] > 0.0) ? fabs(gi) : fmax(gi, 0.0);
     rf2 += ri * ri;
-    const double t = gi - I.dcon[i];
-    gd2 += t * t;
+    const double dv = gi - I.dcon[i];
+    gd2 += dv * dv;
   }
 }
 
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     ys[i] = ycur[i];
     if (phase == PH_TRIAL && P.variant == RAPDB_YX) {
       const double s = (1.0 + theta) * gk[i] - theta * gp[i];
-      yts[i] = fmax(0.0, ycur[i] + sigma * s);
+      yts[i] = P.dual_simplex ? ycur[i] + sigma * s : fmax(0.0, ycur[i] + sigma * s);
     } else if (phase == PH_XY2) {
       yts[i] = I.yb[ycur0 ^ 1][i];
     } else {
@@ -260,6 +266,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     }
   }
   __syncthreads();
+  if (P.dual_simplex && phase == PH_TRIAL && P.variant == RAPDB_YX) proj_simplex_block(yts, m, P.dual_r, red);
   if (cb == 0 && phase == PH_TRIAL && P.variant == RAPDB_YX)
     for (int i = tid; i < m; i += NT) I.yb[ycur0 ^ 1][i] = yts[i];
 
@@ -518,7 +525,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   if (phase == PH_TRIAL && fresh) {
     double fe[2] = {0.0, 0.0};
     if (kkt_due) {
-      kkt_feas_terms(I, gk, ys, fe[0], fe[1]);
+      kkt_feas_terms(I, gk, ys, fe[0], fe[1], red);
       block_allsum<2>(fe, red);
     }
     if (tid != 0) return;
@@ -575,12 +582,18 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   }
   if (phase == PH_GAPP) {
     if (gap_iter == 1) {
-      // y-part of G_xi in closed form, y' = max(0, y + g(x)/(2 xi)): fixed during the evaluation
+      // y-part of G_xi in closed form, y' = proj_Y(y + g(x)/(2 xi)) (max(0, .), or
+      // the simplex projection): fixed during the evaluation
+      for (int i = tid; i < m; i += NT) {
+        const double v = ys[i] + gk[i] / (2.0 * P.xi);
+        yts[i] = P.dual_simplex ? v : fmax(0.0, v);
+      }
+      __syncthreads();
+      if (P.dual_simplex) proj_simplex_block(yts, m, P.dual_r, red);
       double yp[2] = {0.0, 0.0};
       for (int i = tid; i < m; i += NT) {
-        const double gi = gk[i];
-        const double lp = fmax(0.0, ys[i] + gi / (2.0 * P.xi));
-        yp[0] += lp * gi;
+        const double lp = yts[i];
+        yp[0] += lp * gk[i];
         yp[1] += (lp - ys[i]) * (lp - ys[i]);
       }
       block_allsum<2>(yp, red);
@@ -693,7 +706,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   if (phase == PH_KKT32B) {
     // the residual one precision level up (check_level) at x^k
     double fe[2] = {0.0, 0.0};
-    kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1]);
+    kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1], red);
     block_allsum<2>(fe, red);
     if (tid == 0) {
       double rel, rs, rf;
@@ -943,9 +956,10 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
       const double* Di = D + (size_t)(ii + 1) * NDOT;
       const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
       I.gnew[ii] = g;
-      yt[ii] = fmax(0.0, y[ii] + sig * g);
+      yt[ii] = P.dual_simplex ? y[ii] + sig * g : fmax(0.0, y[ii] + sig * g);
     }
     __syncthreads();
+    if (P.dual_simplex) proj_simplex_block(yt, m, P.dual_r, red);
     if (tid == 0) {
       S.passes += 1;
       S.phase = PH_XY2;

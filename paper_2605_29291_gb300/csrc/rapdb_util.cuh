@@ -106,6 +106,12 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   for (int i = threadIdx.x; i < I.m; i += blockDim.x)
     if (!(I.yb[0][i] >= 0.0)) atomicOr(&flags[1], 1);
   if (threadIdx.x != 0) return;
+  if (I.P.dual_simplex && I.m > 0) {
+    // a simplex dual start must lie on the simplex
+    double sy = 0.0;
+    for (int i = 0; i < I.m; ++i) sy += I.yb[0][i];
+    if (!(fabs(sy - I.P.dual_r) <= 1e-6 * I.P.dual_r)) atomicOr(&flags[1], 2);
+  }
   State& S = states[b];
   const unsigned long long now = globaltimer();
   S = State{};
@@ -219,8 +225,11 @@ __global__ void k_kkt_final(const Inst* __restrict__ insts, const double* __rest
     for (int q = 0; q < 3; ++q) p[q] += vpart[(size_t)bq * 3 + q];
   for (int i = 1; i <= I.m; ++i) g[i - 1] = 0.5 * dots[i * NDOT + D_XU] + dots[i * NDOT + D_CX] + I.dcon[i - 1];
   double rf2 = 0.0, gd2 = 0.0;
+  const double tc = I.P.dual_simplex ? simplex_cone_t_serial(g, y, I.m) : 0.0;
   for (int i = 0; i < I.m; ++i) {
-    const double ri = (y[i] > 0.0) ? fabs(g[i]) : fmax(g[i], 0.0);
+    double ri;
+    if (I.P.dual_simplex) ri = (y[i] > 0.0) ? g[i] - tc : fmax(g[i] - tc, 0.0);
+    else ri = (y[i] > 0.0) ? fabs(g[i]) : fmax(g[i], 0.0);
     rf2 += ri * ri;
     const double t = g[i] - I.dcon[i];
     gd2 += t * t;

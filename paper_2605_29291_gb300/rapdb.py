@@ -19,6 +19,7 @@ YX, XY = 0, 1
 F32, BF16, FP8 = 0, 1, 2
 Q0_DENSE, Q0_DIAG, Q0_ZERO = 0, 1, 2
 RESTART_NONE, RESTART_FIXED, RESTART_GAP = 0, 1, 2
+DUAL_NONNEG, DUAL_SIMPLEX = 0, 1
 
 
 class CParams(C.Structure):
@@ -33,6 +34,7 @@ class CParams(C.Structure):
         ("max_iter", C.c_int32), ("max_trials", C.c_int32), ("kkt_every", C.c_int32), ("use_graph", C.c_int32),
         ("tol", C.c_double), ("time_limit_s", C.c_double),
         ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32), ("pass_variant", C.c_int32),
+        ("dual_set", C.c_int32), ("dual_radius", C.c_double),
     ]
 
 
@@ -124,6 +126,8 @@ class Params:
     rows_per_block: int = 0
     gap_inner_max: int = 200
     pass_variant: int = 0
+    dual_set: int = 0
+    dual_radius: float = 1.0
 
     @classmethod
     def default(cls, variant: int = YX, **kw) -> "Params":

@@ -40,7 +40,7 @@ def test_binding_loads_and_mirrors_defaults():
     assert yx.xi == gp["xi"]["value"] and yx.q == gp["q"]["value"]
     assert yx.gap_first == gp["gap_first"]["yx"] and xy.gap_first == gp["gap_first"]["xy"]
     # struct layout: the ctypes mirror must match the C struct size
-    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8
+    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8 + 8
 
 
 def test_create_rejects_bad_sizes_without_touching_the_gpu():
@@ -60,3 +60,15 @@ def test_wait_selftest_rejects_bad_arguments_without_touching_the_gpu():
     from paper_2605_29291_gb300 import rapdb as R
     for complete, limit in ((0, 0), (1, -5), (0, 2000001), (2, 1000)):
         assert R.lib.rapdb_wait_selftest(complete, limit, None, None, None) == R.ERR_INVALID
+
+
+def test_params_struct_matches_the_library_layout():
+    """rapdb_default_params writes exactly sizeof(CParams) bytes and its last
+    fields land where the ctypes mirror reads them."""
+    from paper_2605_29291_gb300 import rapdb as R
+    size = ctypes.sizeof(R.CParams)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    R.lib.rapdb_default_params(ctypes.cast(buf, ctypes.POINTER(R.CParams)), 0)
+    assert all(b == 0xAB for b in bytes(buf)[size:])
+    p = R.CParams.from_buffer_copy(bytes(buf)[:size])
+    assert p.dual_set == R.DUAL_NONNEG and p.dual_radius == 1.0 and p.pass_variant == 0
