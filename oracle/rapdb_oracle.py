@@ -30,6 +30,10 @@ Sources (arXiv 2605.29291):
     by the sort-and-threshold method of Held, Wolfe and Crowder (1974), the
     simplex normal cone in the KKT residual, and the simplex projection in
     the y-part of G_xi.
+  * Linear equalities Ax = b (the paper's problem class with the equality
+    block, eq. NCP; the kernel-learning constraint b'x = 0 of Sec. 5.2): the
+    last n_eq rows of the constraint data are a_k'x - b_k with Q = 0 and a
+    free (unprojected) multiplier; their KKT component is |a_k'x - b_k|.
 
 Parity pins (see tests/test_oracle_pins.py, tests/test_oracle_simplex_pins.py):
 closed forms (ball constraint,
@@ -150,8 +154,9 @@ class Problem:
     dual_radius set, the dual set is the simplex {y >= 0, sum y = dual_radius}
     instead of the nonnegative orthant."""
 
-    def __init__(self, Q, c, d, lb, ub, dual_radius=None):
+    def __init__(self, Q, c, d, lb, ub, dual_radius=None, n_eq=0):
         self.dual_radius = None if dual_radius is None else float(dual_radius)
+        self.n_eq = int(n_eq)            # the last n_eq constraints are equalities (free multipliers)
         self.Q = np.asarray(Q, dtype=np.float64)
         self.c = np.asarray(c, dtype=np.float64)
         self.r = np.asarray(d, dtype=np.float64)
@@ -160,13 +165,26 @@ class Problem:
         self.n = self.Q.shape[1]
         self.m = self.Q.shape[0] - 1
         assert self.c.shape == (self.m + 1, self.n) and self.r.shape == (self.m,)
+        assert 0 <= self.n_eq <= self.m
+        self.m_ineq = self.m - self.n_eq
+        assert not np.any(self.Q[1 + self.m_ineq:]), "equality rows carry no quadratic term"
 
     @classmethod
     def from_data(cls, data, dual_radius=None) -> "Problem":
+        """The problem of a QCQPData; equalities A_eq x = b_eq (if any) become
+        the last rows, a_k'x - b_k with a zero quadratic term."""
         h = data.numpy()
         if dual_radius is None:
             dual_radius = (data.meta or {}).get("dual_radius")
-        return cls(data.dense_q(), h.c, h.d, h.lb, h.ub, dual_radius)
+        Q, c, d = data.dense_q(), h.c, h.d
+        p = 0
+        if getattr(h, "A_eq", None) is not None:
+            A = np.asarray(h.A_eq, np.float64).reshape(-1, data.n)
+            p = A.shape[0]
+            Q = np.concatenate([Q, np.zeros((p, data.n, data.n), Q.dtype)], axis=0)
+            c = np.concatenate([np.asarray(c, np.float64), A], axis=0)
+            d = np.concatenate([np.asarray(d, np.float64), -np.asarray(h.b_eq, np.float64)])
+        return cls(Q, c, d, h.lb, h.ub, dual_radius, n_eq=p)
 
     # objective and constraints --------------------------------------------
     def f(self, x):
@@ -201,15 +219,23 @@ class Problem:
         return np.minimum(np.maximum(x, self.lb), self.ub)
 
     def proj_y(self, lam):
+        """Projection onto Y: the orthant or the simplex for the inequality
+        multipliers, the identity for the equality multipliers."""
+        lam = np.asarray(lam, np.float64)
+        mi = self.m_ineq
+        head = lam[:mi]
         if self.dual_radius is not None:
-            return proj_simplex(lam, self.dual_radius)
-        return np.maximum(lam, 0.0)
+            head = proj_simplex(head, self.dual_radius) if mi > 0 else head
+        else:
+            head = np.maximum(head, 0.0)
+        return np.concatenate([head, lam[mi:]])
 
     def default_lam0(self):
-        """A dual start in Y: 0, or the simplex's centre."""
-        if self.dual_radius is not None:
-            return np.full(self.m, self.dual_radius / max(self.m, 1))
-        return np.zeros(self.m)
+        """A dual start in Y: 0, or the simplex's centre (equality multipliers 0)."""
+        lam = np.zeros(self.m)
+        if self.dual_radius is not None and self.m_ineq > 0:
+            lam[:self.m_ineq] = self.dual_radius / self.m_ineq
+        return lam
 
 
 def Dp(x, xk):
@@ -371,7 +397,8 @@ def kkt_residual(prob: Problem, x, lam):
 
       r_stat_j = dist(0, grad_x Phi(x, lam)_j + N_X(x)_j)   (box normal cone),
       r_feas_i = dist(0, -g_i(x) + N_{R+}(lam_i)),
-                 (simplex dual: ||r_feas|| = dist(g(x), N_Delta(lam))),
+                 (simplex dual: ||r_feas|| = dist(g(x), N_Delta(lam)); an
+                 equality row contributes |a_k'x - b_k|),
       rel_kkt = max(||r_stat|| / (1 + max(||Q_0x+q_0||, ||sum lam_i(Q_ix+q_i)||)),
                     ||r_feas|| / (1 + max(||r||, ||(g_i(x) - r_i)_i||))).
     """
@@ -386,11 +413,12 @@ def kkt_residual(prob: Problem, x, lam):
                   np.where(x >= prob.ub, np.maximum(grad, 0.0), np.abs(grad)))
     g = prob.g(x)
     r_stat = float(np.linalg.norm(rs))
-    if prob.dual_radius is not None:
-        r_feas = simplex_cone_distance(g, lam)[0]      # dist(0, -g + N_Delta(lam))
+    mi = prob.m_ineq
+    if prob.dual_radius is not None and mi > 0:
+        r_in = simplex_cone_distance(g[:mi], lam[:mi])[0]      # dist(0, -g + N_Delta(lam))
     else:
-        rf = np.where(lam > 0.0, np.abs(g), np.maximum(g, 0.0))
-        r_feas = float(np.linalg.norm(rf))
+        r_in = float(np.linalg.norm(np.where(lam[:mi] > 0.0, np.abs(g[:mi]), np.maximum(g[:mi], 0.0))))
+    r_feas = math.sqrt(r_in ** 2 + float(np.sum(g[mi:] ** 2)))   # equalities: |a_k'x - b_k|
     den_s = 1.0 + max(float(np.linalg.norm(gf)), float(np.linalg.norm(gc)))
     den_f = 1.0 + max(float(np.linalg.norm(prob.r)), float(np.linalg.norm(g - prob.r)))
     return max(r_stat / den_s, r_feas / den_f), r_stat, r_feas

@@ -59,6 +59,8 @@ class QCQPData:
     q0diag: object = None          # (n,) float32 when q0_kind == Q0_DIAG
     name: str = ""
     meta: dict = field(default_factory=dict)
+    A_eq: object = None            # (p, n) float32: linear equalities A_eq x = b_eq (optional)
+    b_eq: object = None            # (p,) float32
 
     @property
     def M(self) -> int:
@@ -71,7 +73,8 @@ class QCQPData:
                 return a
             return a.detach().cpu().numpy()
         return QCQPData(self.n, self.m, h(self.Q), h(self.c), h(self.d), h(self.lb),
-                        h(self.ub), self.q0_kind, h(self.q0diag), self.name, dict(self.meta))
+                        h(self.ub), self.q0_kind, h(self.q0diag), self.name, dict(self.meta),
+                        h(self.A_eq), h(self.b_eq))
 
     def to(self, device) -> "QCQPData":
         """Copy of the data as contiguous float32 torch tensors on `device`."""
@@ -84,7 +87,7 @@ class QCQPData:
                 a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
             return a.to(device=device, dtype=torch.float32).contiguous()
         return QCQPData(self.n, self.m, t(self.Q), t(self.c), t(self.d), t(self.lb), t(self.ub),
-                        self.q0_kind, t(self.q0diag), self.name, dict(self.meta))
+                        self.q0_kind, t(self.q0diag), self.name, dict(self.meta), t(self.A_eq), t(self.b_eq))
 
     def dense_q(self) -> np.ndarray:
         """(m+1, n, n) float32 host stack with Q_0 materialised (for the oracle)."""
@@ -257,7 +260,7 @@ def kml_qcqp(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0,
 
 
 def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: float = 1.0,
-               device=None) -> QCQPData:
+               device=None, bias: bool = False) -> QCQPData:
     """The kernel-learning min-max problem as the paper states it (Sec. 5.2,
     eq. min-max-KML), with the dual on the simplex:
 
@@ -266,9 +269,9 @@ def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: f
 
     r_i = trace(K_i) = n (unit-diagonal kernels), c = sum_i r_i, so
     c / r_i = m.  As QCQP data: Q_0 = 2 lam I (diagonal), c_0 = -2 1,
-    Q_i = 2 m H(K_i), c_i = 0, d_i = 0; meta['dual_radius'] = 1.  The
-    equality b'x = 0 of the paper's form is left out (no equalities on
-    this path).  Same features and kernels as kml_qcqp."""
+    Q_i = 2 m H(K_i), c_i = 0, d_i = 0; meta['dual_radius'] = 1.  With
+    bias=True the paper's equality b'x = 0 (b the labels) is attached as
+    A_eq = b', b_eq = 0.  Same features and kernels as kml_qcqp."""
     a, b = kml_features(n, dfeat, seed)
     specs = kml_kernel_specs(m)
     assert len(specs) == m
@@ -295,12 +298,14 @@ def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: f
     lb = np.zeros(n, np.float32)
     ub = np.full(n, C, np.float32)
     q0diag = np.full(n, 2.0 * lam, np.float32)
-    name = f"kml_minmax(n={n},d={dfeat},m={m},seed={seed})"
+    name = f"kml_minmax(n={n},d={dfeat},m={m},seed={seed}{',bias' if bias else ''})"
     meta = {"dual_radius": 1.0}
+    A_eq = b.astype(np.float32).reshape(1, n) if bias else None
+    b_eq = np.zeros(1, np.float32) if bias else None
     if use_torch:
-        t = lambda v: torch.from_numpy(v).to(device)
-        return QCQPData(n, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name, meta)
-    return QCQPData(n, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name, meta)
+        t = lambda v: None if v is None else torch.from_numpy(v).to(device)
+        return QCQPData(n, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name, meta, t(A_eq), t(b_eq))
+    return QCQPData(n, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name, meta, A_eq, b_eq)
 
 
 def ball_qcqp(cvec: np.ndarray, rho: float, box: float = 10.0) -> QCQPData:
