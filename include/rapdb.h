@@ -147,6 +147,26 @@ rapdb_status rapdb_create(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind
                           const float *d, const float *lb, const float *ub,
                           const rapdb_params *p, void *stream);
 
+/* rapdb_create with a block of linear equalities A_eq x = b_eq (the equality
+ * block of the paper's problem class, eq. NCP; for instance the constraint
+ * b'x = 0 of the kernel-learning problem, Sec. 5.2).
+ *   p_eq  >= 0 equalities (p_eq = 0 is rapdb_create).
+ *   A_eq  device, (p_eq, n) float32 row-major; b_eq device, (p_eq,) float32
+ *         (both copied).
+ * Each equality a_k'x - b_k is handled as constraint m + k (k = 1..p_eq)
+ * with no quadratic term (nothing extra is streamed) and a free multiplier:
+ * the dual vector y of rapdb_solve, rapdb_resume and rapdb_kkt_residual then
+ * has m + p_eq entries, the equality multipliers last (any real start), and
+ * the (m+1, n) arrays of rapdb_coupling_pass have m + p_eq + 1 rows.  Its
+ * KKT component is |a_k'x - b_k|.  Errors as for rapdb_create, plus
+ * RAPDB_ERR_INVALID for p_eq < 0, m + p_eq > 12800, NULL A_eq / b_eq with
+ * p_eq > 0 or a NaN in them. */
+rapdb_status rapdb_create_eq(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind,
+                             const float *Q, const float *q0diag, const float *c,
+                             const float *d, const float *lb, const float *ub,
+                             int64_t p_eq, const float *A_eq, const float *b_eq,
+                             const rapdb_params *p, void *stream);
+
 /* Run rAPDB from (x, y) (device, n and m floats; overwritten with the final
  * iterate; y must be >= 0 and x inside the box).  The whole loop -- trial
  * steps, coupling passes, FP64 backtracking tests, step-size updates,

@@ -225,14 +225,17 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
 // Build one instance's buffers.  Q, c, d, lb, ub, q0diag are the caller's device arrays.
 rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m64, int q0_kind, const float* Q,
                             const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
-                            int rb_override) {
+                            int rb_override, int64_t p_eq = 0, const float* A_eq = nullptr,
+                            const float* b_eq = nullptr) {
   const rapdb_params& p = ctx->p;
-  const int n = (int)n64, m = (int)m64;
-  const int M = (q0_kind == RAPDB_Q0_DENSE) ? m + 1 : m;
+  // inequalities 1..m_in with stored matrices, then p_eq linear equalities
+  const int n = (int)n64, m_in = (int)m64, pe = (int)p_eq, m = m_in + pe;
+  const int M = (q0_kind == RAPDB_Q0_DENSE) ? m_in + 1 : m_in;
   Inst& I = H.I;
   I = Inst{};
   I.n = n;
   I.m = m;
+  I.m_ineq = m_in;
   I.M = M;
   I.q0_kind = q0_kind;
   I.s_off = (q0_kind == RAPDB_Q0_DENSE) ? 0 : 1;
@@ -243,7 +246,7 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
 
   // validation
   CK(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), st));
-  k_validate<<<1024, 256, 0, st>>>(Q, n, M, c, m, d, lb, ub, q0_kind == RAPDB_Q0_DIAG ? q0diag : nullptr,
+  k_validate<<<1024, 256, 0, st>>>(Q, n, M, c, m_in, d, lb, ub, q0_kind == RAPDB_Q0_DIAG ? q0diag : nullptr,
                                    ctx->d_flags);
   CK(cudaGetLastError());
   int flags[4];
@@ -252,6 +255,16 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "NaN or Inf in the problem data");
   if (flags[1]) return fail(ctx, RAPDB_ERR_INVALID, "negative diagonal entry: some Q_i is not PSD");
   if (flags[2]) return fail(ctx, RAPDB_ERR_INVALID, "lb > ub");
+  std::vector<float> hb(pe);
+  if (pe > 0) {
+    std::vector<float> ha((size_t)pe * n);
+    CK(cudaMemcpy(ha.data(), A_eq, ha.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hb.data(), b_eq, (size_t)pe * 4, cudaMemcpyDeviceToHost));
+    for (float v : ha)
+      if (!std::isfinite(v)) return fail(ctx, RAPDB_ERR_INVALID, "NaN or Inf in the equality data");
+    for (float v : hb)
+      if (!std::isfinite(v)) return fail(ctx, RAPDB_ERR_INVALID, "NaN or Inf in the equality data");
+  }
 
   // stored Q
   const bool aligned = ((uintptr_t)Q % 16) == 0;
@@ -310,8 +323,11 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   float *cc = nullptr, *lbp = nullptr, *ubp = nullptr, *q0d = nullptr;
   double* dd = nullptr;
   AL(cc, (size_t)(m + 1) * ldv);
-  CK(cudaMemcpy2DAsync(cc, (size_t)ldv * 4, c, (size_t)n * 4, (size_t)n * 4, (size_t)(m + 1),
+  CK(cudaMemcpy2DAsync(cc, (size_t)ldv * 4, c, (size_t)n * 4, (size_t)n * 4, (size_t)(m_in + 1),
                        cudaMemcpyDeviceToDevice, st));
+  if (pe > 0)   // equality rows a_k after the inequality rows
+    CK(cudaMemcpy2DAsync(cc + (size_t)(m_in + 1) * ldv, (size_t)ldv * 4, A_eq, (size_t)n * 4, (size_t)n * 4,
+                         (size_t)pe, cudaMemcpyDeviceToDevice, st));
   AL(lbp, ldv);
   AL(ubp, ldv);
   CK(cudaMemcpyAsync(lbp, lb, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
@@ -320,12 +336,20 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   if (q0_kind == RAPDB_Q0_DIAG) CK(cudaMemcpyAsync(q0d, q0diag, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
   AL(dd, std::max(m, 1));
   double dn = 0.0;
-  if (m > 0) {
-    k_f2d<<<1, 256, 0, st>>>(d, dd, m);
-    std::vector<float> hd(m);
-    CK(cudaMemcpyAsync(hd.data(), d, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  if (m_in > 0) {
+    k_f2d<<<1, 256, 0, st>>>(d, dd, m_in);
+    std::vector<float> hd(m_in);
+    CK(cudaMemcpyAsync(hd.data(), d, (size_t)m_in * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (int i = 0; i < m; ++i) dn += (double)hd[i] * (double)hd[i];
+    for (int i = 0; i < m_in; ++i) dn += (double)hd[i] * (double)hd[i];
+  }
+  if (pe > 0) {   // an equality a'x = b is the constraint a'x - b: d = -b
+    std::vector<double> hdb(pe);
+    for (int k = 0; k < pe; ++k) {
+      hdb[k] = -(double)hb[k];
+      dn += hdb[k] * hdb[k];
+    }
+    CK(cudaMemcpy(dd + m_in, hdb.data(), (size_t)pe * 8, cudaMemcpyHostToDevice));
   }
   I.c = cc;
   {
@@ -672,10 +696,19 @@ void rapdb_default_params(rapdb_params* p, int32_t variant) {
 rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
                           const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
                           const rapdb_params* p, void* stream) {
+  return rapdb_create_eq(out, n, m, q0_kind, Q, q0diag, c, d, lb, ub, 0, nullptr, nullptr, p, stream);
+}
+
+rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
+                             const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
+                             int64_t p_eq, const float* A_eq, const float* b_eq, const rapdb_params* p,
+                             void* stream) {
   rapdb_ctx* ctx = nullptr;
   if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (n <= 0 || m < 0 || n > (1 << 28) || m > 12800) return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes n, m");
+  if (p_eq < 0 || m + p_eq > 12800 || (p_eq > 0 && (!A_eq || !b_eq)))
+    return fail(nullptr, RAPDB_ERR_INVALID, "bad equality block (p_eq, A_eq, b_eq)");
   if (q0_kind < RAPDB_Q0_DENSE || q0_kind > RAPDB_Q0_ZERO) return fail(nullptr, RAPDB_ERR_INVALID, "bad q0_kind");
   const int64_t M = (q0_kind == RAPDB_Q0_DENSE) ? m + 1 : m;
   if (M < 1) return fail(nullptr, RAPDB_ERR_INVALID, "m = 0 needs a dense Q_0 (nothing to stream otherwise)");
@@ -694,7 +727,8 @@ rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind
   ctx->hi.resize(1);
   rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
   if (s == RAPDB_OK)
-    s = build_instance(ctx, ctx->hi[0], n, m, q0_kind, Q, q0diag, c, d, lb, ub, p->rows_per_block);
+    s = build_instance(ctx, ctx->hi[0], n, m, q0_kind, Q, q0diag, c, d, lb, ub, p->rows_per_block, p_eq, A_eq,
+                       b_eq);
   if (s == RAPDB_OK && p->storage == RAPDB_FP8) {
     const Inst& I = ctx->hi[0].I;
     s = dalloc(ctx, &ctx->XS, (size_t)std::max(I.M, 1) * I.ldv);
@@ -888,7 +922,7 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v,
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, vpad, uo, Ut, Wt, ctx->XS, ctx->VS, ctx->tvpart, 0);
   launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, vpad, ctx->XS, ctx->VS, uo, Ut, Wt,
                ctx->tpart, 0, &ctx->d_ctrl->err);
-  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, dots);
+  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, dots, xpad, vpad);
   CK(cudaGetLastError());
   CK(cudaMemcpy2DAsync(U, (size_t)I.n * 4, Ut, (size_t)I.ldv * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
                        cudaMemcpyDeviceToDevice, st));
@@ -922,7 +956,7 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
                                       level >= 1 ? 1 : 0);
   launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut,
                Wt, ctx->tpart, level, &ctx->d_ctrl->err, xzero, Ulo);
-  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots);
+  k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots, xpad, xpad);
   k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, Ulo, ctx->tvpart);
   k_kkt_final<<<1, 32, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout);
   CK(cudaGetLastError());

@@ -80,7 +80,9 @@ struct DevParams {
 
 // Immutable description of one instance (device memory).
 struct Inst {
-  int n, m, M;          // variables, constraints, stored matrices
+  int n, m, M;          // variables, constraints (inequalities + equalities), stored matrices
+  int m_ineq;           // constraints 1..m_ineq are inequalities; m_ineq+1..m are linear
+                        // equalities a'x = b (no stored matrix, free multipliers)
   int ld;               // row stride (elements) of the stored Q
   int ld32;             // row stride of the float32 Q (refinement / KKT pass)
   int ldv;              // stride of (m+1, n) vector arrays (multiple of 16)

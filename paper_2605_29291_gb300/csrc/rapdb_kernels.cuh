@@ -112,11 +112,12 @@ __device__ __forceinline__ void kkt_feas_terms(const Inst& I, const double* g, c
                                                double& gd2, double* smem) {
   rf2 = 0.0;
   gd2 = 0.0;
-  const double t = I.P.dual_simplex ? simplex_cone_t_block(g, y, I.m, smem) : 0.0;
+  const double t = I.P.dual_simplex ? simplex_cone_t_block(g, y, I.m_ineq, smem) : 0.0;
   for (int i = threadIdx.x; i < I.m; i += NT) {
     const double gi = g[i];
     double ri;
-    if (I.P.dual_simplex) ri = (y[i] > 0.0) ? gi - t : fmax(gi - t, 0.0);
+    if (i >= I.m_ineq) ri = gi;                 // equality: |a'x - b|
+    else if (I.P.dual_simplex) ri = (y[i] > 0.0) ? gi - t : fmax(gi - t, 0.0);
     else ri = (y[i] > 0.0) ? fabs(gi) : fmax(gi, 0.0);
     rf2 += ri * ri;
     const double dv = gi - I.dcon[i];
@@ -258,7 +259,8 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     ys[i] = ycur[i];
     if (phase == PH_TRIAL && P.variant == RAPDB_YX) {
       const double s = (1.0 + theta) * gk[i] - theta * gp[i];
-      yts[i] = P.dual_simplex ? ycur[i] + sigma * s : fmax(0.0, ycur[i] + sigma * s);
+      // inequality multipliers: max(0, .) or the simplex below; equality multipliers are free
+      yts[i] = (P.dual_simplex || i >= I.m_ineq) ? ycur[i] + sigma * s : fmax(0.0, ycur[i] + sigma * s);
     } else if (phase == PH_XY2) {
       yts[i] = I.yb[ycur0 ^ 1][i];
     } else {
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     }
   }
   __syncthreads();
-  if (P.dual_simplex && phase == PH_TRIAL && P.variant == RAPDB_YX) proj_simplex_block(yts, m, P.dual_r, red);
+  if (P.dual_simplex && phase == PH_TRIAL && P.variant == RAPDB_YX) proj_simplex_block(yts, I.m_ineq, P.dual_r, red);
   if (cb == 0 && phase == PH_TRIAL && P.variant == RAPDB_YX)
     for (int i = tid; i < m; i += NT) I.yb[ycur0 ^ 1][i] = yts[i];
 
@@ -586,10 +588,10 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       // the simplex projection): fixed during the evaluation
       for (int i = tid; i < m; i += NT) {
         const double v = ys[i] + gk[i] / (2.0 * P.xi);
-        yts[i] = P.dual_simplex ? v : fmax(0.0, v);
+        yts[i] = (P.dual_simplex || i >= I.m_ineq) ? v : fmax(0.0, v);
       }
       __syncthreads();
-      if (P.dual_simplex) proj_simplex_block(yts, m, P.dual_r, red);
+      if (P.dual_simplex) proj_simplex_block(yts, I.m_ineq, P.dual_r, red);
       double yp[2] = {0.0, 0.0};
       for (int i = tid; i < m; i += NT) {
         const double lp = yts[i];
@@ -894,6 +896,28 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
   if (!arrive_last(&S.arrive_pass, (unsigned)I.M)) return;
   const int tid = threadIdx.x;
   if (I.s_off && tid < NDOT) I.dots[tid] = S.dots0[tid];
+  if (I.m > I.m_ineq && !gap_phase(phase)) {
+    // linear equalities (no stored matrix): u = w = 0, c'x and c'v here
+    const float* xlo_e = comp ? ((phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1]) : nullptr;
+    for (int i = I.m_ineq + 1; i <= I.m; ++i) {
+      const float* ci = I.c + (size_t)i * ldv;
+      double sv[2] = {0.0, 0.0};
+      for (int jj = tid; jj < I.n; jj += NT) {
+        const double xj = (double)x[jj] + (xlo_e ? (double)xlo_e[jj] : 0.0);
+        sv[0] += (double)ci[jj] * xj;
+        sv[1] += (double)ci[jj] * (double)v[jj];
+      }
+      block_allsum<2>(sv, red);
+      if (tid == 0) {
+        double* Di = I.dots + (size_t)i * NDOT;
+        Di[D_XU] = 0.0;
+        Di[D_VW] = 0.0;
+        Di[D_VUO] = 0.0;
+        Di[D_CX] = sv[0];
+        Di[D_CV] = sv[1];
+      }
+    }
+  }
   __syncthreads();
 
   const DevParams& P = I.P;
@@ -956,10 +980,10 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
       const double* Di = D + (size_t)(ii + 1) * NDOT;
       const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
       I.gnew[ii] = g;
-      yt[ii] = P.dual_simplex ? y[ii] + sig * g : fmax(0.0, y[ii] + sig * g);
+      yt[ii] = (P.dual_simplex || ii >= I.m_ineq) ? y[ii] + sig * g : fmax(0.0, y[ii] + sig * g);
     }
     __syncthreads();
-    if (P.dual_simplex) proj_simplex_block(yt, m, P.dual_r, red);
+    if (P.dual_simplex) proj_simplex_block(yt, I.m_ineq, P.dual_r, red);
     if (tid == 0) {
       S.passes += 1;
       S.phase = PH_XY2;

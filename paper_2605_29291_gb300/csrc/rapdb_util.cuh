@@ -104,12 +104,12 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
     if (!(x >= I.lb[j] && x <= I.ub[j])) atomicOr(&flags[0], 1);
   }
   for (int i = threadIdx.x; i < I.m; i += blockDim.x)
-    if (!(I.yb[0][i] >= 0.0)) atomicOr(&flags[1], 1);
+    if (i < I.m_ineq ? !(I.yb[0][i] >= 0.0) : !(fabs(I.yb[0][i]) < INFINITY)) atomicOr(&flags[1], 1);
   if (threadIdx.x != 0) return;
-  if (I.P.dual_simplex && I.m > 0) {
+  if (I.P.dual_simplex && I.m_ineq > 0) {
     // a simplex dual start must lie on the simplex
     double sy = 0.0;
-    for (int i = 0; i < I.m; ++i) sy += I.yb[0][i];
+    for (int i = 0; i < I.m_ineq; ++i) sy += I.yb[0][i];
     if (!(fabs(sy - I.P.dual_r) <= 1e-6 * I.P.dual_r)) atomicOr(&flags[1], 2);
   }
   State& S = states[b];
@@ -165,8 +165,28 @@ __global__ void __launch_bounds__(NT) k_vec_plain(const Inst* __restrict__ insts
 
 // Fixed-order final reduction of a stand-alone pass into dots[(m+1)][5].
 __global__ void __launch_bounds__(NT) k_dots_final(const Inst* __restrict__ insts, const double* __restrict__ part,
-                                                   const double* __restrict__ vpart, double* __restrict__ dots) {
+                                                   const double* __restrict__ vpart, double* __restrict__ dots,
+                                                   const float* __restrict__ x, const float* __restrict__ v) {
+  __shared__ double red[NWARP * 2];
   const Inst& I = insts[0];
+  // linear equalities (no stored matrix): u = w = 0, c'x and c'v
+  for (int i = I.m_ineq + 1; i <= I.m; ++i) {
+    const float* ci = I.c + (size_t)i * I.ldv;
+    double sv[2] = {0.0, 0.0};
+    for (int jj = threadIdx.x; jj < I.n; jj += NT) {
+      sv[0] += (double)ci[jj] * (double)x[jj];
+      sv[1] += (double)ci[jj] * (double)v[jj];
+    }
+    block_allsum<2>(sv, red);
+    if (threadIdx.x == 0) {
+      double* Di = dots + (size_t)i * NDOT;
+      Di[D_XU] = 0.0;
+      Di[D_VW] = 0.0;
+      Di[D_VUO] = 0.0;
+      Di[D_CX] = sv[0];
+      Di[D_CV] = sv[1];
+    }
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int pq = warp; pq < I.M * NDOT; pq += NWARP) {
     const double* src = part + (size_t)pq * I.nrb;
@@ -225,10 +245,11 @@ __global__ void k_kkt_final(const Inst* __restrict__ insts, const double* __rest
     for (int q = 0; q < 3; ++q) p[q] += vpart[(size_t)bq * 3 + q];
   for (int i = 1; i <= I.m; ++i) g[i - 1] = 0.5 * dots[i * NDOT + D_XU] + dots[i * NDOT + D_CX] + I.dcon[i - 1];
   double rf2 = 0.0, gd2 = 0.0;
-  const double tc = I.P.dual_simplex ? simplex_cone_t_serial(g, y, I.m) : 0.0;
+  const double tc = I.P.dual_simplex ? simplex_cone_t_serial(g, y, I.m_ineq) : 0.0;
   for (int i = 0; i < I.m; ++i) {
     double ri;
-    if (I.P.dual_simplex) ri = (y[i] > 0.0) ? g[i] - tc : fmax(g[i] - tc, 0.0);
+    if (i >= I.m_ineq) ri = g[i];               // equality: |a'x - b|
+    else if (I.P.dual_simplex) ri = (y[i] > 0.0) ? g[i] - tc : fmax(g[i] - tc, 0.0);
     else ri = (y[i] > 0.0) ? fabs(g[i]) : fmax(g[i], 0.0);
     rf2 += ri * ri;
     const double t = g[i] - I.dcon[i];

@@ -56,6 +56,8 @@ def _load():
     sig = {
         "rapdb_default_params": (None, [P, C.c_int32]),
         "rapdb_create": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp, P, vp]),
+        "rapdb_create_eq": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int64,
+                                      vp, vp, P, vp]),
         "rapdb_solve": (C.c_int, [vp, vp, vp, I]),
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
@@ -174,17 +176,21 @@ class Solver:
     def __init__(self, data, params: Params | None = None):
         import torch
         self.params = params or Params.default()
-        self.n, self.m = int(data.n), int(data.m)
-        self._keep = [data.Q, data.c, data.d, data.lb, data.ub, data.q0diag]
+        A_eq, b_eq = getattr(data, "A_eq", None), getattr(data, "b_eq", None)
+        self.p_eq = 0 if A_eq is None else int(A_eq.shape[0])
+        # m counts the equalities too: the dual vector has m entries, the
+        # equality multipliers last
+        self.n, self.m = int(data.n), int(data.m) + self.p_eq
+        self._keep = [data.Q, data.c, data.d, data.lb, data.ub, data.q0diag, A_eq, b_eq]
         for t in self._keep:
             if t is not None:
                 assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
         self.device = data.Q.device
         self.ctx = C.c_void_p()
         cp = self.params.to_c()
-        st = lib.rapdb_create(C.byref(self.ctx), self.n, self.m, int(data.q0_kind), _ptr(data.Q),
-                              _ptr(data.q0diag), _ptr(data.c), _ptr(data.d), _ptr(data.lb), _ptr(data.ub),
-                              C.byref(cp), _stream_handle(self.device))
+        st = lib.rapdb_create_eq(C.byref(self.ctx), self.n, int(data.m), int(data.q0_kind), _ptr(data.Q),
+                                 _ptr(data.q0diag), _ptr(data.c), _ptr(data.d), _ptr(data.lb), _ptr(data.ub),
+                                 self.p_eq, _ptr(A_eq), _ptr(b_eq), C.byref(cp), _stream_handle(self.device))
         _check(st, None)
         self._log = None
 
