@@ -497,13 +497,14 @@ def run_ours(args):
                 torch.cuda.empty_cache()
                 log(f"{name}: {kml[name]}")
             # the paper's own kernel-learning formulation: the min-max problem
-            # with the dual on the simplex (Sec. 5.2), strongly convex in x with
-            # mu = 2 lambda = 2, non-monotone yx, to rel KKT 1e-6; without
-            # restarts (APDB-yx) and with the paper's restart every 200
-            # iterations (one solve each; the context's graph is built at create)
-            runs = (("kml_minmax_n5000_m8_bf16", "C3m", R.BF16, (("apdb", R.RESTART_NONE),
-                                                                 ("rapdb_every_200", R.RESTART_FIXED))),
-                    ("kml_minmax_n16000_m20_fp8", "C5m", R.FP8, (("apdb", R.RESTART_NONE),)))
+            # with the dual on the simplex and the bias equality b'x = 0 (Sec.
+            # 5.2), strongly convex in x with mu = 2 lambda = 2, non-monotone yx,
+            # to rel KKT 1e-6; without restarts (APDB-yx) and with the paper's
+            # restart every 200 iterations (one solve each; the context's graph
+            # is built at create)
+            runs = (("kml_minmax_n5000_m8_bf16", "C3mb", R.BF16, (("apdb", R.RESTART_NONE),
+                                                                  ("rapdb_every_200", R.RESTART_FIXED))),
+                    ("kml_minmax_n16000_m20_fp8", "C5mb", R.FP8, (("apdb", R.RESTART_NONE),)))
             for name, cfg, st, modes in runs:
                 dk = W.config(cfg, device=dev)
                 kml[name] = {"n": dk.n, "m": dk.m}
@@ -513,7 +514,8 @@ def run_ours(args):
                                           dual_set=R.DUAL_SIMPLEX, dual_radius=1.0)
                     sk = R.Solver(dk, pk)
                     xk = torch.zeros(dk.n, device=dev)
-                    yk = torch.full((dk.m,), 1.0 / dk.m, device=dev)
+                    yk = torch.zeros(sk.m, device=dev)        # simplex centre; equality multiplier 0
+                    yk[:dk.m] = 1.0 / dk.m
                     ik = sk.solve(xk, yk, check=False)
                     ms0, b0 = sk.time_pass(reps=10, level=0)
                     kml[name][mode] = {"iters": ik["iters"], "passes": ik["passes"], "time_to_tol_s": ik["seconds"],

@@ -349,6 +349,10 @@ def config(name: str, device=None, seed: int = 0) -> QCQPData:
         return kml_minmax(5000, 20, 8, seed=seed, device=device)
     if name == "C5m":
         return kml_minmax(16000, 32, 20, seed=seed, device=device)
+    if name == "C3mb":
+        return kml_minmax(5000, 20, 8, seed=seed, device=device, bias=True)
+    if name == "C5mb":
+        return kml_minmax(16000, 32, 20, seed=seed, device=device, bias=True)
     if name == "P1":
         return paper_random_qcqp(1000, 10, seed=seed)
     raise KeyError(name)
