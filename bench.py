@@ -502,15 +502,16 @@ def run_ours(args):
             # to rel KKT 1e-6; without restarts (APDB-yx) and with the paper's
             # restart every 200 iterations (one solve each; the context's graph
             # is built at create)
-            runs = (("kml_minmax_n5000_m8_bf16", "C3mb", R.BF16, (("apdb", R.RESTART_NONE),
-                                                                  ("rapdb_every_200", R.RESTART_FIXED))),
-                    ("kml_minmax_n16000_m20_fp8", "C5mb", R.FP8, (("apdb", R.RESTART_NONE),)))
+            runs = (("kml_minmax_n5000_m8_bf16", "C3mb", R.BF16, (("apdb", R.RESTART_NONE, 0),
+                                                                  ("rapdb_every_200", R.RESTART_FIXED, 0),
+                                                                  ("rapdb_every_200_warm_tau", R.RESTART_FIXED, 1))),
+                    ("kml_minmax_n16000_m20_fp8", "C5mb", R.FP8, (("apdb", R.RESTART_NONE, 0),)))
             for name, cfg, st, modes in runs:
                 dk = W.config(cfg, device=dev)
                 kml[name] = {"n": dk.n, "m": dk.m}
-                for mode, rs in modes:
+                for mode, rs, warm in modes:
                     pk = R.Params.default(R.YX, c_nm=1, mu=2.0, storage=st, refine=1, tol=1e-6, max_iter=20000,
-                                          time_limit_s=60.0, restart=rs, restart_period=200,
+                                          time_limit_s=60.0, restart=rs, restart_period=200, restart_warm_tau=warm,
                                           dual_set=R.DUAL_SIMPLEX, dual_radius=1.0)
                     sk = R.Solver(dk, pk)
                     xk = torch.zeros(dk.n, device=dev)

@@ -103,6 +103,8 @@ typedef struct {
                               /* y on the simplex {y >= 0, sum y = dual_radius} (the */
                               /* min-max kernel-learning problem, Sec. 5.2)         */
   double dual_radius;         /* the simplex's sum (> 0), used with RAPDB_DUAL_SIMPLEX */
+  int32_t restart_warm_tau;   /* 1: a restart starts from the last accepted tau       */
+                              /*    instead of tau_bar (0, the paper's reset)          */
 } rapdb_params;
 
 typedef struct {

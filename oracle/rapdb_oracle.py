@@ -74,6 +74,7 @@ class Params:
     restart: str = "fixed"           # "none" | "fixed" (Algorithm 2) | "gap" (eq. ada_restart)
     restart_period: int = 200
     restart_from_average: bool = False
+    restart_warm_tau: bool = False   # a restart starts from the last accepted tau instead of tau_bar
     xi: float = 0.04
     q: float = 0.5
     gap_first: int = 50
@@ -274,21 +275,23 @@ class RoutineState:
     T: float = 0.0
 
 
-def start_routine(prob: Problem, x0, lam0, p: Params) -> RoutineState:
+def start_routine(prob: Problem, x0, lam0, p: Params, tau_start=None) -> RoutineState:
     """Initialisation line of Algorithm 1: (x^-1, y^-1) = (x^0, y^0),
     tau_-1 = tau_0 = tau_bar, sigma_-1 = gamma_0 tau_0, cumulative sums zero.
     alpha_0, beta_0 follow the recurrences at k = -1 (yx: alpha = c_alpha /
-    sigma; xy: alpha = c_alpha / tau, beta = gamma_0 c_beta / sigma)."""
-    sigma_m1 = p.gamma0 * p.tau_bar
+    sigma; xy: alpha = c_alpha / tau, beta = gamma_0 c_beta / sigma).
+    tau_start replaces tau_bar (the warm-started restart option)."""
+    t0 = p.tau_bar if tau_start is None else float(tau_start)
+    sigma_m1 = p.gamma0 * t0
     if p.variant == "yx":
         a0, b0 = p.c_alpha / sigma_m1, 0.0
     else:
-        a0, b0 = p.c_alpha / p.tau_bar, p.gamma0 * p.c_beta / sigma_m1
+        a0, b0 = p.c_alpha / t0, p.gamma0 * p.c_beta / sigma_m1
     x0 = np.array(x0, dtype=np.float64)
     lam0 = np.array(lam0, dtype=np.float64)
     return RoutineState(x=x0.copy(), x_prev=x0.copy(), lam=lam0.copy(), lam_prev=lam0.copy(),
-                        tau_prev=p.tau_bar, sigma_prev=sigma_m1, gamma=p.gamma0,
-                        tau_init=p.tau_bar, alpha_k=a0, beta_k=b0, x0=x0.copy(),
+                        tau_prev=t0, sigma_prev=sigma_m1, gamma=p.gamma0,
+                        tau_init=t0, alpha_k=a0, beta_k=b0, x0=x0.copy(),
                         lam0=lam0.copy(), x_cum=np.zeros_like(x0), lam_cum=np.zeros_like(lam0))
 
 
@@ -526,7 +529,7 @@ def rapdb(prob: Problem, x0=None, lam0=None, p: Params | None = None, keep_itera
                 xs, ls = st.x_cum / st.T, st.lam_cum / st.T
             else:
                 xs, ls = st.x, st.lam
-            st = start_routine(prob, xs, ls, p)
+            st = start_routine(prob, xs, ls, p, st.tau_prev if p.restart_warm_tau else None)
             restarts += 1
         elif p.restart == "gap" and it >= p.gap_first:
             if st.k > 0 and p.restart_from_average:
@@ -541,7 +544,7 @@ def rapdb(prob: Problem, x0=None, lam0=None, p: Params | None = None, keep_itera
                 fire = G <= p.q * G_ref
                 log.setdefault("gap", []).append((it, G, bool(fire)))
                 if fire:
-                    st = start_routine(prob, xs, ls, p)
+                    st = start_routine(prob, xs, ls, p, st.tau_prev if p.restart_warm_tau else None)
                     restarts += 1
                     G_ref = G
         try:

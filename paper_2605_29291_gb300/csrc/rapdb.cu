@@ -168,6 +168,7 @@ DevParams make_devparams(const rapdb_params& p, const rapdb_ctx* ctx) {
   d.gap_every = p.gap_every;
   d.gap_inner_max = p.gap_inner_max;
   d.dual_simplex = p.dual_set == RAPDB_DUAL_SIMPLEX ? 1 : 0;
+  d.warm_tau = p.restart_warm_tau ? 1 : 0;
   d.dual_r = p.dual_radius;
   d.mu = p.mu;
   d.c_alpha = p.c_alpha;
@@ -691,6 +692,7 @@ void rapdb_default_params(rapdb_params* p, int32_t variant) {
   p->pass_variant = 0;
   p->dual_set = RAPDB_DUAL_NONNEG;
   p->dual_radius = 1.0;
+  p->restart_warm_tau = 0;
 }
 
 rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,

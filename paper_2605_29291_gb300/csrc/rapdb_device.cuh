@@ -65,6 +65,7 @@ struct DevParams {
   int variant, c_nm, backtracking, restart, restart_period, restart_from_average;
   int max_iter, max_trials, kkt_every, refine, gap_first, gap_every, gap_inner_max;
   int dual_simplex;     // 1: y on the simplex {y >= 0, sum y = dual_r}; 0: y >= 0
+  int warm_tau;         // a restart starts from the last accepted tau instead of tau_bar
   double dual_r;
   double mu, c_alpha, c_beta, delta, eta, tau_bar, gamma0, tol, stall_ratio, xi, q;
   int log_cap;

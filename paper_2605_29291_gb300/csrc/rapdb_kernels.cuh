@@ -64,17 +64,20 @@ __device__ __forceinline__ void finish(State& S, Ctrl* ctrl, int status) {
 
 // Reset of Algorithm 1's initialisation line at a (re)start:
 // tau_{-1} = tau_0 = tau_bar, sigma_{-1} = gamma_0 tau_bar, gamma = gamma_0,
-// alpha_0 / beta_0 from the parameter recurrences at k = -1.
+// alpha_0 / beta_0 from the parameter recurrences at k = -1.  With warm_tau
+// a restart (after at least one accepted iteration) starts from the last
+// accepted tau instead of tau_bar.
 static __device__ void restart_scalars(const DevParams& P, State& S) {
-  S.tau_prev = P.tau_bar;
-  S.sigma_prev = P.gamma0 * P.tau_bar;
+  const double t0 = (P.warm_tau && S.k > 0 && S.tau_prev > 0.0) ? S.tau_prev : P.tau_bar;
+  S.tau_prev = t0;
+  S.sigma_prev = P.gamma0 * t0;
   S.gamma = P.gamma0;
-  S.tau = P.tau_bar;
+  S.tau = t0;
   if (P.variant == RAPDB_YX) {
     S.alpha_k = P.c_alpha / S.sigma_prev;
     S.beta_k = 0.0;
   } else {
-    S.alpha_k = P.c_alpha / P.tau_bar;
+    S.alpha_k = P.c_alpha / t0;
     S.beta_k = P.gamma0 * P.c_beta / S.sigma_prev;
   }
   S.k = 0;

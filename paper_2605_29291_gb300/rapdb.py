@@ -34,7 +34,7 @@ class CParams(C.Structure):
         ("max_iter", C.c_int32), ("max_trials", C.c_int32), ("kkt_every", C.c_int32), ("use_graph", C.c_int32),
         ("tol", C.c_double), ("time_limit_s", C.c_double),
         ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32), ("pass_variant", C.c_int32),
-        ("dual_set", C.c_int32), ("dual_radius", C.c_double),
+        ("dual_set", C.c_int32), ("dual_radius", C.c_double), ("restart_warm_tau", C.c_int32),
     ]
 
 
@@ -130,6 +130,7 @@ class Params:
     pass_variant: int = 0
     dual_set: int = 0
     dual_radius: float = 1.0
+    restart_warm_tau: int = 0
 
     @classmethod
     def default(cls, variant: int = YX, **kw) -> "Params":

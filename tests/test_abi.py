@@ -40,7 +40,7 @@ def test_binding_loads_and_mirrors_defaults():
     assert yx.xi == gp["xi"]["value"] and yx.q == gp["q"]["value"]
     assert yx.gap_first == gp["gap_first"]["yx"] and xy.gap_first == gp["gap_first"]["xy"]
     # struct layout: the ctypes mirror must match the C struct size
-    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8 + 8
+    assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8 + 8 + 8
 
 
 def test_create_rejects_bad_sizes_without_touching_the_gpu():
@@ -72,3 +72,4 @@ def test_params_struct_matches_the_library_layout():
     assert all(b == 0xAB for b in bytes(buf)[size:])
     p = R.CParams.from_buffer_copy(bytes(buf)[:size])
     assert p.dual_set == R.DUAL_NONNEG and p.dual_radius == 1.0 and p.pass_variant == 0
+    assert p.restart_warm_tau == 0

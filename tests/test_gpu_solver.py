@@ -37,7 +37,7 @@ def oracle_params(R, p, **kw):
                     gamma0=p.gamma0, restart=restart, restart_period=p.restart_period,
                     restart_from_average=bool(p.restart_from_average), xi=p.xi, q=p.q, gap_first=p.gap_first,
                     gap_every=p.gap_every, max_iter=p.max_iter, max_trials=p.max_trials, kkt_every=p.kkt_every,
-                    tol=p.tol, **kw)
+                    tol=p.tol, restart_warm_tau=bool(p.restart_warm_tau), **kw)
 
 
 @pytest.fixture(scope="module")
@@ -482,3 +482,26 @@ def test_batched_xy_adaptive_matches_single(R, cuda):
         assert torch.equal(x, xb)
         s.close()
     bs.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_warm_started_tau_across_restarts_matches_oracle(R, cuda, c1, variant):
+    """With restart_warm_tau a restart starts from the last accepted tau: the
+    same accept/reject pattern and step sizes as the oracle across the
+    restarts at k = 40, 80, and the same solution."""
+    p = R.Params.default(variant, restart=R.RESTART_FIXED, restart_period=40, restart_warm_tau=1, tol=1e-6,
+                         max_iter=20000)
+    s = R.Solver(c1.to(cuda), p)
+    s.set_log(120, iterates=False)
+    x, y = gpu_vecs(c1, cuda)
+    info = s.solve(x, y)
+    assert info["status"] == R.OK, info
+    prob = O.Problem.from_data(c1)
+    r = O.rapdb(prob, p=oracle_params(R, p))
+    assert r.status == 0
+    k = min(120, info["iters"], r.iters)
+    np.testing.assert_array_equal(s.log["trials"].cpu().numpy()[:k], np.array(r.log["trials"][:k]))
+    np.testing.assert_allclose(s.log["tau"].cpu().numpy()[:k], np.array(r.log["tau"][:k]), rtol=1e-9)
+    fo = prob.f(r.x)
+    assert abs(info["obj"] - fo) <= 1e-5 * (1 + abs(fo))
+    s.close()

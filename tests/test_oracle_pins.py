@@ -426,3 +426,18 @@ def test_adaptive_restart_fires_only_on_halving():
             ref = G
             fired += 1
     assert fired == r.restarts and fired >= 1
+
+
+def test_warm_started_restart_takes_the_last_accepted_tau():
+    """restart_warm_tau: the first trial after a restart is the last accepted
+    tau of the previous run (tau_bar without the option)."""
+    data = W.config("C1")
+    prob = O.Problem.from_data(data)
+    for warm in (False, True):
+        p = O.default_params("yx", restart="fixed", restart_period=20, tol=0.0, max_iter=45,
+                             restart_warm_tau=warm)
+        r = O.rapdb(prob, p=p)
+        ti, ta = r.log["tau_init"], r.log["tau"]
+        assert ti[0] == p.tau_bar
+        assert ti[20] == (ta[19] if warm else p.tau_bar)
+        assert ti[40] == (ta[39] if warm else p.tau_bar)
