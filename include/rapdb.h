@@ -80,15 +80,22 @@ typedef struct {
   int32_t restart;            /* rapdb_restart                                        */
   double mu;                  /* strong convexity modulus used by gamma_{k+1}         */
   double c_alpha, c_beta, delta, eta;
-  double tau_bar;             /* first trial step size of every run                   */
+  double tau_bar;             /* first trial step of every run (of the first run only  */
+                              /*    with restart_warm_tau)                            */
   double gamma0;              /* sigma = gamma * tau                                  */
   int32_t restart_period;     /* fixed restart: iterations per run (Algorithm 2's K^) */
   int32_t restart_from_average; /* 1: restart from the weighted average (Algorithm 2)   */
   double xi, q;               /* smoothed gap parameters (eq. (ada_restart))           */
   int32_t gap_first, gap_every; /* gap schedule: first evaluation, then period          */
   int32_t storage;            /* rapdb_storage                                        */
-  int32_t refine;             /* quantised storage: switch to float32 Q on a KKT stall*/
-  double stall_ratio;         /* stall: rel KKT fell by less than this factor per run */
+  int32_t refine;             /* 1: compensated (double-float) float32 products: from */
+                              /*    the start with F32 storage; BF16/FP8 storage      */
+                              /*    switches to them when a precision check (restart  */
+                              /*    boundaries, every restart_period/4 iterations)    */
+                              /*    finds a stall, the stored problem solved, or the  */
+                              /*    true residual above twice the stored level's      */
+  double stall_ratio;         /* stall: the true rel KKT fell by less than this factor */
+                              /*    since the previous precision check               */
   int32_t max_iter, max_trials, kkt_every;
   int32_t use_graph;          /* 1: loop bodies captured in a CUDA graph of 32 bodies */
                               /*    (two launches kept in flight); 0: host launches    */
@@ -169,11 +176,14 @@ rapdb_status rapdb_create_eq(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_k
                              int64_t p_eq, const float *A_eq, const float *b_eq,
                              const rapdb_params *p, void *stream);
 
-/* Run rAPDB from (x, y) (device, n and m floats; overwritten with the final
- * iterate; y must be >= 0 and x inside the box).  The whole loop -- trial
+/* Run rAPDB from (x, y) (device, n and m floats -- m + p_eq with equalities;
+ * overwritten with the final iterate).  x must lie in the box; y in the dual
+ * set: y >= 0, or on the simplex with RAPDB_DUAL_SIMPLEX, equality
+ * multipliers free (RAPDB_ERR_INVALID otherwise).  The whole loop -- trial
  * steps, coupling passes, FP64 backtracking tests, step-size updates,
- * restarts and the KKT stop test -- runs on the device; the host waits once,
- * at the end, then fills *info (host, may be NULL).  Returns info->status. */
+ * restarts, precision checks and the KKT stop test -- runs on the device; the
+ * host waits once per graph launch (32 loop bodies) and at the end, then fills
+ * *info (host, may be NULL).  Returns info->status. */
 rapdb_status rapdb_solve(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
 
 /* The float64 iterate of the last rapdb_solve / rapdb_resume: x (device, n
