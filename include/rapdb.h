@@ -294,7 +294,10 @@ rapdb_status rapdb_resume(rapdb_ctx *ctx, float *x, float *y, rapdb_info *info);
  * warp streams together, and 16-byte chunks in flight per row (any output
  * may be NULL).  With rows_per_block = 0 in the parameters, rapdb_create
  * times every supported tile on the context's own data (CUDA events on its
- * stream) and keeps the fastest. */
+ * stream) and keeps the fastest; the choice is remembered for the process,
+ * per device and problem shape (n, stored matrices, storage, refinement,
+ * row stride, Q_0 kind), and later contexts of that shape reuse it without
+ * timing. */
 rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32_t *ctas,
                             int32_t *rows_per_warp, int32_t *chunks_in_flight);
 

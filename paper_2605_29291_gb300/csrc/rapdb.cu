@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "rapdb_launch.h"
@@ -641,6 +644,40 @@ rapdb_status autotune(rapdb_ctx* ctx) {
   return retile(ctx, best_rb);
 }
 
+// Tiles found by the autotuner, remembered per device and problem shape so
+// that later contexts of the same shape skip the timing launches.  Key:
+// device, n, stored matrices, storage, incremental (float32 with refinement),
+// row stride, Q_0 kind.
+using TileKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tile_mutex;
+std::map<TileKey, std::pair<int, int>> g_tile_cache;   // -> (variant, rows per block)
+
+TileKey tile_key(const rapdb_ctx* ctx) {
+  const Inst& I = ctx->hi[0].I;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int inc = (I.storage == RAPDB_F32 && I.P.refine && I.Ulo[0]) ? 1 : 0;
+  return TileKey(dev, I.n, I.M, I.storage, inc, I.ld, I.q0_kind);
+}
+
+// Autotune, or take the tile a previous context of the same shape found.
+rapdb_status pick_tile(rapdb_ctx* ctx) {
+  const TileKey key = tile_key(ctx);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mutex);
+    auto it = g_tile_cache.find(key);
+    if (it != g_tile_cache.end()) {
+      ctx->pvar = it->second.first;
+      return retile(ctx, it->second.second);
+    }
+  }
+  rapdb_status s = autotune(ctx);
+  if (s != RAPDB_OK) return s;
+  std::lock_guard<std::mutex> lk(g_tile_mutex);
+  g_tile_cache[key] = {ctx->pvar, ctx->hi[0].I.rb};
+  return RAPDB_OK;
+}
+
 int64_t body_cap(const rapdb_params& p) {
   // every trial is one body; iterations <= max_iter, trials <= max_trials each,
   // plus set-up, restart and KKT bodies
@@ -750,7 +787,7 @@ rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_k
     if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tout, 8);
   }
   if (s == RAPDB_OK) s = finalize_ctx(ctx);
-  if (s == RAPDB_OK && p->rows_per_block == 0) s = autotune(ctx);
+  if (s == RAPDB_OK && p->rows_per_block == 0) s = pick_tile(ctx);
   if (s == RAPDB_OK && p->rows_per_block > 0) ctx->pvar = p->pass_variant;
   if (s == RAPDB_OK) s = build_graph(ctx, 32);
   if (s != RAPDB_OK) {
