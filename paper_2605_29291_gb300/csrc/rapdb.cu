@@ -3,6 +3,7 @@
 // batched contexts and checkpointing.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -109,6 +110,19 @@ void launch_plain(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, co
   if (storage == RAPDB_F32) launch_plain_f32(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
   else if (storage == RAPDB_BF16) launch_plain_bf16(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
   else launch_plain_fp8(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
+}
+
+// NVTX range for the duration of a scope (set-up, solve, stand-alone pass
+// and residual phases show up by name in a profiler's timeline; no cost
+// without one attached).
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+};
+
+std::string ctrl_error_text(int code) {
+  if (code == 1) return "a bounded wait in the coupling pass gave up";
+  return "range check " + std::to_string(code) + " of the checked build failed";
 }
 
 rapdb_status fail(rapdb_ctx* ctx, rapdb_status st, const std::string& msg) {
@@ -561,8 +575,8 @@ rapdb_status run_loop(rapdb_ctx* ctx, int64_t max_bodies) {
       CK(cudaEventSynchronize(ctx->ev[old]));
       pending = 1;
       const int act = ctx->h_ctrl[old].active;
-      if (act <= 0) {
-        done = true;
+      if (act <= 0 || ctx->h_ctrl[old].err != 0) {
+        done = true;     // all instances finished, or a kernel reported an error
       } else if (ctx->batched && 2 * act <= ctx->mapped && ctx->npblk > 4 * 152) {
         // half of the mapped instances have finished: launch CTAs for the
         // running ones only (each instance's arithmetic is unchanged)
@@ -599,6 +613,7 @@ rapdb_status retile(rapdb_ctx* ctx, int rb) {
 // Autotuner: time every (tile variant, rows per CTA) on the caller's data with
 // CUDA events and keep the fastest.
 rapdb_status autotune(rapdb_ctx* ctx) {
+  NvtxScope nvtx_scope("rapdb_autotune");
   cudaStream_t st = ctx->stream;
   const Inst I0 = ctx->hi[0].I;
   const int rbs[3] = {32, 64, 128};
@@ -678,6 +693,19 @@ rapdb_status pick_tile(rapdb_ctx* ctx) {
   return RAPDB_OK;
 }
 
+// End of a stand-alone call (pass, residual, timing): wait for the stream,
+// then turn an error a kernel recorded into a status, and clear it.
+rapdb_status finish_standalone(rapdb_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  int err = 0;
+  CK(cudaMemcpy(&err, &ctx->d_ctrl->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(cudaMemset(&ctx->d_ctrl->err, 0, sizeof(int)));
+    return fail(ctx, RAPDB_ERR_CUDA, ctrl_error_text(err));
+  }
+  return RAPDB_OK;
+}
+
 int64_t body_cap(const rapdb_params& p) {
   // every trial is one body; iterations <= max_iter, trials <= max_trials each,
   // plus set-up, restart and KKT bodies
@@ -742,6 +770,7 @@ rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_k
                              const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
                              int64_t p_eq, const float* A_eq, const float* b_eq, const rapdb_params* p,
                              void* stream) {
+  NvtxScope nvtx_scope("rapdb_create");
   rapdb_ctx* ctx = nullptr;
   if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -803,6 +832,7 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
                                   const float* const* Q, const float* const* c, const float* const* d,
                                   const float* const* lb, const float* const* ub, const rapdb_params* p,
                                   void* stream) {
+  NvtxScope nvtx_scope("rapdb_create_batched");
   if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (B <= 0 || !n || !m || !Q || !c || !d || !lb || !ub) return fail(nullptr, RAPDB_ERR_INVALID, "bad batch arguments");
@@ -845,6 +875,7 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
 }
 
 static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* y, rapdb_info* info, bool resume) {
+  NvtxScope nvtx_scope("rapdb_solve");
   cudaStream_t st = ctx->stream;
   const int B = ctx->B;
   ctx->launches = 0;
@@ -886,7 +917,7 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
   CK(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(State) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&ctx->h_ctrl[0], ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (ctx->h_ctrl[0].err) return fail(ctx, RAPDB_ERR_CUDA, "a bounded wait in the coupling pass gave up");
+  if (ctx->h_ctrl[0].err) return fail(ctx, RAPDB_ERR_CUDA, ctrl_error_text(ctx->h_ctrl[0].err));
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
   rapdb_status first_bad = RAPDB_OK;
@@ -939,6 +970,7 @@ rapdb_status rapdb_solve_batched(rapdb_ctx* ctx, float* const* x, float* const* 
 
 rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v, const float* uold, float* U,
                                  float* W, double* dots) {
+  NvtxScope nvtx_scope("rapdb_coupling_pass");
   if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
   if (!x || !v || !U || !W || !dots) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
   const Inst& I = ctx->hi[0].I;
@@ -967,12 +999,12 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v,
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(W, (size_t)I.n * 4, Wt, (size_t)I.ldv * 4, (size_t)I.n * 4, (size_t)(I.m + 1),
                        cudaMemcpyDeviceToDevice, st));
-  CK(cudaStreamSynchronize(st));
-  return RAPDB_OK;
+  return finish_standalone(ctx);
 }
 
 rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, double* rel_kkt, double* r_stat,
                                 double* r_feas) {
+  NvtxScope nvtx_scope("rapdb_kkt_residual");
   if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
   const Inst& I = ctx->hi[0].I;
   if (!x || (I.m > 0 && !y)) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
@@ -1001,7 +1033,10 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
   CK(cudaGetLastError());
   double out[4];
   CK(cudaMemcpyAsync(out, ctx->tout, sizeof(out), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  {
+    rapdb_status fs = finish_standalone(ctx);
+    if (fs != RAPDB_OK) return fs;
+  }
   if (rel_kkt) *rel_kkt = out[0];
   if (r_stat) *r_stat = out[1];
   if (r_feas) *r_feas = out[2];
@@ -1010,6 +1045,7 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
 
 rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double* ms_per_pass,
                              int64_t* bytes_per_pass) {
+  NvtxScope nvtx_scope("rapdb_time_pass");
   if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
   if (reps < 1) return fail(ctx, RAPDB_ERR_INVALID, "reps must be >= 1");
   const Inst& I = ctx->hi[0].I;
@@ -1044,6 +1080,10 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
   CK(cudaEventSynchronize(ctx->t1));
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+  {
+    rapdb_status fs = finish_standalone(ctx);
+    if (fs != RAPDB_OK) return fs;
+  }
   if (ms_per_pass) *ms_per_pass = (double)ms / reps;
   if (bytes_per_pass) {
     const int64_t eb = lv >= 1 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));

@@ -40,6 +40,18 @@ __device__ __forceinline__ bool pass_phase(int ph) {
 }
 __device__ __forceinline__ bool gap_phase(int ph) { return ph == PH_GAPP || ph == PH_GAPF || ph == PH_GAPV; }
 
+// Range checks of the checked build (RAPDB_CHECKED): a CTA whose indices or
+// launch configuration are out of range records a code in Ctrl::err (the first
+// one wins) and returns before touching memory; the host loop stops at its
+// next poll.  No trap and no device assert.
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+enum CheckCode : int { CHK_PASS_RANGE = 101, CHK_PASS_SMEM = 102, CHK_VEC_RANGE = 111, CHK_VEC_SMEM = 112,
+                       CHK_PLAIN_RANGE = 121 };
+
 // Power iterations per smoothed-gap evaluation (first one / warm-started).
 constexpr int GAP_POWER_FIRST = 30;
 constexpr int GAP_POWER_WARM = 10;
@@ -245,6 +257,16 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const int m = I.m, n = I.n, ldv = I.ldv;
   const int cb = blockIdx.x - I.vblk0;
   const int tid = threadIdx.x;
+#ifdef RAPDB_CHECKED
+  {
+    const int code = !(cb >= 0 && cb < I.ncb) ? CHK_VEC_RANGE
+                     : (dyn_smem_bytes() < (unsigned)(2 * m) * 8u ? CHK_VEC_SMEM : 0);
+    if (code) {
+      if (tid == 0) atomicCAS(&ctrl->err, 0, code);
+      return;
+    }
+  }
+#endif
   const int lc = tid % VCOL, grp = tid / VCOL;
   const int fresh = S.fresh;
   const int k = S.k, it = S.it;
@@ -770,7 +792,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
 // each, area rounded up to 128 bytes) followed by the slot buffers
 template <int NST>
 __host__ __device__ constexpr size_t tma_bar_bytes() {
-  return ((size_t)NWARP * NST * 8 + 127) / 128 * 128;
+  return NST <= 0 ? 0 : ((size_t)NWARP * (size_t)(NST > 0 ? NST : 0) * 8 + 127) / 128 * 128;
 }
 template <int NST, int RPW, int CWB>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
@@ -836,6 +858,17 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
   const int row0 = r * I.rb;
   const int rows = min(I.rb, I.n - row0);
   const int ldv = I.ldv;
+#ifdef RAPDB_CHECKED
+  {
+    const bool in_range = item >= 0 && item < I.M * I.nrb && rows >= 1 && rows <= I.rb && i <= I.m_ineq;
+    const int code = !in_range ? CHK_PASS_RANGE
+                     : (NST > 0 && dyn_smem_bytes() < (unsigned)tma_smem_bytes<NST, RPW, CWB>() ? CHK_PASS_SMEM : 0);
+    if (code) {
+      if (threadIdx.x == 0) atomicCAS(&ctrl->err, 0, code);
+      return;
+    }
+  }
+#endif
   const int level = (phase == PH_KKT32) ? S.check_level : S.precision;
   const bool comp = (level == 2) && !gap_phase(phase);               // compensated products
   const bool use32 = (ST != RAPDB_F32) && (level >= 1);
@@ -1045,6 +1078,13 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass_plain(const Ins
   const int row0 = r * I.rb;
   const int rows = min(I.rb, I.n - row0);
   const int ldv = I.ldv;
+#ifdef RAPDB_CHECKED
+  if (!(s < I.M && rows >= 1 && rows <= I.rb) ||
+      (NST > 0 && dyn_smem_bytes() < (unsigned)tma_smem_bytes<NST, RPW, CWB>())) {
+    if (threadIdx.x == 0 && err) atomicCAS(err, 0, CHK_PLAIN_RANGE);
+    return;
+  }
+#endif
   double* out = part + (size_t)s * NDOT * I.nrb + r;
   const float* uo = uold ? uold + (size_t)i * ldv : nullptr;
   const float* crow = I.c + (size_t)i * ldv;

@@ -11,7 +11,9 @@ import os
 from dataclasses import dataclass, fields
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librapdb.so")
+# RAPDB_LIBRARY selects another build of the library (the checked build in
+# the tests); the default is the in-tree librapdb.so
+LIB_PATH = os.environ.get("RAPDB_LIBRARY") or os.path.join(HERE, "librapdb.so")
 
 OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_BACKTRACK, ERR_MAXITER, ERR_TIMEOUT, ERR_NUMERIC = range(8)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "NOMEM", "BACKTRACK", "MAXITER", "TIMEOUT", "NUMERIC"]
@@ -49,7 +51,7 @@ class CInfo(C.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"librapdb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        raise ImportError(f"the rAPDB library is not built ({LIB_PATH}); run __graft_entry__.build()")
     lib = C.CDLL(LIB_PATH)
     P, I, vp = C.POINTER(CParams), C.POINTER(CInfo), C.c_void_p
     ctxpp = C.POINTER(vp)
