@@ -112,6 +112,19 @@ typedef struct {
   double dual_radius;         /* the simplex's sum (> 0), used with RAPDB_DUAL_SIMPLEX */
   int32_t restart_warm_tau;   /* 1: a restart starts from the last accepted tau       */
                               /*    instead of tau_bar (0, the paper's reset)          */
+  int32_t pack_sym;           /* 1: symmetric block packing.  The context keeps the   */
+                              /*    upper block triangle of every float32 Q_i in      */
+                              /*    128 x 128 tiles (about half of Q's bytes, on top  */
+                              /*    of Q), and the incremental trial passes read each */
+                              /*    tile once for its rows and, transposed, for its   */
+                              /*    columns: half the bytes of a row-streaming pass.  */
+                              /*    Needs refine = 1, exactly symmetric Q_i (checked  */
+                              /*    at create: RAPDB_ERR_INVALID) and a single-       */
+                              /*    instance context; rows_per_block and              */
+                              /*    pass_variant are ignored (the other passes use    */
+                              /*    64-row items of tile variant 1).  Results are     */
+                              /*    reproducible run to run; they differ from an      */
+                              /*    unpacked context's in rounding only.              */
 } rapdb_params;
 
 typedef struct {
@@ -219,6 +232,22 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx *ctx, const float *x, const float *y,
 rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
                                  const float *uold, float *U, float *W, double *dots);
 
+/* The packed incremental pass of a pack_sym context (the form of its trial
+ * passes, with zero low parts), for every STORED matrix Q_i in order (i = 0..m
+ * when Q_0 is dense, i = 1..m otherwise; M matrices):
+ *     W[s] = Q_i v,   U[s] = Uold[s] + W[s]   (rounded once from float64)
+ * computed from the upper block triangle (each off-diagonal tile read once
+ * for its rows and, transposed, for its columns) and, when dots is not NULL,
+ *     dots[5*s + 0] = x'U[s], dots[5*s+1] = v'W[s], dots[5*s+2] = v'Uold[s],
+ *     dots[5*s + 3] = c_i'x,  dots[5*s+4] = c_i'v
+ * (float64; the same fixed-order sums the solver forms).  x, v: device, n
+ * floats; uold, U, W: device, (M, n) float32 row-major; dots: device, 5*M
+ * doubles.  The context's solver state is not changed.  Runs on the
+ * context's stream and returns when it has finished.  RAPDB_ERR_INVALID
+ * without pack_sym or on NULL arguments. */
+rapdb_status rapdb_packed_pass(rapdb_ctx *ctx, const float *x, const float *v, const float *uold,
+                               float *U, float *W, double *dots);
+
 /* Time the context's coupling-pass kernel: `reps` back-to-back launches on
  * the context's stream, on the current solver iterate (x^k, and d of the
  * last trial as the second right-hand side), bracketed by two CUDA events on
@@ -227,10 +256,12 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
  * compensated (double-float) products (contexts created with refine = 1),
  * 3 = the incremental form of level 2 that the solver's trial passes use
  * (U = U^k + Q d: one float32 right-hand side added to the double-float
- * products at x^k).
+ * products at x^k), 4 = level 3 through the packed upper block triangle
+ * (contexts created with pack_sym = 1; the form their trials use).
  * *ms_per_pass (host) receives the average duration of one launch,
  * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
- * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8).  Outputs
+ * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8); at level 4
+ * the packed tiles, M * T(T+1)/2 * 128 * 128 * 4 with T = ceil(n / 128).  Outputs
  * go to context scratch; the solver state is not changed.  RAPDB_ERR_INVALID
  * when the level does not exist in this context. */
 rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, int32_t level, double *ms_per_pass,

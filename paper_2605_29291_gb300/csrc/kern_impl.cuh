@@ -51,6 +51,18 @@ void RAPDB_CAT(launch_pass_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const In
   }
 }
 
+// The coupling pass of a context with symmetric block packing, and its CTAs
+// resident per SM (the packed pass runs one persistent wave).
+void RAPDB_CAT(launch_pass_sym_, RAPDB_SUF)(dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C,
+                                            const int* pm, const float* XS, const float* VS) {
+  k_pass_sym<RAPDB_ST><<<g, NT, 0, s>>>(I, S, C, pm, XS, VS);
+}
+int RAPDB_CAT(pass_sym_occupancy_, RAPDB_SUF)() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pass_sym<RAPDB_ST>, NT, 0) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
 void RAPDB_CAT(launch_plain_, RAPDB_SUF)(int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x,
                                          const float* v, const float* XS, const float* VS, const float* uold,
                                          float* U, float* W, double* part, int level, const float* xlo,

@@ -28,6 +28,7 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 struct InstHost {
   Inst I;                      // device-pointer copy uploaded to the context's array
   int64_t q_bytes;             // bytes of stored Q read by one pass
+  int64_t qp_bytes = 0;        // bytes of the packed tiles read by one packed pass
 };
 
 }  // namespace
@@ -68,6 +69,8 @@ struct rapdb_ctx {
   int g_bodies = 0;
   int64_t launches = 0;        // kernels launched by the current call
   int pvar = 0;                // coupling-pass tile variant (kVarRPW / kVarUNR)
+  int sym_grid = 0;            // pack_sym: CTAs of the solver's pass kernel (one resident wave)
+  int sym_plain_grid = 0;      // ... and of the stand-alone packed pass
   float tune_ms = 0.0f;        // autotuner: best pass time
   State* h_state = nullptr;    // pinned
   Ctrl* h_ctrl = nullptr;      // pinned, 2 slots
@@ -95,6 +98,19 @@ void launch_vec(int storage, dim3 g, size_t smem, cudaStream_t s, const Inst* I,
   if (storage == RAPDB_F32) launch_vec_f32(g, smem, s, I, S, C, vm, XS, VS);
   else if (storage == RAPDB_BF16) launch_vec_bf16(g, smem, s, I, S, C, vm, XS, VS);
   else launch_vec_fp8(g, smem, s, I, S, C, vm, XS, VS);
+}
+
+void launch_pass_sym(int storage, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* pm,
+                     const float* XS, const float* VS) {
+  if (storage == RAPDB_F32) launch_pass_sym_f32(g, s, I, S, C, pm, XS, VS);
+  else if (storage == RAPDB_BF16) launch_pass_sym_bf16(g, s, I, S, C, pm, XS, VS);
+  else launch_pass_sym_fp8(g, s, I, S, C, pm, XS, VS);
+}
+
+int pass_sym_occupancy(int storage) {
+  if (storage == RAPDB_F32) return pass_sym_occupancy_f32();
+  if (storage == RAPDB_BF16) return pass_sym_occupancy_bf16();
+  return pass_sym_occupancy_fp8();
 }
 
 void launch_pass(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* pm,
@@ -237,6 +253,10 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
     return fail(ctx, RAPDB_ERR_INVALID, "dual_set must be RAPDB_DUAL_NONNEG or RAPDB_DUAL_SIMPLEX");
   if (p->dual_set == RAPDB_DUAL_SIMPLEX && !(p->dual_radius > 0.0 && std::isfinite(p->dual_radius)))
     return fail(ctx, RAPDB_ERR_INVALID, "dual_radius must be positive and finite");
+  if (p->pack_sym != 0 && p->pack_sym != 1) return fail(ctx, RAPDB_ERR_INVALID, "pack_sym must be 0 or 1");
+  if (p->pack_sym && !p->refine)
+    return fail(ctx, RAPDB_ERR_INVALID,
+                "pack_sym packs the float32 matrices of the compensated trial passes: it needs refine = 1");
   return RAPDB_OK;
 }
 
@@ -383,7 +403,8 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
   I.dnorm = sqrt(dn);
 
   // tiles
-  I.rb = rb_override > 0 ? rb_override : pick_rows_per_block(n, M);
+  // (a context with packed tiles runs its row-streaming passes on 64-row items)
+  I.rb = p.pack_sym ? 64 : (rb_override > 0 ? rb_override : pick_rows_per_block(n, M));
   I.nrb = (n + I.rb - 1) / I.rb;
   I.ncb = (n + VCOL - 1) / VCOL;
 
@@ -415,6 +436,41 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
     AL(I.gzf, ldv);
     AL(I.gwf, ldv);
     AL(I.gpf, ldv);
+  }
+  if (p.pack_sym && M > 0) {
+    // symmetric block packing of the float32 matrices the trial passes read
+    const float* Qf = (p.storage == RAPDB_F32) ? (const float*)I.Q : I.Q32;
+    const int ldq = (p.storage == RAPDB_F32) ? I.ld : I.ld32;
+    CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), st));
+    k_sym_check<<<2048, dim3(32, 8), 0, st>>>(Qf, ldq, n, M, ctx->d_flags);
+    CK(cudaGetLastError());
+    int asym = 0;
+    CK(cudaMemcpyAsync(&asym, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (asym) return fail(ctx, RAPDB_ERR_INVALID, "pack_sym needs exactly symmetric Q_i (Q_i[j][k] == Q_i[k][j])");
+    const int T = (n + STB - 1) / STB;
+    const int64_t ntile64 = (int64_t)T * (T + 1) / 2;
+    if ((int64_t)M * ntile64 > (int64_t)INT32_MAX / 2)
+      return fail(ctx, RAPDB_ERR_INVALID, "pack_sym: too many tiles for this n and m");
+    const int ntile = (int)ntile64;
+    std::vector<int> tij;
+    tij.reserve(ntile);
+    for (int a = 0; a < T; ++a)
+      for (int b2 = a; b2 < T; ++b2) tij.push_back((a << 16) | b2);
+    int* dtij = nullptr;
+    float* qp = nullptr;
+    AL(dtij, ntile);
+    CK(cudaMemcpyAsync(dtij, tij.data(), tij.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    AL(qp, (size_t)M * ntile * STB * STB);
+    k_pack_sym<<<4096, 256, 0, st>>>(Qf, ldq, n, M, T, ntile, dtij, qp);
+    CK(cudaGetLastError());
+    AL(I.sp, (size_t)M * T * T * STB);
+    AL(I.spart, (size_t)M * NDOT * T);
+    I.Qp = qp;
+    I.tij = dtij;
+    I.tsym = T;
+    I.ntile = ntile;
+    H.qp_bytes = (int64_t)M * ntile * STB * STB * 4;
   }
   I.P = make_devparams(p, ctx);
   return RAPDB_OK;
@@ -483,7 +539,13 @@ rapdb_status launch_body(rapdb_ctx* ctx, cudaStream_t s) {
   (void)blk;
   auto vec = [&]() { launch_vec(st, gv, sm, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS); };
   vec();
-  if (ctx->npblk > 0) launch_pass(st, ctx->pvar, gp, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
+  if (ctx->sym_grid > 0) {
+    const Inst& I = ctx->hi[0].I;
+    launch_pass_sym(st, dim3(ctx->sym_grid), s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS,
+                    ctx->VS);
+    k_sym_finish<0><<<I.M * I.tsym, NT, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
+  } else if (ctx->npblk > 0)
+    launch_pass(st, ctx->pvar, gp, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
   if (ctx->variant == RAPDB_XY) vec();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, RAPDB_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -723,6 +785,23 @@ rapdb_status finish_standalone(rapdb_ctx* ctx) {
   return RAPDB_OK;
 }
 
+// pack_sym contexts: tile variant 1 for the row-streaming passes, and one
+// resident wave of CTAs (at most one per tile) for the pass kernels.
+rapdb_status setup_sym(rapdb_ctx* ctx) {
+  const Inst& I = ctx->hi[0].I;
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int occ_plain = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, k_sym_plain<0>, NT, 0));
+  const int64_t tiles = (int64_t)I.M * I.ntile;
+  const int64_t wave = (int64_t)std::max(nsm, 1) * pass_sym_occupancy(ctx->storage);
+  ctx->pvar = 1;
+  ctx->sym_grid = (int)std::max<int64_t>(1, std::min(tiles, wave));
+  ctx->sym_plain_grid = (int)std::max<int64_t>(1, std::min(tiles, (int64_t)std::max(nsm, 1) * std::max(occ_plain, 1)));
+  return RAPDB_OK;
+}
+
 int64_t body_cap(const rapdb_params& p) {
   // every trial is one body; iterations <= max_iter, trials <= max_trials each,
   // plus set-up, restart and KKT bodies
@@ -775,6 +854,7 @@ void rapdb_default_params(rapdb_params* p, int32_t variant) {
   p->dual_set = RAPDB_DUAL_NONNEG;
   p->dual_radius = 1.0;
   p->restart_warm_tau = 0;
+  p->pack_sym = 0;
 }
 
 rapdb_status rapdb_create(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
@@ -833,8 +913,12 @@ rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_k
     if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tout, 8);
   }
   if (s == RAPDB_OK) s = finalize_ctx(ctx);
-  if (s == RAPDB_OK && p->rows_per_block == 0) s = pick_tile(ctx);
-  if (s == RAPDB_OK && p->rows_per_block > 0) ctx->pvar = p->pass_variant;
+  if (s == RAPDB_OK && p->pack_sym) {
+    s = setup_sym(ctx);
+  } else {
+    if (s == RAPDB_OK && p->rows_per_block == 0) s = pick_tile(ctx);
+    if (s == RAPDB_OK && p->rows_per_block > 0) ctx->pvar = p->pass_variant;
+  }
   if (s == RAPDB_OK) s = build_graph(ctx, 32);
   if (s != RAPDB_OK) {
     g_last_error = ctx->err;
@@ -858,6 +942,7 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
     if (s != RAPDB_OK) return s;
   }
   if (p->storage != RAPDB_F32) return fail(nullptr, RAPDB_ERR_INVALID, "batched contexts use F32 storage");
+  if (p->pack_sym) return fail(nullptr, RAPDB_ERR_INVALID, "pack_sym needs a single-instance context");
   for (int b = 0; b < B; ++b) {
     if (n[b] <= 0 || m[b] < 0 || m[b] > 12800 || n[b] > (1 << 24))
       return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes in batch");
@@ -1019,6 +1104,35 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx* ctx, const float* x, const float* v,
   return finish_standalone(ctx);
 }
 
+rapdb_status rapdb_packed_pass(rapdb_ctx* ctx, const float* x, const float* v, const float* uold, float* U,
+                               float* W, double* dots) {
+  NvtxScope nvtx_scope("rapdb_packed_pass");
+  if (!ctx || ctx->batched) return fail(ctx, RAPDB_ERR_INVALID, "single-instance context required");
+  const Inst& I = ctx->hi[0].I;
+  if (I.tsym == 0) return fail(ctx, RAPDB_ERR_INVALID, "the context has no packed tiles (pack_sym = 0)");
+  if (!x || !v || !uold || !U || !W) return fail(ctx, RAPDB_ERR_INVALID, "NULL argument");
+  cudaStream_t st = ctx->stream;
+  const size_t rowb = (size_t)I.n * 4, ldb = (size_t)I.ldv * 4;
+  float* xpad = ctx->txv;
+  float* vpad = ctx->txv + I.ldv;
+  CK(cudaMemcpyAsync(xpad, x, rowb, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(vpad, v, rowb, cudaMemcpyDeviceToDevice, st));
+  const size_t off = (size_t)I.s_off * I.ldv;
+  CK(cudaMemcpy2DAsync(ctx->tUo + off, ldb, uold, rowb, rowb, (size_t)I.M, cudaMemcpyDeviceToDevice, st));
+  k_sym_plain<0><<<ctx->sym_plain_grid, NT, 0, st>>>(ctx->d_inst, vpad, &ctx->d_ctrl->err);
+  k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, xpad, nullptr, vpad, ctx->tUo, nullptr, ctx->tU,
+                                                   nullptr, ctx->tW, I.spart);
+  if (dots) {
+    k_sym_dots<<<1, NT, 0, st>>>(ctx->d_inst, I.spart, ctx->tdots);
+    CK(cudaMemcpyAsync(dots, ctx->tdots + (size_t)I.s_off * NDOT, (size_t)I.M * NDOT * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpy2DAsync(U, rowb, ctx->tU + off, ldb, rowb, (size_t)I.M, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpy2DAsync(W, rowb, ctx->tW + off, ldb, rowb, (size_t)I.M, cudaMemcpyDeviceToDevice, st));
+  return finish_standalone(ctx);
+}
+
 rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, double* rel_kkt, double* r_stat,
                                 double* r_feas) {
   NvtxScope nvtx_scope("rapdb_kkt_residual");
@@ -1075,8 +1189,8 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     cur_level = ctx->h_state[0].precision;
   }
   const int lv = level < 0 ? cur_level : level;
-  if (lv > 3 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
-      (lv == 1 && I.storage == RAPDB_F32))
+  if (lv > 4 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
+      (lv == 1 && I.storage == RAPDB_F32) || (lv == 4 && I.tsym == 0))
     return fail(ctx, RAPDB_ERR_INVALID, "precision level not available in this context");
   const float* x = I.xf[xcur];
   const float* v = I.dv;
@@ -1084,9 +1198,14 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
-    launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS,
-                 lv == 2 ? nullptr : I.U[0],
-                 ctx->tU, ctx->tW, ctx->tpart, lv, &ctx->d_ctrl->err, I.xl[xcur], ctx->tUo);
+    if (lv == 4) {
+      k_sym_plain<0><<<ctx->sym_plain_grid, NT, 0, st>>>(ctx->d_inst, v, &ctx->d_ctrl->err);
+      k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, x, I.xl[xcur], v, I.U[0], I.Ulo[0], ctx->tU,
+                                                       ctx->tUo, ctx->tW, I.spart);
+    } else
+      launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS,
+                   lv == 2 ? nullptr : I.U[0],
+                   ctx->tU, ctx->tW, ctx->tpart, lv, &ctx->d_ctrl->err, I.xl[xcur], ctx->tUo);
   };
   launch();   // warm-up
   CK(cudaGetLastError());
@@ -1106,6 +1225,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     const int64_t eb = lv >= 1 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));
     int64_t b = (int64_t)I.M * I.n * I.n * eb;
     if (I.storage == RAPDB_FP8 && lv == 0) b += (int64_t)I.M * I.n * 4;
+    if (lv == 4) b = ctx->hi[0].qp_bytes;
     *bytes_per_pass = b;
   }
   return RAPDB_OK;

@@ -115,6 +115,13 @@ struct Inst {
   double* gnew;         // g(x~) of the current trial (m)
   double* part;         // (M, NDOT, nrb) pass partials
   unsigned int* mcount; // (M) per-matrix arrival counters of the pass
+  // symmetric block packing (pack_sym): the upper block triangle of each
+  // float32 Q_i in STB x STB tiles, read by the incremental trial passes
+  const float* Qp;      // (M, ntile, STB, STB) tiles, zero outside n x n; null: none
+  const int* tij;       // (ntile) tile coordinates I << 16 | J, I <= J, row-major
+  float* sp;            // (M, T, T * STB) tile products: slot J of the rows of block I
+  double* spart;        // (M, NDOT, T) row-block dot partials of the packed pass
+  int tsym, ntile;      // T = ceil(n / STB) (0: no packing), T (T + 1) / 2
   double* vpart;        // (ncb, NVP) vector partials
   double* dots;         // (m+1, NDOT) reduced dots
   double* xcum;         // averaging: sum t_k x^{k+1}  (ldv)

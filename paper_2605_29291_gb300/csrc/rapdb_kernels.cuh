@@ -50,7 +50,7 @@ __device__ __forceinline__ unsigned dyn_smem_bytes() {
   return v;
 }
 enum CheckCode : int { CHK_PASS_RANGE = 101, CHK_PASS_SMEM = 102, CHK_VEC_RANGE = 111, CHK_VEC_SMEM = 112,
-                       CHK_PLAIN_RANGE = 121 };
+                       CHK_PLAIN_RANGE = 121, CHK_SYM_RANGE = 131 };
 
 // Power iterations per smoothed-gap evaluation (first one / warm-started).
 constexpr int GAP_POWER_FIRST = 30;
@@ -837,21 +837,21 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
 // ---------------------------------------------------------------------------
 // k_pass: the fused coupling pass + post-control
 // ---------------------------------------------------------------------------
+static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, int i, const double* part, int nb,
+                                   int phase, bool comp, const float* x, const float* v, double* red, int& s_dec);
+
 template <int ST, int RPW, int UNR, int NST, int CWB>
-__global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __restrict__ insts,
-                                                                State* __restrict__ states,
-                                             Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
-                                             const float* __restrict__ XS, const float* __restrict__ VS) {
-  extern __shared__ __align__(128) uint8_t dsm[];
-  __shared__ double red[NWARP * NDOT];
-  __shared__ int s_dec;
-  const int b = pmap[blockIdx.x];
+__device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State* __restrict__ states,
+                                          Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
+                                          const float* __restrict__ XS, const float* __restrict__ VS, uint8_t* dsm,
+                                          double* red, int& s_dec, int bid) {
+  const int b = pmap[bid];
   const Inst& I = insts[b];
   State& S = states[b];
   const int phase = S.phase;
   if (!pass_phase(phase)) return;
   if (phase == PH_TRIAL && !S.trial_ready) return;   // no trial prepared in this body
-  const int item = blockIdx.x - I.pblk0;
+  const int item = bid - I.pblk0;
   const int s = item / I.nrb;
   const int r = item - s * I.nrb;
   const int i = s + I.s_off;
@@ -918,25 +918,45 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
                                       I.qscale ? I.qscale + (size_t)s * ldv : nullptr, uold, crow, Uo, Wo, out,
                                       I.nrb, red, dsm, &ctrl->err);
   }
-  // ---- last CTA of matrix s: fixed-order reduction of its row-block partials ----
-  if (!arrive_last(&I.mcount[s], (unsigned)I.nrb)) return;
+  pass_finish(I, S, ctrl, s, i, I.part, I.nrb, phase, comp, x, v, red, s_dec);
+}
+
+template <int ST, int RPW, int UNR, int NST, int CWB>
+__global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __restrict__ insts,
+                                                                State* __restrict__ states,
+                                                                Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
+                                                                const float* __restrict__ XS,
+                                                                const float* __restrict__ VS) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  __shared__ double red[NWARP * NDOT];
+  __shared__ int s_dec;
+  pass_body<ST, RPW, UNR, NST, CWB>(insts, states, ctrl, pmap, XS, VS, dsm, red, s_dec, blockIdx.x);
+}
+
+// After a CTA's share of a pass: the last arrival of matrix s reduces the
+// matrix's nb row-block dot partials (part, (M, NDOT, nb)) in a fixed order;
+// the last matrix of the instance runs the control step of the phase.
+static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, int i, const double* part, int nb,
+                                   int phase, bool comp, const float* x, const float* v, double* red, int& s_dec) {
+  if (!arrive_last(&I.mcount[s], (unsigned)nb)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < NDOT) {
-    const double* src = I.part + ((size_t)s * NDOT + warp) * I.nrb;
+    const double* src = part + ((size_t)s * NDOT + warp) * nb;
     double t = 0.0;
-    for (int rr = lane; rr < I.nrb; rr += 32) t += __ldcg(src + rr);
+    for (int rr = lane; rr < nb; rr += 32) t += __ldcg(src + rr);
     t = warp_sum(t);
     if (lane == 0) I.dots[(size_t)i * NDOT + warp] = t;
   }
   // ---- last matrix of the instance: control ----
   if (!arrive_last(&S.arrive_pass, (unsigned)I.M)) return;
   const int tid = threadIdx.x;
+  const int ldv = I.ldv;
   if (I.s_off && tid < NDOT) I.dots[tid] = S.dots0[tid];
   if (I.m > I.m_ineq && !gap_phase(phase)) {
     // linear equalities (no stored matrix): u = w = 0, c'x and c'v here
     const float* xlo_e = comp ? ((phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1]) : nullptr;
-    for (int i = I.m_ineq + 1; i <= I.m; ++i) {
-      const float* ci = I.c + (size_t)i * ldv;
+    for (int ie = I.m_ineq + 1; ie <= I.m; ++ie) {
+      const float* ci = I.c + (size_t)ie * ldv;
       double sv[2] = {0.0, 0.0};
       for (int jj = tid; jj < I.n; jj += NT) {
         const double xj = (double)x[jj] + (xlo_e ? (double)xlo_e[jj] : 0.0);
@@ -945,7 +965,7 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass(const Inst* __r
       }
       block_allsum<2>(sv, red);
       if (tid == 0) {
-        double* Di = I.dots + (size_t)i * NDOT;
+        double* Di = I.dots + (size_t)ie * NDOT;
         Di[D_XU] = 0.0;
         Di[D_VW] = 0.0;
         Di[D_VUO] = 0.0;
@@ -1121,3 +1141,5 @@ __global__ void __launch_bounds__(NT, (NST <= 0 ? 2 : 1)) k_pass_plain(const Ins
 }
 
 }  // namespace rapdb_dev
+
+#include "rapdb_sym.cuh"

@@ -44,7 +44,10 @@ inline size_t var_smem(int vi) {
                          const float* XS, const float* VS);                                                       \
   void launch_plain_##SUF(int vi, dim3 g, cudaStream_t s, const Inst* I, const float* x, const float* v,          \
                           const float* XS, const float* VS, const float* uold, float* U, float* W, double* part,  \
-                          int level, const float* xlo, float* Ulo, int* err);
+                          int level, const float* xlo, float* Ulo, int* err);                                     \
+  void launch_pass_sym_##SUF(dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const int* pm,             \
+                             const float* XS, const float* VS);                                                   \
+  int pass_sym_occupancy_##SUF();
 
 RAPDB_DECLARE_LAUNCHERS(f32)
 RAPDB_DECLARE_LAUNCHERS(bf16)

@@ -51,6 +51,70 @@ __global__ void k_quant_fp8(const float* __restrict__ Q, int n, int M, int ld, i
   }
 }
 
+// ---- symmetric block packing ------------------------------------------------
+// flag = 1 when some Q_s[j][k] != Q_s[k][j]: 32 x 32 blocks (bi, bj), bi <= bj,
+// the mirror block staged through shared memory so both reads coalesce.
+__global__ void k_sym_check(const float* __restrict__ Q, int ld, int n, int M, int* flag) {
+  __shared__ float a[32][33];
+  const int nb = (n + 31) / 32;
+  const int64_t total = (int64_t)M * nb * nb;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int s = (int)(b / ((int64_t)nb * nb));
+    const int rem = (int)(b - (int64_t)s * nb * nb);
+    const int bi = rem / nb, bj = rem - bi * nb;
+    if (bi > bj) continue;     // uniform over the CTA
+    const float* Qs = Q + (size_t)s * n * ld;
+    for (int r = ty; r < 32; r += 8) {
+      const int row = bj * 32 + r, col = bi * 32 + tx;
+      a[r][tx] = (row < n && col < n) ? Qs[(size_t)row * ld + col] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int row = bi * 32 + r, col = bj * 32 + tx;
+      if (row < n && col < n && Qs[(size_t)row * ld + col] != a[tx][r]) atomicOr(flag, 1);
+    }
+    __syncthreads();
+  }
+}
+
+// Qp[s][t] = Q_s[I*STB .. , J*STB .. ] for tile t = (I, J) of tij, zero
+// outside n x n.
+__global__ void k_pack_sym(const float* __restrict__ Q, int ld, int n, int M, int T, int ntile,
+                           const int* __restrict__ tij, float* __restrict__ Qp) {
+  const int64_t total = (int64_t)M * ntile * STB * STB;
+  (void)T;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % STB);
+    const int r = (int)((e / STB) % STB);
+    const int64_t st = e / ((int64_t)STB * STB);
+    const int t = (int)(st % ntile);
+    const int s = (int)(st / ntile);
+    const int ij = tij[t];
+    const int row = (ij >> 16) * STB + r, col = (ij & 0xffff) * STB + c;
+    Qp[e] = (row < n && col < n) ? Q[(size_t)s * n * ld + (size_t)row * ld + col] : 0.f;
+  }
+}
+
+// dots[(s + s_off) * NDOT + q] = sum over the T row blocks of spart[s][q][.]
+// (the same fixed order as the solver's per-matrix reduction).
+__global__ void __launch_bounds__(NT) k_sym_dots(const Inst* __restrict__ insts, const double* __restrict__ spart,
+                                                double* __restrict__ dots) {
+  const Inst& I = insts[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int T = I.tsym;
+  for (int pq = warp; pq < I.M * NDOT; pq += NWARP) {
+    const double* src = spart + (size_t)pq * T;
+    double t = 0.0;
+    for (int rr = lane; rr < T; rr += 32) t += src[rr];
+    t = warp_sum(t);
+    if (lane == 0) {
+      const int ss = pq / NDOT, q = pq - ss * NDOT;
+      dots[(size_t)(ss + I.s_off) * NDOT + q] = t;
+    }
+  }
+}
+
 // ---- validation: NaN / Inf anywhere, negative diagonal, lb > ub ----------
 __global__ void k_validate(const float* __restrict__ Q, int n, int M, const float* __restrict__ c, int m,
                            const float* __restrict__ d, const float* __restrict__ lb,

@@ -37,6 +37,7 @@ class CParams(C.Structure):
         ("tol", C.c_double), ("time_limit_s", C.c_double),
         ("rows_per_block", C.c_int32), ("gap_inner_max", C.c_int32), ("pass_variant", C.c_int32),
         ("dual_set", C.c_int32), ("dual_radius", C.c_double), ("restart_warm_tau", C.c_int32),
+        ("pack_sym", C.c_int32),
     ]
 
 
@@ -64,6 +65,7 @@ def _load():
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
         "rapdb_coupling_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
+        "rapdb_packed_pass": (C.c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "rapdb_set_log": (C.c_int, [vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "rapdb_create_batched": (C.c_int, [ctxpp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                            C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
@@ -133,6 +135,7 @@ class Params:
     dual_set: int = 0
     dual_radius: float = 1.0
     restart_warm_tau: int = 0
+    pack_sym: int = 0
 
     @classmethod
     def default(cls, variant: int = YX, **kw) -> "Params":
@@ -239,6 +242,19 @@ class Solver:
                self.ctx)
         return U, W, dots
 
+    def packed_pass(self, x, v, uold):
+        """The packed incremental pass of a pack_sym context for the M stored
+        matrices: W[s] = Q_i v, U[s] = uold[s] + W[s] and the (M, 5) float64
+        dots (x'U, v'W, v'uold, c'x, c'v)."""
+        import torch
+        M = int(uold.shape[0])
+        U = torch.empty((M, self.n), dtype=torch.float32, device=self.device)
+        W = torch.empty_like(U)
+        dots = torch.empty((M, 5), dtype=torch.float64, device=self.device)
+        _check(lib.rapdb_packed_pass(self.ctx, _ptr(x), _ptr(v), _ptr(uold), _ptr(U), _ptr(W), _ptr(dots)),
+               self.ctx)
+        return U, W, dots
+
     def set_log(self, capacity: int, iterates: bool = True):
         """Record tau_k, trials, KKT residuals, smoothed gaps, f(x^{k+1}) and
         the mean constraint violation of the first `capacity` iterations, and
@@ -288,7 +304,8 @@ class Solver:
     def time_pass(self, reps: int = 20, level: int = -1):
         """(average ms per coupling-pass launch, algorithmic bytes per pass) at a
         precision level (-1: where the last solve ended, 0 stored Q, 1 float32 Q,
-        2 compensated float32 products)."""
+        2 compensated float32 products, 3 their incremental form, 4 the
+        incremental form through the packed tiles of a pack_sym context)."""
         ms, b = C.c_double(), C.c_int64()
         _check(lib.rapdb_time_pass(self.ctx, reps, level, C.byref(ms), C.byref(b)), self.ctx)
         return ms.value, b.value

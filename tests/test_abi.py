@@ -39,7 +39,8 @@ def test_binding_loads_and_mirrors_defaults():
     assert (xy.c_alpha, xy.c_beta, xy.delta) == (gp["xy"]["c_alpha"], gp["xy"]["c_beta"], gp["xy"]["delta"])
     assert yx.xi == gp["xi"]["value"] and yx.q == gp["q"]["value"]
     assert yx.gap_first == gp["gap_first"]["yx"] and xy.gap_first == gp["gap_first"]["xy"]
-    # struct layout: the ctypes mirror must match the C struct size
+    # struct layout: the ctypes mirror must match the C struct size (the last
+    # 8 bytes: restart_warm_tau and pack_sym)
     assert ctypes.sizeof(R.CParams) == 4 * 4 + 7 * 8 + 2 * 4 + 2 * 8 + 2 * 4 + 2 * 4 + 8 + 4 * 4 + 2 * 8 + 2 * 4 + 8 + 8 + 8
 
 
@@ -72,4 +73,25 @@ def test_params_struct_matches_the_library_layout():
     assert all(b == 0xAB for b in bytes(buf)[size:])
     p = R.CParams.from_buffer_copy(bytes(buf)[:size])
     assert p.dual_set == R.DUAL_NONNEG and p.dual_radius == 1.0 and p.pass_variant == 0
-    assert p.restart_warm_tau == 0
+    assert p.restart_warm_tau == 0 and p.pack_sym == 0
+
+
+def test_pack_sym_argument_checks_without_touching_the_gpu():
+    """pack_sym needs refine = 1 and a single-instance context; both are
+    refused before any device call (the data pointers are never read)."""
+    from paper_2605_29291_gb300 import rapdb as R
+    dummy = (ctypes.c_float * 16)()
+    ptr = ctypes.cast(dummy, ctypes.c_void_p)
+    ctx = ctypes.c_void_p()
+    p = R.Params.default(pack_sym=1, refine=0).to_c()
+    st = R.lib.rapdb_create(ctypes.byref(ctx), 4, 1, 0, ptr, None, ptr, ptr, ptr, ptr, ctypes.byref(p), None)
+    assert st == R.ERR_INVALID and b"refine" in R.lib.rapdb_last_error(None)
+    p = R.Params.default(pack_sym=2).to_c()
+    st = R.lib.rapdb_create(ctypes.byref(ctx), 4, 1, 0, ptr, None, ptr, ptr, ptr, ptr, ctypes.byref(p), None)
+    assert st == R.ERR_INVALID and b"pack_sym" in R.lib.rapdb_last_error(None)
+    p = R.Params.default(pack_sym=1).to_c()
+    n = (ctypes.c_int64 * 1)(4)
+    m = (ctypes.c_int64 * 1)(1)
+    arr = (ctypes.c_void_p * 1)(ptr.value)
+    st = R.lib.rapdb_create_batched(ctypes.byref(ctx), 1, n, m, arr, arr, arr, arr, arr, ctypes.byref(p), None)
+    assert st == R.ERR_INVALID and b"single-instance" in R.lib.rapdb_last_error(None)
