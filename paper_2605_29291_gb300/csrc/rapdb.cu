@@ -69,8 +69,8 @@ struct rapdb_ctx {
   int g_bodies = 0;
   int64_t launches = 0;        // kernels launched by the current call
   int pvar = 0;                // coupling-pass tile variant (kVarRPW / kVarUNR)
-  int sym_grid = 0;            // pack_sym: CTAs of the solver's pass kernel (one resident wave)
-  int sym_plain_grid = 0;      // ... and of the stand-alone packed pass
+  int sym_grid = 0;            // pack_sym: CTAs of the row-streaming pass kernel (one resident wave)
+  int sym_tile_grid = 0;       // ... and of the packed tile kernels (one CTA per SM)
   float tune_ms = 0.0f;        // autotuner: best pass time
   State* h_state = nullptr;    // pinned
   Ctrl* h_ctrl = nullptr;      // pinned, 2 slots
@@ -543,6 +543,7 @@ rapdb_status launch_body(rapdb_ctx* ctx, cudaStream_t s) {
     const Inst& I = ctx->hi[0].I;
     launch_pass_sym(st, dim3(ctx->sym_grid), s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS,
                     ctx->VS);
+    k_sym_tiles<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
     k_sym_finish<0><<<I.M * I.tsym, NT, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
   } else if (ctx->npblk > 0)
     launch_pass(st, ctx->pvar, gp, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
@@ -785,20 +786,25 @@ rapdb_status finish_standalone(rapdb_ctx* ctx) {
   return RAPDB_OK;
 }
 
-// pack_sym contexts: tile variant 1 for the row-streaming passes, and one
-// resident wave of CTAs (at most one per tile) for the pass kernels.
+// pack_sym contexts: tile variant 1 for the row-streaming passes, one
+// resident wave of CTAs for their kernel, and one CTA per SM (at most one per
+// tile) for the packed tile kernels, with their shared-memory stages.
 rapdb_status setup_sym(rapdb_ctx* ctx) {
   const Inst& I = ctx->hi[0].I;
   int dev = 0, nsm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int occ_plain = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, k_sym_plain<0>, NT, 0));
+  CK(cudaFuncSetAttribute(k_sym_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes()));
+  CK(cudaFuncSetAttribute(k_sym_plain<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes()));
+  int occ_tiles = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tiles, k_sym_tiles<0>, NTS, sym_smem_bytes()));
+  if (occ_tiles < 1) return fail(ctx, RAPDB_ERR_CUDA, "the packed tile kernel does not fit on an SM");
   const int64_t tiles = (int64_t)I.M * I.ntile;
-  const int64_t wave = (int64_t)std::max(nsm, 1) * pass_sym_occupancy(ctx->storage);
+  const int64_t items = (int64_t)I.M * I.nrb;
   ctx->pvar = 1;
-  ctx->sym_grid = (int)std::max<int64_t>(1, std::min(tiles, wave));
-  ctx->sym_plain_grid = (int)std::max<int64_t>(1, std::min(tiles, (int64_t)std::max(nsm, 1) * std::max(occ_plain, 1)));
+  ctx->sym_grid = (int)std::max<int64_t>(
+      1, std::min(items, (int64_t)std::max(nsm, 1) * pass_sym_occupancy(ctx->storage)));
+  ctx->sym_tile_grid = (int)std::max<int64_t>(1, std::min(tiles, (int64_t)std::max(nsm, 1) * occ_tiles));
   return RAPDB_OK;
 }
 
@@ -1119,7 +1125,7 @@ rapdb_status rapdb_packed_pass(rapdb_ctx* ctx, const float* x, const float* v, c
   CK(cudaMemcpyAsync(vpad, v, rowb, cudaMemcpyDeviceToDevice, st));
   const size_t off = (size_t)I.s_off * I.ldv;
   CK(cudaMemcpy2DAsync(ctx->tUo + off, ldb, uold, rowb, rowb, (size_t)I.M, cudaMemcpyDeviceToDevice, st));
-  k_sym_plain<0><<<ctx->sym_plain_grid, NT, 0, st>>>(ctx->d_inst, vpad, &ctx->d_ctrl->err);
+  k_sym_plain<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), st>>>(ctx->d_inst, vpad, &ctx->d_ctrl->err);
   k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, xpad, nullptr, vpad, ctx->tUo, nullptr, ctx->tU,
                                                    nullptr, ctx->tW, I.spart);
   if (dots) {
@@ -1199,7 +1205,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
     if (lv == 4) {
-      k_sym_plain<0><<<ctx->sym_plain_grid, NT, 0, st>>>(ctx->d_inst, v, &ctx->d_ctrl->err);
+      k_sym_plain<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), st>>>(ctx->d_inst, v, &ctx->d_ctrl->err);
       k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, x, I.xl[xcur], v, I.U[0], I.Ulo[0], ctx->tU,
                                                        ctx->tUo, ctx->tW, I.spart);
     } else

@@ -27,67 +27,121 @@
 namespace rapdb_dev {
 
 constexpr int STB = 128;             // tile edge (rows of a row block)
-constexpr int SRW = STB / NWARP;     // tile rows per warp
 static_assert(NT == 2 * STB, "the row-block reduction splits the T slots over two halves of the CTA");
-static_assert(SRW == 16, "warp_rows16 reduces 16 rows per warp");
-static_assert(STB == 32 * 4, "one float4 column slice per lane");
 
 // The incremental compensated trial pass (the phase the packed tiles serve).
 __device__ __forceinline__ bool sym_phase(const Inst& I, const State& S) {
   return I.tsym > 0 && S.phase == PH_TRIAL && S.trial_ready && S.precision == 2 && S.anchor_age < ANCHOR_EVERY;
 }
 
-// Issue the SRW 16-byte loads of this thread's share of a tile: warp w reads
-// rows w*SRW .. w*SRW+SRW-1, lane l columns 4l .. 4l+3 (each row one 512-byte
-// coalesced load per warp).
-__device__ __forceinline__ void sym_load(const float* tile, uint4 (&raw)[SRW]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint8_t* p = reinterpret_cast<const uint8_t*>(tile + (size_t)warp * SRW * STB + lane * 4);
-#pragma unroll
-  for (int q = 0; q < SRW; ++q) raw[q] = ld_stream16(p + (size_t)q * STB * 4);
+// Row block R of stored matrix s (constraint row i) is complete: sum its T
+// slots in slot order, apply the incremental update and write the block's dot
+// partials to out[q * T].  The slot sums are compensated float32 sums
+// (Knuth's TwoSum per addition, the rounding errors summed alongside): within
+// 2u of the exact sum plus O(T^2 u^2) of the sum of |slots|, with no float64
+// work (float64 runs at a small fraction of the float32 rate on this GPU).
+// The two halves of the CTA take half the slots each; the low half's sum
+// absorbs the high half's with one more TwoSum.  The update and the five dots
+// are float64; the dots are summed over the 128 rows through shared memory
+// (four rows per lane, then a fixed warp tree).  xl, uol and Uol may be null
+// (zero low parts, no low output).  `sh` = NDOT x STB doubles.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float a) {
+  const float t = s + a;
+  const float z = t - s;
+  c += (s - (t - z)) + (a - z);
+  s = t;
 }
 
-// Row partials rp[q] = B[q, 4l..4l+3] . d_J[4l..4l+3] and column partials
-// cp[e] = sum_q d_I[q] B[q, 4l+e] of this thread's share of tile (I, J).
-__device__ __forceinline__ void sym_compute(const uint4 (&raw)[SRW], int TI, int TJ, int n,
-                                            const float* __restrict__ v, float (&rp)[SRW], float (&cp)[4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = TJ * STB + lane * 4;
-  float dj[4];
-  if (c0 + 4 <= n) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(v + c0));
-    dj[0] = t.x; dj[1] = t.y; dj[2] = t.z; dj[3] = t.w;
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dj[e] = (c0 + e < n) ? __ldg(v + c0 + e) : 0.f;
+static __device__ void sym_rows(const Inst& I, const float* __restrict__ Ps, int R, int i,
+                                const float* __restrict__ x, const float* __restrict__ xl,
+                                const float* __restrict__ v, const float* __restrict__ uoh,
+                                const float* __restrict__ uol, float* __restrict__ Uoh, float* __restrict__ Uol,
+                                float* __restrict__ W, double* __restrict__ out, double* sh) {
+  const int T = I.tsym;
+  const size_t ldp = (size_t)T * STB;
+  const int tid = threadIdx.x, t = tid & (STB - 1), half = tid / STB;
+  const int h = T / 2;
+  const int s0 = half ? h : 0, s1 = half ? T : h;
+  const float* src = Ps + (size_t)R * STB + t;
+  float sa = 0.f, ca = 0.f;
+#pragma unroll 8
+  for (int sl = s0; sl < s1; ++sl) two_sum_acc(sa, ca, __ldcg(src + (size_t)sl * ldp));
+  float2* shf = reinterpret_cast<float2*>(sh);
+  if (half) shf[t] = make_float2(sa, ca);
+  __syncthreads();
+  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int j = R * STB + t;
+  if (!half) {
+    const float2 hi = shf[t];
+    two_sum_acc(sa, ca, hi.x);
+    ca += hi.y;
+    if (j < I.n) {
+      const double w = (double)sa + (double)ca;
+      const size_t o = (size_t)i * I.ldv + j;
+      const double uo = (double)uoh[o] + (uol ? (double)uol[o] : 0.0);
+      const double u = uo + w;
+      const float uh = (float)u;
+      Uoh[o] = uh;
+      if (Uol) Uol[o] = (float)(u - (double)uh);
+      W[o] = (float)w;
+      const double xj = (double)x[j] + (xl ? (double)xl[j] : 0.0), vj = v[j], cj = I.c[o];
+      dsum[0] = xj * u;
+      dsum[1] = vj * w;
+      dsum[2] = vj * uo;
+      dsum[3] = cj * xj;
+      dsum[4] = cj * vj;
+    }
   }
-  const int r0 = TI * STB + warp * SRW;
-  const float dil = (lane < SRW && r0 + lane < n) ? __ldg(v + r0 + lane) : 0.f;
+  __syncthreads();   // shf is read
+  if (!half) {
 #pragma unroll
-  for (int e = 0; e < 4; ++e) cp[e] = 0.f;
-#pragma unroll
-  for (int q = 0; q < SRW; ++q) {
-    const float b0 = __uint_as_float(raw[q].x), b1 = __uint_as_float(raw[q].y);
-    const float b2 = __uint_as_float(raw[q].z), b3 = __uint_as_float(raw[q].w);
-    rp[q] = fmaf(b3, dj[3], fmaf(b2, dj[2], fmaf(b1, dj[1], b0 * dj[0])));
-    const float di = __shfl_sync(0xffffffffu, dil, q);
-    cp[0] = fmaf(b0, di, cp[0]);
-    cp[1] = fmaf(b1, di, cp[1]);
-    cp[2] = fmaf(b2, di, cp[2]);
-    cp[3] = fmaf(b3, di, cp[3]);
+    for (int q = 0; q < NDOT; ++q) sh[q * STB + t] = dsum[q];
   }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  if (warp < NDOT) {
+    const double* r = sh + warp * STB;
+    double a = r[lane];
+#pragma unroll
+    for (int k = 1; k < STB / 32; ++k) a += r[lane + 32 * k];
+    a = warp_sum(a);
+    if (lane == 0) out[(size_t)warp * T] = a;
+  }
+  __syncthreads();   // sh is reused by the caller
 }
 
-// Sum of a[0..15] over the warp's 32 lanes by halving: at each step a lane
-// keeps half of its rows and adds its partner's copy of them.  Lane l returns
-// the sum for row sym_row(l); lanes l and l ^ 1 return the same value.
-__device__ __forceinline__ int sym_row(int lane) {
-  return 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+// One CTA's share of the tile products of a packed pass: tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the (M x ntile) list.  Each 64 KB tile is
+// contiguous: one bulk copy (TMA unit) moves it into a shared-memory stage,
+// SNST stages in flight, completed on the stage's mbarrier.  The CTA has
+// NTS = 512 threads: warp w takes rows 8w .. 8w+7 of the tile, lane l columns
+// 4l .. 4l+3 (row partials halved over the lanes, column partials summed over
+// the 16 warps in order: at most 8 + 15 float32 roundings per partial).  The
+// stage is refilled as soon as all threads have read it, and the next tile's
+// d slices are loaded while the current tile is reduced.  No counters and no
+// global fences: the row-block reduction runs in the next kernel.  Every wait
+// is bounded; on a timeout the CTA sets *err, waits (bounded) for its copies
+// in flight and returns.
+// `dsm` = [SNST mbarriers (128 B) | NWS x STB floats | SNST x 64 KB stages].
+constexpr int NTS = 512;
+constexpr int NWS = NTS / 32;
+constexpr int SRW8 = STB / NWS;      // tile rows per warp (8)
+static_assert(SRW8 == 8, "warp_rows8 reduces 8 rows per warp");
+constexpr int SNST = 3;
+constexpr uint32_t STILE = (uint32_t)STB * STB * 4;
+__host__ __device__ constexpr size_t sym_smem_bytes() {
+  return (size_t)128 + (size_t)NWS * STB * 4 + (size_t)SNST * STILE;
 }
-__device__ __forceinline__ float warp_rows16(float (&a)[SRW]) {
+
+// Lane l returns the sum over the 32 lanes of a[r] for r = sym_row8(l) (the
+// four lanes that share l >> 2 return the same value).
+__device__ __forceinline__ int sym_row8(int lane) {
+  return 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+}
+__device__ __forceinline__ float warp_rows8(float (&a)[SRW8]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+  for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
     const bool hi = (lane & o) != 0;
 #pragma unroll
     for (int k = 0; k < h; ++k) {
@@ -96,112 +150,157 @@ __device__ __forceinline__ float warp_rows16(float (&a)[SRW]) {
       a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+  float r = a[0] + __shfl_xor_sync(0xffffffffu, a[0], 2);
+  return r + __shfl_xor_sync(0xffffffffu, r, 1);
 }
 
-// Row block R of stored matrix s (constraint row i) is complete: sum its T
-// slots in slot order (float64; the two halves of the CTA take half the slots
-// each, added low half first), apply the incremental update and write the
-// block's dot partials to out[q * T].  xl, uol and Uol may be null (zero low
-// parts, no low output).
-static __device__ void sym_rows(const Inst& I, const float* __restrict__ Ps, int R, int i,
-                                const float* __restrict__ x, const float* __restrict__ xl,
-                                const float* __restrict__ v, const float* __restrict__ uoh,
-                                const float* __restrict__ uol, float* __restrict__ Uoh, float* __restrict__ Uol,
-                                float* __restrict__ W, double* __restrict__ out, double* sh, double* red) {
-  const int T = I.tsym;
-  const size_t ldp = (size_t)T * STB;
-  const int tid = threadIdx.x, t = tid & (STB - 1), half = tid / STB;
-  const int h = T / 2;
-  const int s0 = half ? h : 0, s1 = half ? T : h;
-  const float* src = Ps + (size_t)R * STB + t;
-  double w = 0.0;
-#pragma unroll 4
-  for (int sl = s0; sl < s1; ++sl) w += (double)__ldcg(src + (size_t)sl * ldp);
-  if (half) sh[t] = w;
-  __syncthreads();
-  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const int j = R * STB + t;
-  if (!half && j < I.n) {
-    w += sh[t];
-    const size_t o = (size_t)i * I.ldv + j;
-    const double uo = (double)uoh[o] + (uol ? (double)uol[o] : 0.0);
-    const double u = uo + w;
-    const float uh = (float)u;
-    Uoh[o] = uh;
-    if (Uol) Uol[o] = (float)(u - (double)uh);
-    W[o] = (float)w;
-    const double xj = (double)x[j] + (xl ? (double)xl[j] : 0.0), vj = v[j], cj = I.c[o];
-    dsum[0] = xj * u;
-    dsum[1] = vj * w;
-    dsum[2] = vj * uo;
-    dsum[3] = cj * xj;
-    dsum[4] = cj * vj;
-  }
-  block_sum<NDOT>(dsum, red);
-  if (tid == 0) {
+// The d slices a thread needs for tile (TI, TJ): d_J[4l .. 4l+3] and, in lanes
+// 0..7, d_I of row 8w + lane (zero past n).
+__device__ __forceinline__ void sym_dslices(const float* __restrict__ v, int n, int TI, int TJ, float (&dj)[4],
+                                            float& dil) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = TJ * STB + lane * 4;
+  if (c0 + 4 <= n) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(v + c0));
+    dj[0] = t.x; dj[1] = t.y; dj[2] = t.z; dj[3] = t.w;
+  } else {
 #pragma unroll
-    for (int q = 0; q < NDOT; ++q) out[(size_t)q * T] = dsum[q];
+    for (int e = 0; e < 4; ++e) dj[e] = (c0 + e < n) ? __ldg(v + c0 + e) : 0.f;
   }
+  const int r = TI * STB + warp * SRW8 + lane;
+  dil = (lane < SRW8 && r < n) ? __ldg(v + r) : 0.f;
 }
 
-// One CTA's share of the tile products of a packed pass: tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... of the (M x ntile) list, the loads of the next
-// tile in flight while the current one is reduced and stored.  No counters
-// and no fences: the row-block reduction runs in the next kernel.
-__device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict__ v, float* sred, int* err) {
+__device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict__ v, uint8_t* dsm, int* err) {
   const int T = I.tsym, nt = I.ntile;
   const size_t ldp = (size_t)T * STB;
   const int total = I.M * nt;
-  int it = blockIdx.x;
-  if (it >= total) return;
+  const int first = blockIdx.x, G = gridDim.x;
+  if (first >= total) return;
+  const int K = (total - first + G - 1) / G;          // tiles of this CTA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-  uint4 raw[SRW];
-  sym_load(I.Qp + (size_t)it * STB * STB, raw);
-  for (;;) {
-    const int s = it / nt, t = it - s * nt;
-    const int ij = __ldg(I.tij + t);
-    const int TI = ij >> 16, TJ = ij & 0xffff;
-#ifdef RAPDB_CHECKED
-    if (!(TI >= 0 && TI <= TJ && TJ < T)) {
-      if (tid == 0 && err) atomicCAS(err, 0, CHK_SYM_RANGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
+  float* sred = reinterpret_cast<float*>(dsm + 128);
+  uint8_t* stg = dsm + 128 + (size_t)NWS * STB * 4;
+  if (tid == 0) {
+    for (int k = 0; k < SNST; ++k) mbar_init(&full[k], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  // the tiles are read once per pass: first out of L2, so that the slot
+  // partials stay there for the row-block kernel
+  const uint64_t pol = l2_policy_evict_first();
+  auto issue = [&](int k) {   // thread 0: tile k of this CTA -> stage k % SNST
+    const int st = k % SNST;
+    const size_t it = (size_t)first + (size_t)k * G;
+    mbar_expect_tx(&full[st], STILE);
+    bulk_g2s_evict_first(stg + (size_t)st * STILE, I.Qp + it * STB * STB, STILE, &full[st], pol);
+  };
+  if (tid == 0)
+    for (int k = 0; k < SNST && k < K; ++k) issue(k);
+  auto coords = [&](int k, int& s, int& TI, int& TJ) {
+    const int it = first + k * G;
+    s = it / nt;
+    const int ij = __ldg(I.tij + (it - s * nt));
+    TI = ij >> 16;
+    TJ = ij & 0xffff;
+  };
+  int s, TI, TJ;
+  coords(0, s, TI, TJ);
+  float dj[4], dil;
+  sym_dslices(v, I.n, TI, TJ, dj, dil);
+  for (int k = 0; k < K; ++k) {
+    const int st = k % SNST;
+    const bool got = mbar_wait_bounded(&full[st], (uint32_t)((k / SNST) & 1), err);
+    if (!__syncthreads_and(got)) {
+      if (tid == 0)
+        for (int k2 = k; k2 < K && k2 < k + SNST; ++k2)
+          mbar_wait_bounded(&full[k2 % SNST], (uint32_t)((k2 / SNST) & 1), err);
+      __syncthreads();
       return;
     }
-#else
-    (void)err;
+#ifdef RAPDB_CHECKED
+    if (!__syncthreads_and(TI >= 0 && TI <= TJ && TJ < T)) {
+      if (tid == 0) {
+        if (err) atomicCAS(err, 0, CHK_SYM_RANGE);
+        for (int k2 = k + 1; k2 < K && k2 < k + SNST; ++k2)
+          mbar_wait_bounded(&full[k2 % SNST], (uint32_t)((k2 / SNST) & 1), err);
+      }
+      __syncthreads();
+      return;
+    }
 #endif
-    float rp[SRW], cp[4];
-    sym_compute(raw, TI, TJ, I.n, v, rp, cp);
-    const int nx = it + gridDim.x;
-    if (nx < total) sym_load(I.Qp + (size_t)nx * STB * STB, raw);
-    float* Ps = I.sp + (size_t)s * T * ldp;
-    const float rv = warp_rows16(rp);
-    if (!(lane & 1)) Ps[(size_t)TJ * ldp + (size_t)TI * STB + warp * SRW + sym_row(lane)] = rv;
-    if (TI != TJ) {
+    // this thread's share of the tile: rows 8w .. 8w+7, columns 4l .. 4l+3
+    float rp[SRW8], cp[4] = {0.f, 0.f, 0.f, 0.f};
+    {
+      const uint8_t* sp = stg + (size_t)st * STILE + ((size_t)warp * SRW8 * STB + lane * 4) * 4;
+      uint4 raw[SRW8];
+#pragma unroll
+      for (int q = 0; q < SRW8; ++q) raw[q] = *reinterpret_cast<const uint4*>(sp + (size_t)q * STB * 4);
+#pragma unroll
+      for (int q = 0; q < SRW8; ++q) {
+        const float b0 = __uint_as_float(raw[q].x), b1 = __uint_as_float(raw[q].y);
+        const float b2 = __uint_as_float(raw[q].z), b3 = __uint_as_float(raw[q].w);
+        rp[q] = fmaf(b3, dj[3], fmaf(b2, dj[2], fmaf(b1, dj[1], b0 * dj[0])));
+        const float di = __shfl_sync(0xffffffffu, dil, q);
+        cp[0] = fmaf(b0, di, cp[0]);
+        cp[1] = fmaf(b1, di, cp[1]);
+        cp[2] = fmaf(b2, di, cp[2]);
+        cp[3] = fmaf(b3, di, cp[3]);
+      }
+    }
+    __syncthreads();   // the stage is consumed (and sred of the previous tile read)
+    if (tid == 0 && k + SNST < K) {
+      fence_proxy_async();
+      issue(k + SNST);
+    }
+    const int cs = s, cI = TI, cJ = TJ;
+    if (k + 1 < K) {   // the next tile's d slices, in flight during the reduction
+      coords(k + 1, s, TI, TJ);
+      sym_dslices(v, I.n, TI, TJ, dj, dil);
+    }
+    float* Ps = I.sp + (size_t)cs * T * ldp;
+    const float rv = warp_rows8(rp);
+    if (!(lane & 3)) Ps[(size_t)cJ * ldp + (size_t)cI * STB + warp * SRW8 + sym_row8(lane)] = rv;
+    if (cI != cJ) {
       *reinterpret_cast<float4*>(sred + warp * STB + lane * 4) = make_float4(cp[0], cp[1], cp[2], cp[3]);
       __syncthreads();
       if (tid < STB) {
         float c = sred[tid];
 #pragma unroll
-        for (int w = 1; w < NWARP; ++w) c += sred[w * STB + tid];
-        Ps[(size_t)TI * ldp + (size_t)TJ * STB + tid] = c;
+        for (int w = 1; w < NWS; ++w) c += sred[w * STB + tid];
+        Ps[(size_t)cI * ldp + (size_t)cJ * STB + tid] = c;
       }
-      __syncthreads();     // sred is rewritten by the next tile
     }
-    if (nx >= total) break;
-    it = nx;
   }
 }
 
-// The solver's coupling pass on a context with packed tiles: the tile
-// products of the packed incremental trial pass when the phase is one (the
-// row blocks, dots and control follow in k_sym_finish), otherwise the
-// row-streaming pass (tile variant 1: 4 rows x 4 chunks per warp) with each
-// CTA taking the row-block items blockIdx.x, blockIdx.x + gridDim.x, ...  A
-// CTA reaches the row pass's control step only in its last item (the step
-// needs all other items to have arrived), and a CTA that owns no item returns
-// whatever state it reads: the state a control step leaves is never a packed
-// trial (only the vector kernel sets trial_ready).
+// The tile products of the packed incremental trial pass (outside such a
+// phase every CTA returns at once; the row blocks, dots and control follow in
+// k_sym_finish).  One persistent CTA per SM.
+template <int DUMMY>
+__global__ void __launch_bounds__(NTS, 1) k_sym_tiles(const Inst* __restrict__ insts, const State* __restrict__ states,
+                                                     Ctrl* __restrict__ ctrl) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  const Inst& I = insts[0];
+  if (!sym_phase(I, states[0])) return;
+#ifdef RAPDB_CHECKED
+  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes()) {
+    if (threadIdx.x == 0) atomicCAS(&ctrl->err, 0, CHK_SYM_RANGE);
+    return;
+  }
+#endif
+  sym_tiles(I, I.dv, dsm, &ctrl->err);
+}
+
+// The row-streaming coupling pass of a context with packed tiles (tile
+// variant 1: 4 rows x 4 chunks per warp), each CTA taking the row-block
+// items blockIdx.x, blockIdx.x + gridDim.x, ...; in a packed trial every CTA
+// returns at once (k_sym_tiles runs it).  A CTA reaches the control step only
+// in its last item (the step needs all other items to have arrived), and a
+// CTA that owns no item returns whatever state it reads: the state a control
+// step leaves is never a packed trial (only the vector kernel sets
+// trial_ready).
 template <int ST>
 __global__ void __launch_bounds__(NT, 2) k_pass_sym(const Inst* __restrict__ insts, State* __restrict__ states,
                                                     Ctrl* __restrict__ ctrl, const int* __restrict__ pmap,
@@ -209,13 +308,8 @@ __global__ void __launch_bounds__(NT, 2) k_pass_sym(const Inst* __restrict__ ins
   extern __shared__ __align__(128) uint8_t dsm[];
   __shared__ double red[NWARP * NDOT];
   __shared__ int s_dec;
-  __shared__ __align__(16) float sred[NWARP * STB];
   const Inst& I = insts[0];
-  State& S = states[0];
-  if (sym_phase(I, S)) {
-    sym_tiles(I, I.dv, sred, &ctrl->err);
-    return;
-  }
+  if (sym_phase(I, states[0])) return;
   for (int bid = blockIdx.x; bid < I.M * I.nrb; bid += gridDim.x)
     pass_body<ST, 4, 4, 0, 0>(insts, states, ctrl, pmap, XS, VS, dsm, red, s_dec, bid);
 }
@@ -229,7 +323,7 @@ template <int DUMMY>
 __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ insts, State* __restrict__ states,
                                                    Ctrl* __restrict__ ctrl) {
   __shared__ double red[NWARP * NDOT];
-  __shared__ double sh[STB];
+  __shared__ double sh[NDOT * STB];
   __shared__ int s_dec;
   const Inst& I = insts[0];
   State& S = states[0];
@@ -246,7 +340,7 @@ __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ inst
   const float* x = I.xf[S.xcur ^ 1];
   const float* Ps = I.sp + (size_t)s * T * T * STB;
   sym_rows(I, Ps, R, i, x, I.xl[S.xcur ^ 1], I.dv, I.U[S.ucur], I.Ulo[S.ucur], I.U[S.ucur ^ 1],
-           I.Ulo[S.ucur ^ 1], I.W, I.spart + (size_t)s * NDOT * T + R, sh, red);
+           I.Ulo[S.ucur ^ 1], I.W, I.spart + (size_t)s * NDOT * T + R, sh);
   pass_finish(I, S, ctrl, s, i, I.spart, T, PH_TRIAL, true, x, I.dv, red, s_dec);
 }
 
@@ -255,10 +349,16 @@ __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ inst
 // block's dot partials in spart.  Arrays are (m+1, ldv) bases indexed by the
 // constraint row; xl, uol, Ulo may be null.
 template <int DUMMY>
-__global__ void __launch_bounds__(NT, 2) k_sym_plain(const Inst* __restrict__ insts, const float* __restrict__ v,
+__global__ void __launch_bounds__(NTS, 1) k_sym_plain(const Inst* __restrict__ insts, const float* __restrict__ v,
                                                      int* err) {
-  __shared__ __align__(16) float sred[NWARP * STB];
-  sym_tiles(insts[0], v, sred, err);
+  extern __shared__ __align__(128) uint8_t dsm[];
+#ifdef RAPDB_CHECKED
+  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes()) {
+    if (threadIdx.x == 0 && err) atomicCAS(err, 0, CHK_SYM_RANGE);
+    return;
+  }
+#endif
+  sym_tiles(insts[0], v, dsm, err);
 }
 
 template <int DUMMY>
@@ -267,14 +367,13 @@ __global__ void __launch_bounds__(NT) k_sym_rows_plain(const Inst* __restrict__ 
                                                        const float* __restrict__ uoh, const float* __restrict__ uol,
                                                        float* __restrict__ U, float* __restrict__ Ulo,
                                                        float* __restrict__ W, double* __restrict__ spart) {
-  __shared__ double red[NWARP * NDOT];
-  __shared__ double sh[STB];
+  __shared__ double sh[NDOT * STB];
   const Inst& I = insts[0];
   const int T = I.tsym;
   if (blockIdx.x >= (unsigned)(I.M * T)) return;
   const int s = blockIdx.x / T, R = blockIdx.x - s * T;
   sym_rows(I, I.sp + (size_t)s * T * T * STB, R, s + I.s_off, x, xl, v, uoh, uol, U, Ulo, W,
-           spart + (size_t)s * NDOT * T + R, sh, red);
+           spart + (size_t)s * NDOT * T + R, sh);
 }
 
 }  // namespace rapdb_dev
