@@ -3,7 +3,9 @@
 A step is one rAPDB solve (yx, non-monotone backtracking, FP32) of the dense
 random QCQP n = 4096, m = 50 (Q_i = A_i'A_i/n, A_i in R^{2048 x 4096}, a
 3.4 GB float32 stack) from x = 0, y = 0 to relative KKT residual <= 1e-6,
-with the inputs resident in HBM.  `value` is rAPDB iterations per second over
+with the inputs resident in HBM; the trial passes read the symmetric block
+packing of the stack (pack_sym, 1.76 GB; --no-pack for the row-streaming
+form).  `value` is rAPDB iterations per second over
 the timed steps (all ranks); the line also carries the time to tolerance,
 coupling passes per second, the coupling-pass roofline, the end-to-end
 number through the C ABI from pinned host buffers, and the FP64 CPU oracle
@@ -33,12 +35,16 @@ METRIC = ("time-to-1e-6 rel KKT & iters/s; coupling-pass HBM GB/s vs 8 TB/s "
 WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1), c_i N(0,1), "
             "d_i=-U[0.1,1], box [-10,10], FP32 storage (3.42 GB Q stack); rAPDB-yx non-monotone, "
             "adaptive (smoothed-gap) restart first at k=50 then every 500, refinement on: compensated "
-            "(double-float) products throughout, trial passes incremental, x0=y0=0, stop at rel KKT <= 1e-6")
-# DRAM bytes (read + write) of one incremental trial-pass launch on this
-# workload: the ncu capture of the same kernel and tile on the 11-matrix case
-# (742.3 MB per launch against 738.2 MB algorithmic;
-# profiles/coupling_pass_n4096_m10_f32.md) scaled by the 51/11 matrices.
+            "(double-float) products throughout, trial passes incremental through the packed upper block "
+            "triangle (128x128 tiles), x0=y0=0, stop at rel KKT <= 1e-6")
+# DRAM bytes (read + write) of one launch of the dominant kernels on this
+# workload, from ncu captures on the 11-matrix case scaled by the 51/11
+# matrices: the row-streaming incremental trial pass (742.3 MB per launch
+# against 738.2 MB algorithmic; profiles/coupling_pass_n4096_m10_f32.md) and
+# the packed tile kernel (385.3 MB per launch against 380.6 MB of tiles;
+# profiles/packed_pass_n4096_m10_f32.md).
 PASS_DRAM_BYTES = 742.3e6 * 51 / 11
+PACKED_TILE_DRAM_BYTES = (380669184 + 4624384) * 51 / 11
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 
@@ -137,7 +143,7 @@ def make_workload(device, seed=0):
 
 def solver_params(R, **kw):
     base = dict(c_nm=1, restart=R.RESTART_GAP, gap_first=50, gap_every=500, restart_period=200, tol=1e-6,
-                max_iter=50000, time_limit_s=300.0, refine=1)
+                max_iter=50000, time_limit_s=300.0, refine=1, pack_sym=0)
     base.update(kw)
     return R.Params.default(R.YX, **base)
 
@@ -338,7 +344,8 @@ def run_ours(args):
     data = make_workload(dev, seed=0)
     torch.cuda.synchronize()
     log("workload generated")
-    p = solver_params(R)
+    pack = 0 if args.no_pack else 1
+    p = solver_params(R, pack_sym=pack)
     s = R.Solver(data, p)
     log(f"solver created, tile {s.tile()}")
     x = torch.zeros(data.n, dtype=torch.float32, device=dev)
@@ -379,20 +386,37 @@ def run_ours(args):
     # dominant kernel: the coupling pass, timed with CUDA events on the
     # solver's stream (the torch current stream)
     # float32 storage with refinement runs every trial pass in the incremental
-    # compensated form (level 3: U^k + Q d); a direct compensated pass (level
-    # 2) re-anchors U every 64 iterations
-    pass_ms, pass_bytes = s.time_pass(reps=20, level=3)
-    plain_ms, _ = s.time_pass(reps=10, level=0)
-    comp_ms, _ = s.time_pass(reps=5, level=2)
+    # compensated form (U^k + Q d); a direct compensated pass (level 2)
+    # re-anchors U every 64 iterations.  With packing the trials read the
+    # upper block triangle: the tile kernel (level 5) is the dominant kernel,
+    # followed by the row-block kernel (level 4 times both)
     pk, pk_kind = peaks()
+    inc_ms, inc_bytes = s.time_pass(reps=20, level=3)
+    plain_ms, full_bytes = s.time_pass(reps=10, level=0)
+    comp_ms, _ = s.time_pass(reps=5, level=2)
+    if pack:
+        pass_ms, pass_bytes = s.time_pass(reps=20, level=5)
+        both_ms, _ = s.time_pass(reps=20, level=4)
+        kernel = ("k_sym_tiles (k_sym_plain stand-alone): tile products of the packed incremental trial pass, "
+                  "64 KB tiles through 3 bulk-copy shared-memory stages")
+        traffic = PACKED_TILE_DRAM_BYTES
+    else:
+        pass_ms, pass_bytes = inc_ms, inc_bytes
+        kernel = "k_pass<f32>, incremental compensated trial pass (U^k + Q d)"
+        traffic = PASS_DRAM_BYTES
     achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": PASS_DRAM_BYTES,
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                 "peak_kind": f"{pk_kind} copy bandwidth", "frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
-                "kernel": "k_pass<f32>, incremental compensated trial pass (U^k + Q d)",
-                "bytes_per_launch": pass_bytes, "ms_per_launch": pass_ms, "tile": s.tile(),
-                "plain_float32_pass_gbs": pass_bytes / (plain_ms * 1e-3) / 1e9,
-                "direct_compensated_pass_gbs": pass_bytes / (comp_ms * 1e-3) / 1e9}
+                "kernel": kernel, "bytes_per_launch": pass_bytes, "ms_per_launch": pass_ms, "tile": s.tile(),
+                "row_streaming_incremental_pass_gbs": full_bytes / (inc_ms * 1e-3) / 1e9,
+                "row_streaming_incremental_pass_ms": inc_ms,
+                "plain_float32_pass_gbs": full_bytes / (plain_ms * 1e-3) / 1e9,
+                "direct_compensated_pass_gbs": full_bytes / (comp_ms * 1e-3) / 1e9}
+    if pack:
+        roofline["packed_pass_ms_with_row_blocks"] = both_ms
+        roofline["packed_pass_gbs_with_row_blocks"] = pass_bytes / (both_ms * 1e-3) / 1e9
+        roofline["full_stack_bytes"] = full_bytes
     x64, y64 = s.solution_f64()
 
     # end to end through the C ABI from pinned host buffers (one step: upload,
@@ -440,12 +464,18 @@ def run_ours(args):
         log(f"batched: {extras['batched']}")
         # same instance: fixed-frequency restart (the paper's practice), and
         # BF16 / FP8 storage with refinement (plain vs mixed)
-        fixed = timed_solve(R, torch, data, solver_params(R, restart=R.RESTART_FIXED), dev)
+        fixed = timed_solve(R, torch, data, solver_params(R, restart=R.RESTART_FIXED, pack_sym=pack), dev)
         log(f"fixed restart: {fixed}")
         extras["fixed_restart"] = fixed
+        if pack:
+            # the same solve with the row-streaming trial passes (no packing)
+            rs_ = timed_solve(R, torch, data, solver_params(R), dev)
+            rs_["speedup_of_packing"] = rs_["time_to_tol_s"] / statistics.median(i["seconds"] for i in infos)
+            log(f"row-streaming trials: {rs_}")
+            extras["row_streaming"] = rs_
         mixed = {}
         for name, st in (("bf16", R.BF16), ("fp8", R.FP8)):
-            mixed[name] = timed_solve(R, torch, data, solver_params(R, storage=st), dev)
+            mixed[name] = timed_solve(R, torch, data, solver_params(R, storage=st, pack_sym=pack), dev)
             mixed[name]["speedup_vs_f32"] = (statistics.median(i["seconds"] for i in infos) /
                                              mixed[name]["time_to_tol_s"])
             log(f"mixed {name}: {mixed[name]}")
@@ -459,7 +489,7 @@ def run_ours(args):
             from paper_2605_29291_gb300 import workloads as W
             ds = W.random_qcqp(data.n, data.m, rows=data.n // 2, seed=seed, device=dev)
             for name, st in (("f32", R.F32), ("bf16", R.BF16), ("fp8", R.FP8)):
-                r_ = timed_solve(R, torch, ds, solver_params(R, storage=st), dev, reps=1)
+                r_ = timed_solve(R, torch, ds, solver_params(R, storage=st, pack_sym=pack), dev, reps=1)
                 per_seed[name].append({"seed": seed, "time_to_tol_s": r_["time_to_tol_s"], "iters": r_["iters"],
                                        "passes": r_["passes"], "rel_kkt": r_["rel_kkt"], "status": r_["status"]})
             del ds
@@ -598,6 +628,8 @@ def main():
     ap.add_argument("--mixed-seeds", type=int, default=2,
                     help="further instances (seeds 1..N) for the plain vs mixed comparison")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-shaped random-QCQP runs")
+    ap.add_argument("--no-pack", action="store_true",
+                    help="row-streaming trial passes (no symmetric block packing) on the main line")
     ap.add_argument("--no-kml", action="store_true", help="skip the kernel-learning-shaped throughput runs")
     ap.add_argument("--kml-iters", type=int, default=2000, help="iteration budget of each kernel-learning run")
     ap.add_argument("--no-extras", action="store_true")

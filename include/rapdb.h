@@ -122,7 +122,8 @@ typedef struct {
                               /*    at create: RAPDB_ERR_INVALID) and a single-       */
                               /*    instance context; rows_per_block and              */
                               /*    pass_variant are ignored (the other passes use    */
-                              /*    64-row items of tile variant 1).  Results are     */
+                              /*    64-row items of tile variant 1, 8 for FP8).       */
+                              /*    Results are                                       */
                               /*    reproducible run to run; they differ from an      */
                               /*    unpacked context's in rounding only.              */
 } rapdb_params;
@@ -257,12 +258,14 @@ rapdb_status rapdb_packed_pass(rapdb_ctx *ctx, const float *x, const float *v, c
  * 3 = the incremental form of level 2 that the solver's trial passes use
  * (U = U^k + Q d: one float32 right-hand side added to the double-float
  * products at x^k), 4 = level 3 through the packed upper block triangle
- * (contexts created with pack_sym = 1; the form their trials use).
+ * (contexts created with pack_sym = 1; the form their trials use: the tile
+ * kernel, then the row-block kernel), 5 = the tile kernel of level 4 alone.
  * *ms_per_pass (host) receives the average duration of one launch,
  * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
- * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8); at level 4
- * the packed tiles, M * T(T+1)/2 * 128 * 128 * 4 with T = ceil(n / 128).  Outputs
- * go to context scratch; the solver state is not changed.  RAPDB_ERR_INVALID
+ * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8); at
+ * levels 4 and 5 the packed tiles, M * T(T+1)/2 * 128 * 128 * 4 with
+ * T = ceil(n / 128).  Outputs go to context scratch; the solver state is not
+ * changed.  RAPDB_ERR_INVALID
  * when the level does not exist in this context. */
 rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, int32_t level, double *ms_per_pass,
                              int64_t *bytes_per_pass);

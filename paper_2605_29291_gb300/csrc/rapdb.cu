@@ -786,9 +786,17 @@ rapdb_status finish_standalone(rapdb_ctx* ctx) {
   return RAPDB_OK;
 }
 
-// pack_sym contexts: tile variant 1 for the row-streaming passes, one
-// resident wave of CTAs for their kernel, and one CTA per SM (at most one per
-// tile) for the packed tile kernels, with their shared-memory stages.
+static_assert(kVarRPW[SYM_ROW_VARIANT<RAPDB_F32>] == SYM_ROW_RPW<RAPDB_F32> &&
+                  kVarUNR[SYM_ROW_VARIANT<RAPDB_F32>] == SYM_ROW_UNR<RAPDB_F32> &&
+                  kVarRPW[SYM_ROW_VARIANT<RAPDB_FP8>] == SYM_ROW_RPW<RAPDB_FP8> &&
+                  kVarUNR[SYM_ROW_VARIANT<RAPDB_FP8>] == SYM_ROW_UNR<RAPDB_FP8> &&
+                  kVarNST[SYM_ROW_VARIANT<RAPDB_F32>] == 0 && kVarNST[SYM_ROW_VARIANT<RAPDB_FP8>] == 0,
+              "the packed context's row-streaming tile is a register variant of the table");
+
+// pack_sym contexts: the tile of SYM_ROW_VARIANT for the row-streaming
+// passes, one resident wave of CTAs for their kernel, and one CTA per SM (at
+// most one per tile) for the packed tile kernels, with their shared-memory
+// stages.
 rapdb_status setup_sym(rapdb_ctx* ctx) {
   const Inst& I = ctx->hi[0].I;
   int dev = 0, nsm = 0;
@@ -801,7 +809,7 @@ rapdb_status setup_sym(rapdb_ctx* ctx) {
   if (occ_tiles < 1) return fail(ctx, RAPDB_ERR_CUDA, "the packed tile kernel does not fit on an SM");
   const int64_t tiles = (int64_t)I.M * I.ntile;
   const int64_t items = (int64_t)I.M * I.nrb;
-  ctx->pvar = 1;
+  ctx->pvar = (ctx->storage == RAPDB_FP8) ? SYM_ROW_VARIANT<RAPDB_FP8> : SYM_ROW_VARIANT<RAPDB_F32>;
   ctx->sym_grid = (int)std::max<int64_t>(
       1, std::min(items, (int64_t)std::max(nsm, 1) * pass_sym_occupancy(ctx->storage)));
   ctx->sym_tile_grid = (int)std::max<int64_t>(1, std::min(tiles, (int64_t)std::max(nsm, 1) * occ_tiles));
@@ -1195,8 +1203,8 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     cur_level = ctx->h_state[0].precision;
   }
   const int lv = level < 0 ? cur_level : level;
-  if (lv > 4 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
-      (lv == 1 && I.storage == RAPDB_F32) || (lv == 4 && I.tsym == 0))
+  if (lv > 5 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
+      (lv == 1 && I.storage == RAPDB_F32) || (lv >= 4 && I.tsym == 0))
     return fail(ctx, RAPDB_ERR_INVALID, "precision level not available in this context");
   const float* x = I.xf[xcur];
   const float* v = I.dv;
@@ -1204,10 +1212,11 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
-    if (lv == 4) {
+    if (lv >= 4) {
       k_sym_plain<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), st>>>(ctx->d_inst, v, &ctx->d_ctrl->err);
-      k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, x, I.xl[xcur], v, I.U[0], I.Ulo[0], ctx->tU,
-                                                       ctx->tUo, ctx->tW, I.spart);
+      if (lv == 4)
+        k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, x, I.xl[xcur], v, I.U[0], I.Ulo[0], ctx->tU,
+                                                         ctx->tUo, ctx->tW, I.spart);
     } else
       launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS,
                    lv == 2 ? nullptr : I.U[0],
@@ -1231,7 +1240,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     const int64_t eb = lv >= 1 ? 4 : (I.storage == RAPDB_F32 ? 4 : (I.storage == RAPDB_BF16 ? 2 : 1));
     int64_t b = (int64_t)I.M * I.n * I.n * eb;
     if (I.storage == RAPDB_FP8 && lv == 0) b += (int64_t)I.M * I.n * 4;
-    if (lv == 4) b = ctx->hi[0].qp_bytes;
+    if (lv >= 4) b = ctx->hi[0].qp_bytes;
     *bytes_per_pass = b;
   }
   return RAPDB_OK;

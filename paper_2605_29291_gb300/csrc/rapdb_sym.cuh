@@ -293,8 +293,18 @@ __global__ void __launch_bounds__(NTS, 1) k_sym_tiles(const Inst* __restrict__ i
   sym_tiles(I, I.dv, dsm, &ctrl->err);
 }
 
-// The row-streaming coupling pass of a context with packed tiles (tile
-// variant 1: 4 rows x 4 chunks per warp), each CTA taking the row-block
+// Row-streaming tile of a context with packed tiles: 4 rows x 4 chunks per
+// warp (tile variant 1), or 8 rows x 2 chunks (variant 8) for FP8 storage,
+// whose 16-byte slices of x and v then serve eight rows.
+template <int ST>
+constexpr int SYM_ROW_VARIANT = (ST == RAPDB_FP8) ? 8 : 1;
+template <int ST>
+constexpr int SYM_ROW_RPW = (ST == RAPDB_FP8) ? 8 : 4;
+template <int ST>
+constexpr int SYM_ROW_UNR = (ST == RAPDB_FP8) ? 2 : 4;
+
+// The row-streaming coupling pass of a context with packed tiles (the tile of
+// SYM_ROW_VARIANT), each CTA taking the row-block
 // items blockIdx.x, blockIdx.x + gridDim.x, ...; in a packed trial every CTA
 // returns at once (k_sym_tiles runs it).  A CTA reaches the control step only
 // in its last item (the step needs all other items to have arrived), and a
@@ -311,7 +321,7 @@ __global__ void __launch_bounds__(NT, 2) k_pass_sym(const Inst* __restrict__ ins
   const Inst& I = insts[0];
   if (sym_phase(I, states[0])) return;
   for (int bid = blockIdx.x; bid < I.M * I.nrb; bid += gridDim.x)
-    pass_body<ST, 4, 4, 0, 0>(insts, states, ctrl, pmap, XS, VS, dsm, red, s_dec, bid);
+    pass_body<ST, SYM_ROW_RPW<ST>, SYM_ROW_UNR<ST>, 0, 0>(insts, states, ctrl, pmap, XS, VS, dsm, red, s_dec, bid);
 }
 
 // Second kernel of a packed trial pass: one CTA per row block (grid M x T)

@@ -26,7 +26,11 @@ def run(data, params, y0=None):
     assert info["status"] in (R.OK, R.ERR_MAXITER), info
     s.kkt_residual(x, y)
     s.coupling_pass(torch.rand(data.n, device=dev), torch.rand(data.n, device=dev))
-    for level in (0, 1, 2, 3):
+    if params.pack_sym:
+        M = int(data.Q.shape[0])
+        s.packed_pass(torch.rand(data.n, device=dev), torch.rand(data.n, device=dev),
+                      torch.rand((M, data.n), device=dev))
+    for level in (0, 1, 2, 3, 4, 5):
         try:
             s.time_pass(reps=1, level=level)
         except R.RapdbError as e:
@@ -51,6 +55,13 @@ run(dense, R.Params.default(R.YX, tol=1e-5, max_iter=3000, restart_from_average=
 kb = W.kml_minmax(150, 5, 3, seed=1, bias=True)
 y0 = torch.tensor([1 / 3, 1 / 3, 1 / 3, 0.0], device=dev)
 run(kb, R.Params.default(R.YX, dual_set=R.DUAL_SIMPLEX, tol=1e-5, max_iter=3000), y0)
+# symmetric block packing: float32, BF16 and FP8 storage, dense and diagonal Q_0, yx and xy
+for storage in (0, 1, 2):
+    for data in (dense, diag):
+        run(data, R.Params.default(R.YX, storage=storage, refine=1, pack_sym=1, tol=1e-5, max_iter=2000))
+run(dense, R.Params.default(R.XY, pack_sym=1, tol=1e-5, max_iter=3000, restart=R.RESTART_GAP, gap_first=50,
+                            gap_every=100))
+run(kb, R.Params.default(R.YX, dual_set=R.DUAL_SIMPLEX, pack_sym=1, tol=1e-5, max_iter=3000), y0)
 # batched, with finished instances dropped from the grids as they finish
 datas = W.batched_random_qcqp(48, seed=5, n_lo=32, n_hi=300, m_lo=1, m_hi=8)
 bs = R.BatchedSolver([d.to(dev) for d in datas], R.Params.default(tol=1e-6, max_iter=20000))

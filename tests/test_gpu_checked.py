@@ -2,8 +2,8 @@
 row ranges and dynamic shared memory against the launch, and report a failed
 check as an error status instead of touching memory) runs every solver path
 clean: all storages and tile variants, dense and diagonal Q_0, xy, restarts,
-the simplex dual with an equality, and batched solves whose launch grids
-shrink as instances finish."""
+the simplex dual with an equality, the symmetric block packing, and batched
+solves whose launch grids shrink as instances finish."""
 import os
 import subprocess
 import sys

@@ -17,7 +17,8 @@ its rows and, transposed, for its columns.
 * sizes that leave a ragged last tile (n = 129, 200, 1000), one tile (128),
   and the full n = 4096, m = 50 workload on sampled rows and by the oracle's
   float64 KKT residual at the solver's iterate;
-* rejection of a non-symmetric Q and of level 4 without packing.
+* FP8 storage with refinement and packing;
+* rejection of a non-symmetric Q and of levels 4 and 5 without packing.
 """
 import numpy as np
 import pytest
@@ -236,6 +237,21 @@ def test_bf16_storage_packs_the_float32_copy(R, cuda):
     assert rel <= 1.1e-6, rel
 
 
+def test_fp8_storage_packs_the_float32_copy(R, cuda):
+    """FP8 (Jacobi-scaled E4M3) storage with refinement and packing: the
+    stored-precision trials, then packed float32 trials after the switch."""
+    data = W.kml_qcqp(200, 6, 8, seed=5)
+    p = packed(R, storage=2, refine=1, tol=1e-6, restart_period=100)
+    s = R.Solver(data.to(cuda), p)
+    x, y = zeros(data, cuda)
+    info = s.solve(x, y)
+    x64, y64 = s.solution_f64()
+    s.close()
+    assert info["status"] == R.OK and info["precision_switches"] >= 1, info
+    rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
+    assert rel <= 1.1e-6, rel
+
+
 def test_non_symmetric_q_rejected(R, cuda):
     data = W.random_qcqp(150, 3, seed=1)
     data.Q[2, 7, 140] += np.float32(1e-3)
@@ -251,12 +267,15 @@ def test_time_pass_level_4(R, cuda):
     ms, b = s.time_pass(reps=3, level=4)
     T = (300 + 127) // 128
     assert ms > 0 and b == 5 * T * (T + 1) // 2 * 128 * 128 * 4
+    ms5, b5 = s.time_pass(reps=3, level=5)
+    assert ms5 > 0 and b5 == b
     ms3, b3 = s.time_pass(reps=3, level=3)
     assert b3 == 5 * 300 * 300 * 4
     s.close()
     s = R.Solver(data, R.Params.default())
-    with pytest.raises(R.RapdbError):
-        s.time_pass(reps=1, level=4)
+    for lv in (4, 5):
+        with pytest.raises(R.RapdbError):
+            s.time_pass(reps=1, level=lv)
     s.close()
 
 
