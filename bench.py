@@ -41,10 +41,10 @@ WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1),
 # workload, from ncu captures on the 11-matrix case scaled by the 51/11
 # matrices: the row-streaming incremental trial pass (742.3 MB per launch
 # against 738.2 MB algorithmic; profiles/coupling_pass_n4096_m10_f32.md) and
-# the packed tile kernel (385.3 MB per launch against 380.6 MB of tiles;
+# the packed tile kernel (385.7 MB per launch against 380.6 MB of tiles;
 # profiles/packed_pass_n4096_m10_f32.md).
 PASS_DRAM_BYTES = 742.3e6 * 51 / 11
-PACKED_TILE_DRAM_BYTES = (380669184 + 4624384) * 51 / 11
+PACKED_TILE_DRAM_BYTES = (380678912 + 4998656) * 51 / 11
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 

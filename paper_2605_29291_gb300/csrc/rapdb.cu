@@ -464,7 +464,7 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
     AL(qp, (size_t)M * ntile * STB * STB);
     k_pack_sym<<<4096, 256, 0, st>>>(Qf, ldq, n, M, T, ntile, dtij, qp);
     CK(cudaGetLastError());
-    AL(I.sp, (size_t)M * T * T * STB);
+    AL(I.sp, (size_t)2 * M * T * T * STB);     // two slot sets (two right-hand sides)
     AL(I.spart, (size_t)M * NDOT * T);
     I.Qp = qp;
     I.tij = dtij;

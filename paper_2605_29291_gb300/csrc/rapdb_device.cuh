@@ -119,7 +119,8 @@ struct Inst {
   // float32 Q_i in STB x STB tiles, read by the incremental trial passes
   const float* Qp;      // (M, ntile, STB, STB) tiles, zero outside n x n; null: none
   const int* tij;       // (ntile) tile coordinates I << 16 | J, I <= J, row-major
-  float* sp;            // (M, T, T * STB) tile products: slot J of the rows of block I
+  float* sp;            // (2, M, T, T * STB) tile products: slot J of the rows of block I,
+                        // one set per right-hand side
   double* spart;        // (M, NDOT, T) row-block dot partials of the packed pass
   int tsym, ntile;      // T = ceil(n / STB) (0: no packing), T (T + 1) / 2
   double* vpart;        // (ncb, NVP) vector partials

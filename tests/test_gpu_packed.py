@@ -12,6 +12,7 @@ its rows and, transposed, for its columns.
 * bit-for-bit reproducibility of the pass and of whole solves;
 * the solver with packed trials against the FP64 oracle: the first iterates
   with a fixed step, full solves (yx, xy, fixed and adaptive restart), the
+  smoothed gap computed through packed two-right-hand-side passes, the
   diagonal Q_0 with the simplex dual and a linear equality, BF16 storage with
   refinement, checkpoint / resume;
 * sizes that leave a ragged last tile (n = 129, 200, 1000), one tile (128),
@@ -153,6 +154,34 @@ def test_full_solve_matches_oracle(R, cuda, variant, restart):
     assert abs(info["obj"] - fo) <= 1e-5 * (1 + abs(fo))
     rel, _, _ = O.kkt_residual(prob, x64, y64)
     assert rel <= 1.1e-6, rel
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_smoothed_gap_through_packed_passes(R, cuda, variant):
+    """The smoothed gap's two-right-hand-side passes read the packed tiles:
+    G_xi at the logged iterates x^30, x^40 (fixed step) equals the oracle's
+    exact G_xi within the subproblem's stopping bound, and the restarts fire
+    as the oracle's rule says."""
+    c1 = W.config("C1")
+    kw = dict(backtracking=0, tau_bar=0.05, tol=0.0, max_iter=45, restart=R.RESTART_GAP, gap_first=30,
+              gap_every=10)
+    p = packed(R, variant, **kw)
+    s = R.Solver(c1.to(cuda), p)
+    s.set_log(50)
+    x, y = zeros(c1, cuda)
+    info = s.solve(x, y)
+    assert info["iters"] == 45
+    xl = s.log["x"].cpu().numpy().astype(np.float64)
+    yl = s.log["y"].cpu().numpy().astype(np.float64)
+    G = s.log["gap"].cpu().numpy().copy()
+    s.close()
+    prob = O.Problem.from_data(c1)
+    for e, it in enumerate([30, 40]):
+        Go = O.smoothed_gap(prob, xl[it - 1], yl[it - 1, :c1.m], p.xi)
+        assert Go > 0
+        assert abs(G[e] - Go) <= 2e-3 * abs(Go) + 1e-9, (it, G[e], Go)
+    r = O.rapdb(prob, p=oracle_params(R, p))
+    assert info["restarts"] == r.restarts
 
 
 def test_packed_solve_is_deterministic_and_close_to_unpacked(R, cuda):
