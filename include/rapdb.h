@@ -115,9 +115,10 @@ typedef struct {
   int32_t pack_sym;           /* 1: symmetric block packing.  The context keeps the   */
                               /*    upper block triangle of every float32 Q_i in      */
                               /*    128 x 128 tiles (about half of Q's bytes, on top  */
-                              /*    of Q), and the incremental trial passes read each */
-                              /*    tile once for its rows and, transposed, for its   */
-                              /*    columns: half the bytes of a row-streaming pass.  */
+                              /*    of Q), and the incremental trial passes and the   */
+                              /*    smoothed gap's passes read each tile once for its */
+                              /*    rows and, transposed, for its columns: half the   */
+                              /*    bytes of a row-streaming pass.                    */
                               /*    Needs refine = 1, exactly symmetric Q_i (checked  */
                               /*    at create: RAPDB_ERR_INVALID) and a single-       */
                               /*    instance context; rows_per_block and              */

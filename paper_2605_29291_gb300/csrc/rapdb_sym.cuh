@@ -10,8 +10,8 @@
 // The transposed products land in rows that other CTAs own.  Each tile
 // product goes to its own slot of a partial buffer (slot J of the rows of
 // block I); a second kernel, one CTA per row block, sums the block's T slots
-// in slot order, in float64, then applies the incremental compensated update
-// of the trial pass:
+// in slot order (a compensated float32 sum), then applies the incremental
+// compensated update of the trial pass:
 //   w = (Q_i d)_j,  u = U^k_j (double-float) + w,  U' = hi/lo of u,  W = w,
 // with the per-row dots x'u, v'w, v'U^k, c'x, c'v.  The tile kernel streams
 // with no counters or fences (the kernel boundary orders its stores before
@@ -186,7 +186,7 @@ static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, co
 // 4l .. 4l+3 (row partials halved over the lanes, column partials summed over
 // the 16 warps in order: at most 8 + 15 float32 roundings per partial).  The
 // stage is refilled as soon as all threads have read it, and the next tile's
-// d slices are loaded while the current tile is reduced.  No counters and no
+// right-hand-side slices are loaded while the current tile is reduced.  No counters and no
 // global fences: the row-block reduction runs in the next kernel.  Every wait
 // is bounded; on a timeout the CTA sets *err, waits (bounded) for its copies
 // in flight and returns.
@@ -222,8 +222,8 @@ __device__ __forceinline__ float warp_rows8(float (&a)[SRW8]) {
   return r + __shfl_xor_sync(0xffffffffu, r, 1);
 }
 
-// The d slices a thread needs for tile (TI, TJ): d_J[4l .. 4l+3] and, in lanes
-// 0..7, d_I of row 8w + lane (zero past n).
+// The slices of a right-hand side v a thread needs for tile (TI, TJ):
+// v_J[4l .. 4l+3] and, in lanes 0..7, v_I of row 8w + lane (zero past n).
 __device__ __forceinline__ void sym_dslices(const float* __restrict__ v, int n, int TI, int TJ, float (&dj)[4],
                                             float& dil) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
