@@ -18,7 +18,8 @@ its rows and, transposed, for its columns.
 * sizes that leave a ragged last tile (n = 129, 200, 1000), one tile (128),
   and the full n = 4096, m = 50 workload on sampled rows and by the oracle's
   float64 KKT residual at the solver's iterate;
-* FP8 storage with refinement and packing;
+* FP8 storage with refinement and packing; BF16 and FP8 storage with adaptive
+  restart, whose gap passes read the packed tiles after the precision switch;
 * rejection of a non-symmetric Q and of levels 4 and 5 without packing.
 """
 import numpy as np
@@ -277,6 +278,26 @@ def test_fp8_storage_packs_the_float32_copy(R, cuda):
     x64, y64 = s.solution_f64()
     s.close()
     assert info["status"] == R.OK and info["precision_switches"] >= 1, info
+    rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
+    assert rel <= 1.1e-6, rel
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_quantised_storage_adaptive_restart_packed_gap(R, cuda, storage):
+    """BF16 / FP8 storage with refinement, adaptive restart and packing: the
+    smoothed gap's passes read the stored matrices before the precision
+    switch and the packed float32 tiles after it; the solve ends at rel KKT
+    1e-6 by the oracle's float64 residual."""
+    data = W.kml_qcqp(200, 6, 8, seed=4)
+    p = packed(R, storage=storage, refine=1, tol=1e-6, restart=R.RESTART_GAP, gap_first=20, gap_every=20,
+               restart_period=100, max_iter=20000)
+    s = R.Solver(data.to(cuda), p)
+    x, y = zeros(data, cuda)
+    info = s.solve(x, y)
+    x64, y64 = s.solution_f64()
+    s.close()
+    assert info["status"] == R.OK and info["precision_switches"] >= 1, info
+    assert info["passes"] > info["trials"] + 20, info          # gap passes ran
     rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
     assert rel <= 1.1e-6, rel
 
