@@ -42,7 +42,11 @@ QP by exhaustive active-set enumeration, the ergodic bounds (Lemmas with eqs.
 4.16apd / 3.3apd) at random points, step-size invariants (monotone identity of
 the trial count, the golden-ratio bound of the non-monotone rule), the algebraic
 identity of E_k for quadratics, G_xi(z*) = 0 and G_xi >= 0, and the
-x-subproblem against brute-force active-set enumeration.
+x-subproblem against brute-force active-set enumeration; the adaptive-restart
+schedule, its decisions and reference value against closed-form gaps of a
+separable QCQP, and the restart from the weighted average against the
+independently formed average and the closed-form first step of the next run
+(tests/test_oracle_restart_pins.py, each also run on planted mistakes).
 Parity unpinned: absolute iteration counts of the paper's tables (different
 instances and data).
 """
