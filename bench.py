@@ -38,11 +38,10 @@ WORKLOAD = ("dense random QCQP n=4096 m=50, Q_i=A_i'A_i/n, A_i 2048x4096 N(0,1),
             "(double-float) products throughout, trial passes incremental through the packed upper block "
             "triangle (128x128 tiles), x0=y0=0, stop at rel KKT <= 1e-6")
 # DRAM bytes (read + write) of one launch of the dominant kernels on this
-# workload, from ncu captures on the 11-matrix case scaled by the 51/11
-# matrices: the row-streaming incremental trial pass (742.3 MB per launch
-# against 738.2 MB algorithmic; profiles/coupling_pass_n4096_m10_f32.md) and
-# the packed tile kernel (385.7 MB per launch against 380.6 MB of tiles;
-# profiles/packed_pass_n4096_m10_f32.md).
+# workload, from ncu captures on the 11-matrix case (n = 4096, m = 10) scaled
+# by the 51/11 matrices: the row-streaming incremental trial pass (742.3 MB
+# per launch against 738.2 MB algorithmic) and the packed tile kernel (385.7
+# MB per launch against 380.6 MB of tiles).
 PASS_DRAM_BYTES = 742.3e6 * 51 / 11
 PACKED_TILE_DRAM_BYTES = (380678912 + 4998656) * 51 / 11
 NOMINAL_HBM_GBS = 8000.0

@@ -213,9 +213,18 @@ rapdb_status rapdb_get_solution_f64(rapdb_ctx *ctx, double *x, double *y);
  * was created with refine = 1, else the float32 Q, else the stored copy),
  * then
  *   r_stat_j = dist(0, grad_x L(x,y)_j + N_[lb,ub](x_j)),
- *   r_feas_i = |g_i(x)| if y_i > 0 else max(g_i(x), 0),
+ *   ||r_feas|| = dist(g(x), N_Y(y)) over the inequality constraints, plus
+ *                the equality residuals: with Y the orthant (RAPDB_DUAL_NONNEG)
+ *                its components are |g_i(x)| if y_i > 0 else max(g_i(x), 0);
+ *                with Y the simplex {y >= 0, sum y = dual_radius}
+ *                (RAPDB_DUAL_SIMPLEX), N_Y(y) = {t 1 - nu : nu >= 0, nu_i = 0
+ *                where y_i > 0}, so the components are g_i(x) - t if y_i > 0
+ *                else max(g_i(x) - t, 0) with the scalar t that minimises
+ *                their norm; every linear equality a_k'x = b_k of
+ *                rapdb_create_eq adds the component |a_k'x - b_k|,
  *   rel = max(||r_stat|| / (1 + max(||Q_0x+c_0||, ||sum_i y_i(Q_ix+c_i)||)),
  *             ||r_feas|| / (1 + max(||d||, ||(g_i(x) - d_i)_i||))),
+ * (with equalities, d holds -b_k and g_i(x) - d_i holds a_k'x for them),
  * the residual r(x, v, lambda) of the metric subregularity theorem (Sec. 4)
  * with the normalisation stated above.  Outputs are host doubles (any may be
  * NULL). */
@@ -352,9 +361,12 @@ rapdb_status rapdb_get_tile(const rapdb_ctx *ctx, int32_t *rows_per_block, int32
  *   dots  device output, (m+1, 5) doubles as in rapdb_coupling_pass
  * Limits: n % 4 == 0 and (m+1) * 5 * ceil(n/32) <= 131072 (e.g. n = 4096 with
  * m up to 203); otherwise RAPDB_ERR_INVALID and nothing runs.  The call is
- * asynchronous on `stream` (a cudaStream_t, NULL = default stream).  The
- * first call on each device finds the scratch array's device address (with
- * that device current); make that first call before any stream capture.
+ * asynchronous on `stream` (a cudaStream_t, NULL = default stream).  Each
+ * call looks up the scratch array's device address for the current device
+ * (so a call after cudaDeviceReset, or under another context, finds the
+ * array where that context holds it); the first call on a device also loads
+ * the library's device code there, so make that first call before any
+ * stream capture.
  * Every call on a device shares the one scratch array, so calls whose work
  * overlaps on the GPU (different streams without ordering, or several host
  * threads) race and give wrong results: order them on one stream.  Each call

@@ -11,8 +11,6 @@
 // file-scope device array of fixed size.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "rapdb_device.cuh"
 
 using namespace rapdb_dev;
@@ -27,9 +25,6 @@ constexpr long long NA_MAX_PARTIALS = 1ll << 17;  // 131072 doubles = 1 MiB
 // in it has to start at zero.
 static __device__ __align__(256) double g_na_partials[NA_MAX_PARTIALS];
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-double* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
 
 __global__ void __launch_bounds__(NT) k_pass_noalloc(const float* __restrict__ Q, int n, int nrb,
                                                      const float* __restrict__ x, const float* __restrict__ v,
@@ -70,20 +65,15 @@ extern "C" rapdb_status rapdb_coupling_pass_noalloc(int64_t n, int64_t m, const 
   const long long M = m + 1;
   const long long nrb = (n + NA_ROWS - 1) / NA_ROWS;
   if (M * NDOT * nrb > NA_MAX_PARTIALS) return RAPDB_ERR_INVALID;   // beyond the fixed scratch
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return RAPDB_ERR_CUDA;
-  double* part = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      // first call on this device (the device is current): the array's
-      // device address; in host code the symbol itself is only a stand-in
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_na_partials) != cudaSuccess || !p) return RAPDB_ERR_CUDA;
-      g_na_ptr[dev] = (double*)p;
-    }
-    part = g_na_ptr[dev];
-  }
+  // The array's device address in the current device's context.  In host
+  // code the symbol itself is only a stand-in, never a device address.  The
+  // address is looked up on every call rather than remembered: after a
+  // cudaDeviceReset, or with another context current on the device, the
+  // library's device code is loaded again, possibly at another address.  The
+  // first call on a device is the one that loads that code.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_partials) != cudaSuccess || !p) return RAPDB_ERR_CUDA;
+  double* part = (double*)p;
   cudaStream_t st = (cudaStream_t)stream;
   k_pass_noalloc<<<(unsigned)(M * nrb), NT, 0, st>>>(Q, (int)n, (int)nrb, x, v, uold, c, U, W, part);
   k_dots_noalloc<<<(unsigned)((M * NDOT + NWARP - 1) / NWARP), NT, 0, st>>>(part, (int)M, (int)nrb, dots);
