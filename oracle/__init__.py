@@ -12,5 +12,6 @@ from .rapdb_oracle import (  # noqa: F401
     Params, Problem, Result, default_params, rapdb, apdb, kkt_residual,
     smoothed_gap, gap_x_subproblem, start_routine, apdb_iteration,
     yx_trial, xy_trial, BacktrackError, proj_simplex, simplex_cone_distance,
+    proj_box_hyperplane, hyperplane_cone_distance, box_cone_residual,
 )
 from .quant import bf16_round, e4m3_round, e4m3_decode_table, fp8_jacobi_quantize  # noqa: F401

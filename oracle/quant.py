@@ -93,7 +93,10 @@ def fp8_jacobi_quantize(Q: np.ndarray):
     pos = dg > 0
     sq = np.where(pos, np.sqrt(np.where(pos, dg, np.float32(1))), np.float32(1)).astype(np.float32)
     r = (np.float32(1) / sq).astype(np.float32)
-    C = ((Q * r[:, None]).astype(np.float32) * r[None, :]).astype(np.float32)
+    # Q_jk * (r_j * r_k): the product of the two factors first, so that the
+    # codes of (j, k) and (k, j) are equal and Q~ is exactly symmetric
+    rr = (r[:, None] * r[None, :]).astype(np.float32)
+    C = (Q * rr).astype(np.float32)
     C = (C * np.float32(256.0)).astype(np.float32)
     codes = e4m3_encode(C)
     s = (sq * np.float32(1.0 / 16.0)).astype(np.float32)
@@ -118,9 +121,10 @@ def jacobi_factors(diag: np.ndarray):
 
 def fp8_jacobi_codes(q: np.ndarray, r_row: np.ndarray, r_col: np.ndarray) -> np.ndarray:
     """E4M3 codes of single entries Q_jk of the Jacobi-scaled storage, given
-    r_j and r_k (broadcast against q): E4M3(((Q_jk * r_j) * r_k) * 256), each
+    r_j and r_k (broadcast against q): E4M3((Q_jk * (r_j * r_k)) * 256), each
     product rounded to float32 as in fp8_jacobi_quantize.  Lets a few rows or
     columns of a matrix too large to quantise here be checked on their own."""
     q = np.asarray(q, dtype=np.float32)
-    C = ((q * np.asarray(r_row, np.float32)).astype(np.float32) * np.asarray(r_col, np.float32)).astype(np.float32)
+    rr = (np.asarray(r_row, np.float32) * np.asarray(r_col, np.float32)).astype(np.float32)
+    C = (q * rr).astype(np.float32)
     return e4m3_encode((C * np.float32(256.0)).astype(np.float32))

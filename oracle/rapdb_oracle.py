@@ -34,6 +34,18 @@ Sources (arXiv 2605.29291):
     block, eq. NCP; the kernel-learning constraint b'x = 0 of Sec. 5.2): the
     last n_eq rows of the constraint data are a_k'x - b_k with Q = 0 and a
     free (unprojected) multiplier; their KKT component is |a_k'x - b_k|.
+  * A primal set with one hyperplane, X = {lb <= x <= ub, a'x = beta} (the
+    kernel-learning problem of Sec. 5.2, eq. min-max-KML, minimises over
+    {x >= 0, b'x = 0}: lb = 0, ub = +inf, a = b, beta = 0).  The Euclidean
+    projection onto X is x = clamp(v - nu a) with the scalar nu that solves
+    a'clamp(v - nu a) = beta (the optimality conditions of the projection;
+    the left side is piecewise linear and non-increasing in nu, so nu is
+    found exactly between two of its breakpoints).  The normal cone is
+    N_X(x) = {t a + N_box(x)}, so r_stat = min over t of the box-cone
+    residual of grad + t a (a convex piecewise quadratic, minimised piece by
+    piece).  The gap's x-subproblem over X is the box QP with the term t a'x
+    added, t found by bisection so that a'x(t) = beta (a'x(t) is
+    non-increasing in t).
 
 Parity pins (see tests/test_oracle_pins.py, tests/test_oracle_simplex_pins.py):
 closed forms (ball constraint,
@@ -154,13 +166,122 @@ def simplex_cone_distance(g, lam):
     return math.sqrt(best[0]), best[1]
 
 
+def hyperplane_phi(v, lb, ub, a, beta, nu):
+    """a'clamp(v - nu a, lb, ub) - beta."""
+    return float(a @ np.minimum(np.maximum(v - nu * a, lb), ub)) - beta
+
+
+def proj_box_hyperplane(v, lb, ub, a, beta):
+    """Euclidean projection of v onto {lb <= x <= ub, a'x = beta}.
+
+    The projection is x = clamp(v - nu a, lb, ub) for the nu with
+    a'x = beta.  phi(nu) = a'clamp(v - nu a) - beta is continuous, piecewise
+    linear and non-increasing; its breakpoints are the nu at which some
+    v_j - nu a_j reaches lb_j or ub_j.  The root lies between two adjacent
+    breakpoints (found by bisection over the sorted breakpoints), or beyond the
+    outermost one, and is the root of the linear piece there.  Returns
+    (x, nu)."""
+    v = np.asarray(v, np.float64)
+    a = np.asarray(a, np.float64)
+    nz = a != 0.0
+    bps = []
+    for bound in (lb, ub):
+        bb = np.asarray(bound, np.float64)
+        ok = nz & np.isfinite(bb)
+        bps.append((v[ok] - bb[ok]) / a[ok])
+    bp = np.unique(np.concatenate(bps))
+    phi = lambda t: hyperplane_phi(v, lb, ub, a, beta, t)
+
+    def slope_at(t0, t1):
+        # phi is linear on [t0, t1]: its slope from two evaluations, or from
+        # the free coordinates when the piece is unbounded
+        mid = 0.5 * (t0 + t1) if np.isfinite(t0) and np.isfinite(t1) else (t1 - 1.0 if np.isfinite(t1) else t0 + 1.0)
+        xm = v - mid * a
+        free = (xm > lb) & (xm < ub)
+        return -float(np.sum(a[free] ** 2))
+
+    if bp.size == 0:
+        sl = slope_at(-np.inf, np.inf)
+        if sl == 0.0:
+            raise ValueError("the hyperplane does not meet the box")
+        nu = phi(0.0) / -sl
+        return np.minimum(np.maximum(v - nu * a, lb), ub), nu
+    lo_i, hi_i = 0, bp.size - 1
+    f_lo, f_hi = phi(bp[lo_i]), phi(bp[hi_i])
+    if f_lo < 0.0:          # root below the smallest breakpoint
+        sl = slope_at(-np.inf, bp[0])
+        if sl == 0.0:
+            raise ValueError("the hyperplane does not meet the box")
+        nu = bp[0] - f_lo / sl
+    elif f_hi > 0.0:        # root above the largest breakpoint
+        sl = slope_at(bp[-1], np.inf)
+        if sl == 0.0:
+            raise ValueError("the hyperplane does not meet the box")
+        nu = bp[-1] - f_hi / sl
+    else:
+        # phi(bp[lo_i]) >= 0 >= phi(bp[hi_i]): bisect to adjacent breakpoints
+        while hi_i - lo_i > 1:
+            mid = (lo_i + hi_i) // 2
+            fm = phi(bp[mid])
+            if fm >= 0.0:
+                lo_i, f_lo = mid, fm
+            else:
+                hi_i, f_hi = mid, fm
+        if f_lo == 0.0:
+            nu = bp[lo_i]
+        elif f_hi == 0.0:
+            nu = bp[hi_i]
+        else:               # linear between the two: its root
+            nu = bp[lo_i] + f_lo * (bp[hi_i] - bp[lo_i]) / (f_lo - f_hi)
+    return np.minimum(np.maximum(v - nu * a, lb), ub), nu
+
+
+def box_cone_residual(g, x, lb, ub):
+    """Componentwise dist(0, g + N_box(x)): max(-g, 0) at a lower bound,
+    max(g, 0) at an upper bound, |g| inside."""
+    return np.where(x <= lb, np.maximum(-g, 0.0), np.where(x >= ub, np.maximum(g, 0.0), np.abs(g)))
+
+
+def hyperplane_cone_distance(g, x, lb, ub, a):
+    """dist(0, g + N_X(x)) for X = box with the hyperplane a'x = beta:
+    N_X(x) = {t a + nu : nu in N_box(x)}, so the distance is the minimum over
+    t of F(t) = ||box_cone_residual(g + t a)||.  F^2 is convex and piecewise
+    quadratic; its breakpoints are the t at which g_j + t a_j = 0 for a
+    coordinate at a bound.  On each piece the active terms are fixed and the
+    minimiser is the least-squares t over them, clamped to the piece.
+    Returns (distance, t)."""
+    g = np.asarray(g, np.float64)
+    a = np.asarray(a, np.float64)
+    at_lo, at_hi = x <= lb, x >= ub
+    bound = (at_lo | at_hi) & (a != 0.0)
+    edges = np.unique(-g[bound] / a[bound])
+    edges = np.concatenate([[-np.inf], edges, [np.inf]])
+    best = (np.inf, 0.0)
+    F2 = lambda t: float(np.sum(box_cone_residual(g + t * a, x, lb, ub) ** 2))
+    for p in range(edges.size - 1):
+        lo, hi = edges[p], edges[p + 1]
+        mid = 0.5 * (lo + hi) if np.isfinite(lo) and np.isfinite(hi) else (hi - 1.0 if np.isfinite(hi) else
+                                                                             (lo + 1.0 if np.isfinite(lo) else 0.0))
+        gm = g + mid * a
+        act = ~(at_lo | at_hi) | (at_lo & (gm < 0.0)) | (at_hi & (gm > 0.0))
+        den = float(np.sum(a[act] ** 2))
+        t = -float(np.sum(a[act] * g[act])) / den if den > 0.0 else mid
+        t = min(max(t, lo), hi)
+        val = F2(t)
+        if val < best[0]:
+            best = (val, t)
+    return np.sqrt(best[0]), best[1]
+
+
 class Problem:
     """Float64 copy of the canonical float32 data.  Q[0] is Q_0.  With
     dual_radius set, the dual set is the simplex {y >= 0, sum y = dual_radius}
-    instead of the nonnegative orthant."""
+    instead of the nonnegative orthant.  With hyperplane = (a, beta) the primal
+    set is the box intersected with {a'x = beta}."""
 
-    def __init__(self, Q, c, d, lb, ub, dual_radius=None, n_eq=0):
+    def __init__(self, Q, c, d, lb, ub, dual_radius=None, n_eq=0, hyperplane=None):
         self.dual_radius = None if dual_radius is None else float(dual_radius)
+        self.hyp = None if hyperplane is None else (np.asarray(hyperplane[0], np.float64), float(hyperplane[1]))
         self.n_eq = int(n_eq)            # the last n_eq constraints are equalities (free multipliers)
         self.Q = np.asarray(Q, dtype=np.float64)
         self.c = np.asarray(c, dtype=np.float64)
@@ -181,6 +302,9 @@ class Problem:
         h = data.numpy()
         if dual_radius is None:
             dual_radius = (data.meta or {}).get("dual_radius")
+        hyp = None
+        if getattr(data, "hyp_a", None) is not None:
+            hyp = (np.asarray(data.numpy().hyp_a, np.float64), float(data.hyp_beta))
         Q, c, d = data.dense_q(), h.c, h.d
         p = 0
         if getattr(h, "A_eq", None) is not None:
@@ -189,7 +313,7 @@ class Problem:
             Q = np.concatenate([Q, np.zeros((p, data.n, data.n), Q.dtype)], axis=0)
             c = np.concatenate([np.asarray(c, np.float64), A], axis=0)
             d = np.concatenate([np.asarray(d, np.float64), -np.asarray(h.b_eq, np.float64)])
-        return cls(Q, c, d, h.lb, h.ub, dual_radius, n_eq=p)
+        return cls(Q, c, d, h.lb, h.ub, dual_radius, n_eq=p, hyperplane=hyp)
 
     # objective and constraints --------------------------------------------
     def f(self, x):
@@ -221,6 +345,8 @@ class Problem:
         return self.phi(x, lam)
 
     def proj_x(self, x):
+        if self.hyp is not None:
+            return proj_box_hyperplane(x, self.lb, self.ub, self.hyp[0], self.hyp[1])[0]
         return np.minimum(np.maximum(x, self.lb), self.ub)
 
     def proj_y(self, lam):
@@ -402,7 +528,8 @@ def apdb(prob: Problem, x0, lam0, K: int, p: Params, log: dict | None = None):
 def kkt_residual(prob: Problem, x, lam):
     """Returns (rel_kkt, r_stat, r_feas) with
 
-      r_stat_j = dist(0, grad_x Phi(x, lam)_j + N_X(x)_j)   (box normal cone),
+      r_stat_j = dist(0, grad_x Phi(x, lam)_j + N_X(x)_j)   (box normal cone;
+                 with the hyperplane, ||r_stat|| = dist(0, grad + N_X(x))),
       r_feas_i = dist(0, -g_i(x) + N_{R+}(lam_i)),
                  (simplex dual: ||r_feas|| = dist(g(x), N_Delta(lam)); an
                  equality row contributes |a_k'x - b_k|),
@@ -416,10 +543,11 @@ def kkt_residual(prob: Problem, x, lam):
     for i in range(1, prob.m + 1):
         gc = gc + lam[i - 1] * (prob.Q[i] @ x + prob.c[i])
     grad = gf + gc
-    rs = np.where(x <= prob.lb, np.maximum(-grad, 0.0),
-                  np.where(x >= prob.ub, np.maximum(grad, 0.0), np.abs(grad)))
+    if prob.hyp is not None:        # dist(0, grad + N_X(x)) with the hyperplane's direction
+        r_stat = float(hyperplane_cone_distance(grad, x, prob.lb, prob.ub, prob.hyp[0])[0])
+    else:
+        r_stat = float(np.linalg.norm(box_cone_residual(grad, x, prob.lb, prob.ub)))
     g = prob.g(x)
-    r_stat = float(np.linalg.norm(rs))
     mi = prob.m_ineq
     if prob.dual_radius is not None and mi > 0:
         r_in = simplex_cone_distance(g[:mi], lam[:mi])[0]      # dist(0, -g + N_Delta(lam))
@@ -440,7 +568,9 @@ def gap_x_subproblem(prob: Problem, x, lam, xi):
     """argmin_{x' in X} Phi(x', lam) + xi ||x' - x||^2: a strongly convex box QP
     (Hessian Q(lam) + 2 xi I).  Solved exactly by bounded-variable least
     squares (an active-set method that terminates at the exact minimiser):
-    with H = L L', 0.5 x'Hx + l'x = 0.5||L'x + L^{-1} l||^2 - const."""
+    with H = L L', 0.5 x'Hx + l'x = 0.5||L'x + L^{-1} l||^2 - const.  With
+    the hyperplane a'x = beta in X, the equality's multiplier t is found by
+    bisection on a'x(t) = beta, x(t) the box QP's minimiser with l + t a."""
     from scipy.linalg import cholesky, solve_triangular
     from scipy.optimize import lsq_linear
     H = prob.Q[0].copy()
@@ -451,11 +581,34 @@ def gap_x_subproblem(prob: Problem, x, lam, xi):
     H = H + 2.0 * xi * np.eye(prob.n)
     lin = lin - 2.0 * xi * np.asarray(x, np.float64)
     L = cholesky(H, lower=True)
-    rhs = -solve_triangular(L, lin, lower=True)
     lb, ub = prob.lb, prob.ub
-    res = lsq_linear(L.T, rhs, bounds=(lb, ub), method="bvls", tol=1e-15,
-                     lsmr_tol=None, max_iter=None)
-    return prob.proj_x(res.x)
+
+    def box_qp(l):
+        rhs = -solve_triangular(L, l, lower=True)
+        res = lsq_linear(L.T, rhs, bounds=(lb, ub), method="bvls", tol=1e-15,
+                         lsmr_tol=None, max_iter=None)
+        return np.minimum(np.maximum(res.x, lb), ub)
+
+    if prob.hyp is None:
+        return box_qp(lin)
+    # X with the hyperplane a'x = beta: the box QP with the multiplier term
+    # t a'x; h(t) = a'x(t) - beta is non-increasing in t, bisected to the root
+    a, beta = prob.hyp
+    h = lambda t: float(a @ box_qp(lin + t * a)) - beta
+    t_lo, t_hi = -1.0, 1.0
+    while h(t_lo) < 0.0:
+        t_lo *= 2.0
+    while h(t_hi) > 0.0:
+        t_hi *= 2.0
+    for _ in range(200):
+        t = 0.5 * (t_lo + t_hi)
+        if t == t_lo or t == t_hi:
+            break
+        if h(t) > 0.0:
+            t_lo = t
+        else:
+            t_hi = t
+    return box_qp(lin + 0.5 * (t_lo + t_hi) * a)
 
 
 def smoothed_gap(prob: Problem, x, lam, xi):

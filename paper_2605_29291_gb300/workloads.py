@@ -16,7 +16,9 @@ The paper writes q_i for c_i and r_i for d_i.  Arrays returned:
         is diagonal (``q0diag`` holds its diagonal) or zero
     c   float32 (m+1, n), row 0 = c_0
     d   float32 (m,)
-    lb, ub float32 (n,)
+    lb, ub float32 (n,) (ub may be +inf)
+    hyp_a, hyp_beta  optional: the primal set is the box intersected with
+        {hyp_a'x = hyp_beta}
 
 Recipes:
   * ``random_qcqp``: Q_0 = A_0'A_0/n + ridge*I and Q_i = A_i'A_i/n with
@@ -61,6 +63,8 @@ class QCQPData:
     meta: dict = field(default_factory=dict)
     A_eq: object = None            # (p, n) float32: linear equalities A_eq x = b_eq (optional)
     b_eq: object = None            # (p,) float32
+    hyp_a: object = None           # (n,) float32: primal set box and {hyp_a'x = hyp_beta} (optional)
+    hyp_beta: float = 0.0
 
     @property
     def M(self) -> int:
@@ -74,7 +78,7 @@ class QCQPData:
             return a.detach().cpu().numpy()
         return QCQPData(self.n, self.m, h(self.Q), h(self.c), h(self.d), h(self.lb),
                         h(self.ub), self.q0_kind, h(self.q0diag), self.name, dict(self.meta),
-                        h(self.A_eq), h(self.b_eq))
+                        h(self.A_eq), h(self.b_eq), h(self.hyp_a), self.hyp_beta)
 
     def to(self, device) -> "QCQPData":
         """Copy of the data as contiguous float32 torch tensors on `device`."""
@@ -87,7 +91,8 @@ class QCQPData:
                 a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
             return a.to(device=device, dtype=torch.float32).contiguous()
         return QCQPData(self.n, self.m, t(self.Q), t(self.c), t(self.d), t(self.lb), t(self.ub),
-                        self.q0_kind, t(self.q0diag), self.name, dict(self.meta), t(self.A_eq), t(self.b_eq))
+                        self.q0_kind, t(self.q0diag), self.name, dict(self.meta), t(self.A_eq), t(self.b_eq),
+                        t(self.hyp_a), self.hyp_beta)
 
     def dense_q(self) -> np.ndarray:
         """(m+1, n, n) float32 host stack with Q_0 materialised (for the oracle)."""
@@ -260,7 +265,7 @@ def kml_qcqp(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0,
 
 
 def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: float = 1.0,
-               device=None, bias: bool = False) -> QCQPData:
+               device=None, bias: bool = False, primal_set: bool = False) -> QCQPData:
     """The kernel-learning min-max problem as the paper states it (Sec. 5.2,
     eq. min-max-KML), with the dual on the simplex:
 
@@ -271,7 +276,10 @@ def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: f
     c / r_i = m.  As QCQP data: Q_0 = 2 lam I (diagonal), c_0 = -2 1,
     Q_i = 2 m H(K_i), c_i = 0, d_i = 0; meta['dual_radius'] = 1.  With
     bias=True the paper's equality b'x = 0 (b the labels) is attached as
-    A_eq = b', b_eq = 0.  Same features and kernels as kml_qcqp."""
+    A_eq = b', b_eq = 0 (a constraint with a free multiplier).  With
+    primal_set=True the primal set is the paper's own, {x >= 0, b'x = 0}:
+    lb = 0, ub = +inf and the hyperplane hyp_a = b, hyp_beta = 0 (no upper
+    bound C).  Same features and kernels as kml_qcqp."""
     a, b = kml_features(n, dfeat, seed)
     specs = kml_kernel_specs(m)
     assert len(specs) == m
@@ -296,16 +304,19 @@ def kml_minmax(n: int, dfeat: int, m: int, seed: int = 0, C: float = 1.0, lam: f
     c[0] = -2.0
     d = np.zeros(m, np.float32)
     lb = np.zeros(n, np.float32)
-    ub = np.full(n, C, np.float32)
+    ub = np.full(n, np.inf if primal_set else C, np.float32)
     q0diag = np.full(n, 2.0 * lam, np.float32)
-    name = f"kml_minmax(n={n},d={dfeat},m={m},seed={seed}{',bias' if bias else ''})"
+    name = (f"kml_minmax(n={n},d={dfeat},m={m},seed={seed}{',bias' if bias else ''}"
+            f"{',primal_set' if primal_set else ''})")
     meta = {"dual_radius": 1.0}
     A_eq = b.astype(np.float32).reshape(1, n) if bias else None
     b_eq = np.zeros(1, np.float32) if bias else None
+    hyp_a = b.astype(np.float32) if primal_set else None
     if use_torch:
         t = lambda v: None if v is None else torch.from_numpy(v).to(device)
-        return QCQPData(n, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name, meta, t(A_eq), t(b_eq))
-    return QCQPData(n, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name, meta, A_eq, b_eq)
+        return QCQPData(n, m, Q, t(c), t(d), t(lb), t(ub), Q0_DIAG, t(q0diag), name, meta, t(A_eq), t(b_eq),
+                        t(hyp_a), 0.0)
+    return QCQPData(n, m, Q, c, d, lb, ub, Q0_DIAG, q0diag, name, meta, A_eq, b_eq, hyp_a, 0.0)
 
 
 def ball_qcqp(cvec: np.ndarray, rho: float, box: float = 10.0) -> QCQPData:
@@ -353,6 +364,10 @@ def config(name: str, device=None, seed: int = 0) -> QCQPData:
         return kml_minmax(5000, 20, 8, seed=seed, device=device, bias=True)
     if name == "C5mb":
         return kml_minmax(16000, 32, 20, seed=seed, device=device, bias=True)
+    if name == "C3mx":       # the paper's primal set {x >= 0, b'x = 0}
+        return kml_minmax(5000, 20, 8, seed=seed, device=device, primal_set=True)
+    if name == "C5mx":
+        return kml_minmax(16000, 32, 20, seed=seed, device=device, primal_set=True)
     if name == "P1":
         return paper_random_qcqp(1000, 10, seed=seed)
     raise KeyError(name)

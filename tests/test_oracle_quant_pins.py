@@ -68,6 +68,33 @@ def test_fp8_jacobi_is_symmetric_and_close(seed):
     assert err.max() <= 2.0 ** -4 + 2.0 ** -9
 
 
+def test_fp8_codes_are_symmetric_near_rounding_ties():
+    """The code of (j, k) equals the code of (k, j) even where the scaled
+    entry lies next to a tie between two E4M3 values: entries are placed at
+    the midpoints of adjacent codes, nudged by one float32 ulp either way, so
+    that forming (Q_jk r_j) r_k and (Q_jk r_k) r_j in float32 would round to
+    different codes for some of them."""
+    rng = np.random.default_rng(12)
+    vals = O.e4m3_decode_table()
+    pos = np.unique(vals[np.isfinite(vals) & (vals > 0) & (vals <= 256)])
+    mids = 0.5 * (pos[:-1] + pos[1:])
+    N = 200000
+    t = rng.choice(mids, N) * rng.choice([-1.0, 1.0], N)
+    rj = rng.uniform(0.3, 3.0, N).astype(np.float32)
+    rk = rng.uniform(0.3, 3.0, N).astype(np.float32)
+    q = (t / (256.0 * rj.astype(np.float64) * rk)).astype(np.float32)
+    q = np.where(rng.random(N) < 0.5, np.nextafter(q, np.float32(np.inf)), np.nextafter(q, np.float32(-np.inf)))
+    a = QZ.fp8_jacobi_codes(q, rj, rk)
+    b = QZ.fp8_jacobi_codes(q, rk, rj)
+    np.testing.assert_array_equal(a, b)
+    # the other order of the products does break the symmetry on these entries
+    left = ((q * rj).astype(np.float32) * rk).astype(np.float32)
+    right = ((q * rk).astype(np.float32) * rj).astype(np.float32)
+    e1 = QZ.e4m3_encode((left * np.float32(256)).astype(np.float32))
+    e2 = QZ.e4m3_encode((right * np.float32(256)).astype(np.float32))
+    assert np.any(e1 != e2)
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_fp8_entrywise_codes_equal_the_whole_matrix_quantiser(seed):
     """Codes of sampled rows and of single columns, computed entry by entry,
