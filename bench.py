@@ -158,14 +158,18 @@ def timed_solve(R, torch, data, p, dev, reps=2):
         x.zero_()
         y.zero_()
         infos.append(s.solve(x, y))
-    ms, b = s.time_pass(reps=10, level=0)      # the pass over the stored matrices
+    # the trial pass the solve ran: the packed quantised tiles (level 6) of a
+    # quantised packed context, the packed float32 tiles (level 5), else the
+    # stored matrices (level 0)
+    lv = 6 if (p.pack_sym and p.storage != R.F32) else (5 if p.pack_sym else 0)
+    ms, b = s.time_pass(reps=10, level=lv)
     tile = s.tile()
     s.close()
     t = statistics.median(i["seconds"] for i in infos)
     return {"time_to_tol_s": t, "iters": infos[-1]["iters"], "passes": infos[-1]["passes"],
-            "precision_switches": infos[-1]["precision_switches"], "rel_kkt": infos[-1]["rel_kkt"],
-            "status": infos[-1]["status"], "iters_per_s": infos[-1]["iters"] / t,
-            "stored_pass_gbs": b / (ms * 1e-3) / 1e9, "stored_pass_bytes": b, "tile": tile}
+            "precision_switches": infos[-1]["precision_switches"], "switch_iter": infos[-1]["switch_iter"],
+            "rel_kkt": infos[-1]["rel_kkt"], "status": infos[-1]["status"], "iters_per_s": infos[-1]["iters"] / t,
+            "trial_tile_gbs": b / (ms * 1e-3) / 1e9, "trial_tile_bytes": b, "trial_tile_level": lv, "tile": tile}
 
 
 def log(msg):
@@ -193,6 +197,89 @@ def oracle_sample(data, budget_s: float):
     del prob
     return {"iters": r.iters, "trials": r.trials, "seconds": dt, "setup_s": t_setup, "probe_s": one,
             "cores": os.cpu_count()}
+
+
+def certify_f_star(paper_random):
+    """The oracle's float64 relative KKT residual and objective at the float64
+    point of every f* solve of the paper-shaped runs (the certificate of the
+    f* used by the paper's termination measure)."""
+    import oracle as O
+    from paper_2605_29291_gb300 import workloads as W
+    for ref in paper_random["f_star_solves"]:
+        prob = O.Problem.from_data(W.paper_random_qcqp(1000, 10, seed=ref["seed"]))
+        x64, y64 = ref.pop("x64"), ref.pop("y64")
+        rel, rs, rf = O.kkt_residual(prob, x64, y64)
+        ref["oracle_rel_kkt"] = rel
+        ref["oracle_f"] = float(prob.f(x64))
+        ref["f_star_gap_vs_oracle_f"] = abs(ref["oracle_f"] - ref["f_star"]) / (1.0 + abs(ref["oracle_f"]))
+        del prob
+
+
+def oracle_timed(prob, p, max_iter):
+    """Wall time of one oracle rAPDB run of at most max_iter iterations."""
+    import oracle as O
+    p.max_iter = max_iter
+    t = time.time()
+    r = O.rapdb(prob, p=p)
+    return r, time.time() - t
+
+
+def cpu_baselines(gpu_batched=None):
+    """The FP64 oracle on the host cores for the other named workloads: full
+    solves to rel KKT 1e-6 where the oracle finishes in seconds (C1, one P1
+    instance), fixed iteration slices of the kernel-learning workloads (C3,
+    C3m), and a sample of the batched workload scaled to all 256 instances
+    (extrapolated, labelled).  The n = 16001 kernel-learning stack (C5) is not
+    run: as dense float64 it needs 43 GB of host memory."""
+    import numpy as np
+    import oracle as O
+    from paper_2605_29291_gb300 import workloads as W
+    cores = os.cpu_count()
+    out = {}
+    # C1: the small oracle-sized case, full solve
+    prob = O.Problem.from_data(W.config("C1"))
+    r, dt = oracle_timed(prob, O.default_params("yx", restart="fixed", restart_period=200, tol=1e-6), 20000)
+    out["C1_n200_m10"] = {"value": r.iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                          "time_to_tol_s": dt if r.status == 0 else None, "iters": r.iters,
+                          "rel_kkt": r.rel_kkt, "status": r.status,
+                          "sample": "full oracle solve to rel KKT 1e-6, rAPDB-yx non-monotone, restart every 200"}
+    # P1: the paper-shaped random QCQP, seed 0, full solve (the paper's K = 400)
+    prob = O.Problem.from_data(W.config("P1"))
+    r, dt = oracle_timed(prob, O.default_params("yx", restart="fixed", restart_period=400, tol=1e-6), 5000)
+    out["P1_n1000_m10"] = {"value": r.iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                           "time_to_tol_s": dt if r.status == 0 else None, "iters": r.iters,
+                           "rel_kkt": r.rel_kkt, "status": r.status,
+                           "sample": "full oracle solve of instance 0 to rel KKT 1e-6, rAPDB-yx non-monotone, "
+                                     "restart every 400"}
+    del prob
+    # C3 / C3m: 20-iteration slices of the kernel-learning workloads
+    for key, cfg, kw in (("C3_kml_n5001_m8", "C3", dict(restart="gap", gap_first=50, gap_every=500)),
+                         ("C3m_kml_minmax_n5000_m8", "C3mb", dict(restart="none", mu=2.0))):
+        prob = O.Problem.from_data(W.config(cfg))
+        r, dt = oracle_timed(prob, O.default_params("yx", tol=0.0, **kw), 20)
+        out[key] = {"value": r.iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                    "s_per_iter": dt / max(r.iters, 1), "s_per_pass": dt / max(r.trials, 1),
+                    "iters": r.iters, "status": r.status,
+                    "sample": f"a {r.iters}-iteration slice ({r.trials} trials) of the FP64 oracle"}
+        del prob
+    # C4: 20-iteration slices of 32 of the 256 batched instances
+    datas = W.batched_random_qcqp(256, seed=0)
+    secs, its = 0.0, 0
+    for d in datas[:32]:
+        prob = O.Problem.from_data(d)
+        r, dt = oracle_timed(prob, O.default_params("yx", tol=0.0), 20)
+        secs += dt
+        its += r.iters
+    c4 = {"value": its / secs, "unit": "iters/s", "cores": cores, "kind": "oracle",
+          "sample": f"20-iteration slices of 32 of the 256 instances ({its} iterations in {secs:.1f} s)"}
+    if gpu_batched is not None:
+        c4["extrapolated_batch_s"] = gpu_batched["iters_total"] * secs / its
+        c4["extrapolated_note"] = ("the batch's total GPU iteration count times the oracle's mean seconds per "
+                                   "iteration on the sample (extrapolated)")
+    out["C4_batched_256"] = c4
+    out["C5_kml_n16001_m20"] = {"value": None, "unit": "iters/s", "kind": "oracle",
+                                "sample": "not run: the dense float64 stack needs 43 GB of host memory"}
+    return out
 
 
 def run_batched(R, torch, dev, count=256, sample=32):
@@ -246,8 +333,9 @@ def run_paper_random(R, torch, dev, seeds=(0, 1, 2, 3), eps=1e-7, cap=50000):
     0), four instances, box [-10, 10].  Per method: iterations until the
     paper's termination measure max(|f - f*|/(1+|f*|), mean_i max(g_i, 0))
     <= eps, from the logged f(x^k) and constraint violation of each iteration.
-    f* comes from a tight solve of the same instance (its relative KKT
-    residual is reported beside it); the paper used MOSEK's."""
+    f* comes from a tight solve of the same instance; the paper used MOSEK's.
+    The float64 point of that solve is kept so that the CPU leg can certify
+    it with the oracle's own residual and objective (certify_f_star)."""
     import numpy as np
     from paper_2605_29291_gb300 import workloads as W
     out = {"eps": eps, "instances": len(seeds), "methods": {}}
@@ -261,9 +349,11 @@ def run_paper_random(R, torch, dev, seeds=(0, 1, 2, 3), eps=1e-7, cap=50000):
         x = torch.zeros(data.n, device=dev)
         y = torch.zeros(data.m, device=dev)
         iref = sref.solve(x, y, check=False)
+        x64, y64 = sref.solution_f64()
         sref.close()
         fstar = iref["obj"]
-        refs.append({"seed": seed, "f_star": fstar, "rel_kkt": iref["rel_kkt"], "iters": iref["iters"]})
+        refs.append({"seed": seed, "f_star": fstar, "rel_kkt": iref["rel_kkt"], "iters": iref["iters"],
+                     "x64": x64.cpu().numpy(), "y64": y64.cpu().numpy()})
         for name, cfg, _ in PAPER_RANDOM_METHODS:
             kw = dict(c_nm=cfg["c_nm"], tol=1e-9, max_iter=cap, refine=1)
             if cfg["restart"] == "fixed":
@@ -490,7 +580,8 @@ def run_ours(args):
             for name, st in (("f32", R.F32), ("bf16", R.BF16), ("fp8", R.FP8)):
                 r_ = timed_solve(R, torch, ds, solver_params(R, storage=st, pack_sym=pack), dev, reps=1)
                 per_seed[name].append({"seed": seed, "time_to_tol_s": r_["time_to_tol_s"], "iters": r_["iters"],
-                                       "passes": r_["passes"], "rel_kkt": r_["rel_kkt"], "status": r_["status"]})
+                                       "passes": r_["passes"], "rel_kkt": r_["rel_kkt"], "status": r_["status"],
+                                       "switch_iter": r_["switch_iter"]})
             del ds
             torch.cuda.empty_cache()
             log(f"seed {seed}: " + ", ".join(f"{k} {v[-1]['time_to_tol_s']:.3f}s/{v[-1]['iters']}it"
@@ -525,37 +616,46 @@ def run_ours(args):
                 del dk, sk
                 torch.cuda.empty_cache()
                 log(f"{name}: {kml[name]}")
-            # the paper's own kernel-learning formulation: the min-max problem
-            # with the dual on the simplex and the bias equality b'x = 0 (Sec.
-            # 5.2), strongly convex in x with mu = 2 lambda = 2, non-monotone yx,
-            # to rel KKT 1e-6; without restarts (APDB-yx) and with the paper's
-            # restart every 200 iterations (one solve each; the context's graph
-            # is built at create)
-            runs = (("kml_minmax_n5000_m8_bf16", "C3mb", R.BF16, (("apdb", R.RESTART_NONE, 0),
-                                                                  ("rapdb_every_200", R.RESTART_FIXED, 0),
-                                                                  ("rapdb_every_200_warm_tau", R.RESTART_FIXED, 1))),
-                    ("kml_minmax_n16000_m20_fp8", "C5mb", R.FP8, (("apdb", R.RESTART_NONE, 0),)))
-            for name, cfg, st, modes in runs:
+            # the paper's own kernel-learning formulation (Sec. 5.2, eq.
+            # min-max-KML): the primal set {x >= 0, b'x = 0} (no upper
+            # bound), the dual on the simplex, strongly convex with mu = 2, to
+            # rel KKT 1e-6; APDB-yx (no restart) and the paper's rAPDB-yx with
+            # a restart every 200 iterations, float32 storage beside the
+            # quantised one (packed tiles)
+            runs = (("kml_minmax_n5000_m8", "C3mx", ((R.F32, "f32"), (R.BF16, "bf16")),
+                     (("apdb", R.RESTART_NONE), ("rapdb_every_200", R.RESTART_FIXED))),
+                    ("kml_minmax_n16000_m20", "C5mx", ((R.F32, "f32"), (R.FP8, "fp8")),
+                     (("apdb", R.RESTART_NONE),)))
+            for name, cfg, storages, modes in runs:
                 dk = W.config(cfg, device=dev)
-                kml[name] = {"n": dk.n, "m": dk.m}
-                for mode, rs, warm in modes:
-                    pk = R.Params.default(R.YX, c_nm=1, mu=2.0, storage=st, refine=1, tol=1e-6, max_iter=20000,
-                                          time_limit_s=60.0, restart=rs, restart_period=200, restart_warm_tau=warm,
-                                          dual_set=R.DUAL_SIMPLEX, dual_radius=1.0)
-                    sk = R.Solver(dk, pk)
-                    xk = torch.zeros(dk.n, device=dev)
-                    yk = torch.zeros(sk.m, device=dev)        # simplex centre; equality multiplier 0
-                    yk[:dk.m] = 1.0 / dk.m
-                    ik = sk.solve(xk, yk, check=False)
-                    ms0, b0 = sk.time_pass(reps=10, level=0)
-                    kml[name][mode] = {"iters": ik["iters"], "passes": ik["passes"], "time_to_tol_s": ik["seconds"],
-                                       "iters_per_s": ik["iters"] / ik["seconds"], "rel_kkt": ik["rel_kkt"],
-                                       "status": ik["status"], "precision_switches": ik["precision_switches"],
-                                       "stored_pass_gbs": b0 / (ms0 * 1e-3) / 1e9, "stored_pass_bytes": b0,
-                                       "tile": sk.tile()}
-                    sk.close()
-                    del sk
-                    log(f"{name} {mode}: {kml[name][mode]}")
+                kml[name] = {"n": dk.n, "m": dk.m, "primal_set": "x >= 0, b'x = 0"}
+                for st, stname in storages:
+                    for mode, rs in modes:
+                        pk = R.Params.default(R.YX, c_nm=1, mu=2.0, storage=st, refine=1, tol=1e-6, max_iter=20000,
+                                              time_limit_s=60.0, restart=rs, restart_period=200,
+                                              dual_set=R.DUAL_SIMPLEX, dual_radius=1.0, pack_sym=1)
+                        sk = R.Solver(dk, pk)
+                        xk = torch.zeros(dk.n, device=dev)
+                        yk = torch.full((sk.m,), 1.0 / dk.m, device=dev)      # the simplex's centre
+                        ik = sk.solve(xk, yk, check=False)
+                        lv = 6 if st != R.F32 else 5
+                        ms0, b0 = sk.time_pass(reps=10, level=lv)
+                        kml[name][f"{mode}_{stname}"] = {
+                            "iters": ik["iters"], "passes": ik["passes"], "time_to_tol_s": ik["seconds"],
+                            "iters_per_s": ik["iters"] / ik["seconds"], "rel_kkt": ik["rel_kkt"],
+                            "status": ik["status"], "precision_switches": ik["precision_switches"],
+                            "switch_iter": ik["switch_iter"], "trial_tile_gbs": b0 / (ms0 * 1e-3) / 1e9,
+                            "trial_tile_bytes": b0}
+                        sk.close()
+                        del sk
+                        log(f"{name} {mode} {stname}: {kml[name][f'{mode}_{stname}']}")
+                    torch.cuda.empty_cache()
+                for mode, _ in modes:
+                    f = kml[name].get(f"{mode}_f32")
+                    for stname in ("bf16", "fp8"):
+                        q = kml[name].get(f"{mode}_{stname}")
+                        if f and q and f["status"] == R.OK and q["status"] == R.OK:
+                            kml[name][f"{mode}_{stname}_speedup_vs_f32"] = f["time_to_tol_s"] / q["time_to_tol_s"]
                 del dk
                 torch.cuda.empty_cache()
             extras["kml"] = kml
@@ -573,6 +673,7 @@ def run_ours(args):
             summ["runs"] = per_seed
             extras["mixed_over_seeds"] = summ
     cpu = None
+    cpu_configs = None
     fp64_check = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
@@ -588,11 +689,36 @@ def run_ours(args):
                       "obj_fp64": float(prob.f(xa))}
         del prob
         smp = oracle_sample(hd, args.cpu_budget)
+        if "paper_random_qcqp" in extras:
+            certify_f_star(extras["paper_random_qcqp"])
+        cpu_configs = cpu_baselines(extras.get("batched"))
         cpu = {"value": smp["iters"] / smp["seconds"], "unit": "iters/s", "cores": smp["cores"],
                "kind": "oracle",
                "sample": f"{smp['iters']} FP64 oracle rAPDB iterations ({smp['trials']} trials) of the same "
                          f"instance in {smp['seconds']:.1f} s (numpy, BLAS default threads)"}
 
+    for ref in extras.get("paper_random_qcqp", {}).get("f_star_solves", []):
+        ref.pop("x64", None)
+        ref.pop("y64", None)
+    # the comparisons the metric names (plain vs mixed / batched), as scalars
+    # at the top of the line
+    summary = {}
+    if "batched" in extras:
+        bt = extras["batched"]
+        summary.update(batched_instances_per_s=bt["instances_per_s"], batched_seconds=bt["seconds"],
+                       batched_speedup_vs_sequential=bt["speedup_vs_sequential"],
+                       batched_converged=bt["converged"], batched_instances=bt["instances"])
+    if "mixed_over_seeds" in extras:
+        mo = extras["mixed_over_seeds"]
+        for name in ("bf16", "fp8"):
+            summary[f"mixed_{name}_speedup_median"] = mo.get(f"{name}_speedup_median")
+            summary[f"mixed_{name}_switch_iters"] = [extras["mixed"][name]["switch_iter"]] + \
+                [r_["switch_iter"] for r_ in mo["runs"][name]]
+    kml_ = extras.get("kml", {})
+    for key, name in (("kml_minmax_n5000_m8", "c3mx"), ("kml_minmax_n16000_m20", "c5mx")):
+        for k_, v_ in kml_.get(key, {}).items():
+            if k_.endswith("_speedup_vs_f32"):
+                summary[f"kml_{name}_{k_}"] = v_
     launches = sum(i["launches"] for i in infos)
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
@@ -605,8 +731,9 @@ def run_ours(args):
         "coupling_gbs_in_solve": passes_all * pass_bytes / t_max / 1e9,
         "rel_kkt": max(i["rel_kkt"] for i in infos), "all_converged": ok,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches),
-        "oracle_check": fp64_check, "extras": extras,
+        "oracle_check": fp64_check, "cpu_baseline_configs": cpu_configs, "extras": extras,
     }
+    line.update(summary)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -93,7 +93,14 @@ typedef struct {
                               /*    switches to them when a precision check (restart  */
                               /*    boundaries, every restart_period/4 iterations)    */
                               /*    finds a stall, the stored problem solved, or the  */
-                              /*    true residual above twice the stored level's      */
+                              /*    true residual above twice the stored level's.     */
+                              /*    BF16/FP8 storage with pack_sym starts instead at  */
+                              /*    the quantised-increment level: the trial products */
+                              /*    are U^k + Q~ d, the increment Q~ d read from the  */
+                              /*    packed BF16/FP8 tiles and U^k a compensated       */
+                              /*    float32 product re-formed (anchored) by the       */
+                              /*    precision check every 64 accepted iterations; a   */
+                              /*    stall there switches to the float32 tiles        */
   double stall_ratio;         /* stall: the true rel KKT fell by less than this factor */
                               /*    since the previous precision check               */
   int32_t max_iter, max_trials, kkt_every;
@@ -118,7 +125,10 @@ typedef struct {
                               /*    of Q), and the incremental trial passes and the   */
                               /*    smoothed gap's passes read each tile once for its */
                               /*    rows and, transposed, for its columns: half the   */
-                              /*    bytes of a row-streaming pass.                    */
+                              /*    bytes of a row-streaming pass.  BF16/FP8 storage  */
+                              /*    also keeps its codes in the same tiles (a half /  */
+                              /*    a quarter of the float32 tiles' bytes), read by   */
+                              /*    the trials of the quantised-increment level.      */
                               /*    Needs refine = 1, exactly symmetric Q_i (checked  */
                               /*    at create: RAPDB_ERR_INVALID) and a single-       */
                               /*    instance context; rows_per_block and              */
@@ -140,6 +150,8 @@ typedef struct {
   double obj;                 /* 0.5 x'Q_0 x + c_0'x at the returned x              */
   double seconds;             /* device time of the solve (CUDA events)             */
   int64_t launches;           /* kernels this call launched (device loop + set-up)  */
+  int32_t switch_iter;        /* iteration of the first precision switch (-1: none) */
+  int32_t reserved_;
 } rapdb_info;
 
 typedef struct rapdb_ctx rapdb_ctx;
@@ -150,7 +162,7 @@ typedef struct rapdb_ctx rapdb_ctx;
 void rapdb_default_params(rapdb_params *p, int32_t variant);
 
 /* Create a single-instance context.
- *   n  > 0 variables, m >= 0 constraints (m = 0: box-constrained QP, which
+ *   n  > 0 variables, 0 <= m <= 6400 constraints (m = 0: box-constrained QP, which
  *   needs q0_kind = DENSE so that one matrix is streamed).
  *   q0_kind: DENSE -> Q holds (m+1) matrices, Q_0 first; DIAG -> Q holds the
  *            m constraint matrices and q0diag (device, n) the diagonal of Q_0;
@@ -158,7 +170,8 @@ void rapdb_default_params(rapdb_params *p, int32_t variant);
  *   Q     device, (M, n, n) float32, M = m+1 (DENSE) or m; symmetric.
  *   c     device, (m+1, n): row 0 = c_0, row i = c_i.
  *   d     device, (m,): the constants d_i (may be NULL when m = 0).
- *   lb,ub device, (n,), lb <= ub, finite.
+ *   lb,ub device, (n,), lb <= ub.
+ *   lb,ub may be infinite (lb = -inf, ub = +inf) but not NaN.
  * Ownership: with F32 storage, n % 4 == 0 and Q 16-byte aligned the context
  * BORROWS Q (no copy): it must stay alive and unchanged until rapdb_destroy.
  * Otherwise the context owns a padded copy (F32 rows padded to a multiple of 4,
@@ -183,13 +196,44 @@ rapdb_status rapdb_create(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind
  * has m + p_eq entries, the equality multipliers last (any real start), and
  * the (m+1, n) arrays of rapdb_coupling_pass have m + p_eq + 1 rows.  Its
  * KKT component is |a_k'x - b_k|.  Errors as for rapdb_create, plus
- * RAPDB_ERR_INVALID for p_eq < 0, m + p_eq > 12800, NULL A_eq / b_eq with
+ * RAPDB_ERR_INVALID for p_eq < 0, m + p_eq > 6400, NULL A_eq / b_eq with
  * p_eq > 0 or a NaN in them. */
 rapdb_status rapdb_create_eq(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind,
                              const float *Q, const float *q0diag, const float *c,
                              const float *d, const float *lb, const float *ub,
                              int64_t p_eq, const float *A_eq, const float *b_eq,
                              const rapdb_params *p, void *stream);
+
+/* Optional parts of a problem beyond those of rapdb_create (zero-initialise
+ * and set what is used).
+ *   p_eq, A_eq, b_eq: linear equalities A_eq x = b_eq with free multipliers,
+ *     as for rapdb_create_eq.
+ *   x_hyp_a, x_hyp_beta: the primal set becomes X = {lb <= x <= ub,
+ *     x_hyp_a'x = x_hyp_beta} (x_hyp_a: device, n floats, copied; NULL keeps
+ *     the box).  The paper's kernel-learning problem (Sec. 5.2, eq.
+ *     min-max-KML) minimises over {x >= 0, b'x = 0}: lb = 0, ub = +inf (the
+ *     box may be unbounded on either side), a = b, beta = 0.  Every trial
+ *     point and every step of the smoothed gap's x-subproblem is projected
+ *     onto X: x = clamp(v - nu a, lb, ub) with the scalar nu for which
+ *     a'x = beta (found on one CTA in double-float arithmetic, to 1e-13 of
+ *     sum |a_j x_j| + |beta|), and the KKT residual's r_stat is
+ *     dist(0, grad_x L + N_X(x)), N_X(x) = {t a + N_box(x)}, minimised over t.
+ *     x0 must lie in X (|a'x0 - beta| <= 1e-6 (1 + sum |a_j x0_j| + |beta|)).
+ *     Single-instance contexts only. */
+typedef struct {
+  int64_t p_eq;
+  const float *A_eq;
+  const float *b_eq;
+  const float *x_hyp_a;
+  double x_hyp_beta;
+} rapdb_extras;
+
+/* rapdb_create with the optional parts in *ex (may be NULL: rapdb_create).
+ * Errors as for rapdb_create_eq, plus RAPDB_ERR_INVALID for a NaN, an
+ * infinite or an all-zero x_hyp_a. */
+rapdb_status rapdb_create_ex(rapdb_ctx **out, int64_t n, int64_t m, int32_t q0_kind, const float *Q,
+                             const float *q0diag, const float *c, const float *d, const float *lb,
+                             const float *ub, const rapdb_extras *ex, const rapdb_params *p, void *stream);
 
 /* Run rAPDB from (x, y) (device, n and m floats -- m + p_eq with equalities;
  * overwritten with the final iterate).  x must lie in the box; y in the dual
@@ -246,7 +290,10 @@ rapdb_status rapdb_coupling_pass(rapdb_ctx *ctx, const float *x, const float *v,
 /* The packed incremental pass of a pack_sym context (the form of its trial
  * passes, with zero low parts), for every STORED matrix Q_i in order (i = 0..m
  * when Q_0 is dense, i = 1..m otherwise; M matrices):
- *     W[s] = Q_i v,   U[s] = Uold[s] + W[s]   (rounded once from float64)
+ *     W[s] = Q_i v,   U[s] = Uold[s] + W[s]   (rounded once from double-float)
+ * where, in a BF16 / FP8 context, Q_i is the stored (quantised) matrix read
+ * from its packed tiles (the quantised-increment level's trials) and, with
+ * FP8, the right-hand side enters as s .* v and the rows are scaled by s
  * computed from the upper block triangle (each off-diagonal tile read once
  * for its rows and, transposed, for its columns) and, when dots is not NULL,
  *     dots[5*s + 0] = x'U[s], dots[5*s+1] = v'W[s], dots[5*s+2] = v'Uold[s],
@@ -269,13 +316,18 @@ rapdb_status rapdb_packed_pass(rapdb_ctx *ctx, const float *x, const float *v, c
  * (U = U^k + Q d: one float32 right-hand side added to the double-float
  * products at x^k), 4 = level 3 through the packed upper block triangle
  * (contexts created with pack_sym = 1; the form their trials use: the tile
- * kernel, then the row-block kernel), 5 = the tile kernel of level 4 alone.
+ * kernel, then the row-block kernel), 5 = the tile kernel of level 4 alone,
+ * 6 = the tile kernel over the packed BF16 / FP8 tiles of a quantised
+ * pack_sym context (the quantised-increment level's trials), 7 = level 6 with
+ * its row-block kernel; -1 in a context whose last solve ended at the
+ * quantised-increment level times level 7.
  * *ms_per_pass (host) receives the average duration of one launch,
  * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
  * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8); at
  * levels 4 and 5 the packed tiles, M * T(T+1)/2 * 128 * 128 * 4 with
- * T = ceil(n / 128).  Outputs go to context scratch; the solver state is not
- * changed.  RAPDB_ERR_INVALID
+ * T = ceil(n / 128); at levels 6 and 7 M * T(T+1)/2 * 128 * 128 * (2 | 1)
+ * (+ M * n * 4 scale bytes for FP8).  Outputs go to context scratch; the
+ * solver state is not changed.  RAPDB_ERR_INVALID
  * when the level does not exist in this context. */
 rapdb_status rapdb_time_pass(rapdb_ctx *ctx, int32_t reps, int32_t level, double *ms_per_pass,
                              int64_t *bytes_per_pass);
@@ -302,7 +354,14 @@ rapdb_status rapdb_set_log(rapdb_ctx *ctx, int32_t capacity, double *tau_log,
  * together in one device loop with per-instance step sizes, restart counters
  * and convergence flags.  Q_dense[b], c[b], d[b], lb[b], ub[b] are host arrays
  * of B device pointers with the layout of rapdb_create (Q_0 dense).  Data are
- * copied into one packed arena owned by the context (F32 storage only). */
+ * copied into one packed arena owned by the context (F32 storage only).
+ * Tiles: with rows_per_block = 0 the context autotunes at create.  The
+ * instances are grouped by size class (ceil(log2 n)); the largest instance of
+ * each class times every tile variant and rows per block (32, 64, 128) on the
+ * pass its trials run; one variant serves the whole batch (the one with the
+ * least time summed over the classes, weighted by their counts) and each class
+ * takes its fastest rows per block (rapdb_get_instance_tile reports them).
+ * With rows_per_block > 0 every instance takes that tile and pass_variant. */
 rapdb_status rapdb_create_batched(rapdb_ctx **out, int32_t B, const int64_t *n,
                                   const int64_t *m, const float *const *Q,
                                   const float *const *c, const float *const *d,
@@ -390,6 +449,12 @@ rapdb_status rapdb_coupling_pass_noalloc(int64_t n, int64_t m, const float *Q, c
  * CUDA call fails. */
 rapdb_status rapdb_wait_selftest(int32_t complete, int64_t limit_us, int32_t *gave_up, double *waited_ms,
                                  float *copied_sum);
+
+/* The tile of instance `instance` of a context (0 for a single-instance
+ * context): its rows per block and the context's tile variant (0..9, as
+ * rapdb_params.pass_variant).  RAPDB_ERR_INVALID for a bad instance. */
+rapdb_status rapdb_get_instance_tile(const rapdb_ctx *ctx, int32_t instance, int32_t *rows_per_block,
+                                     int32_t *variant);
 
 const char *rapdb_last_error(const rapdb_ctx *ctx);
 void rapdb_destroy(rapdb_ctx *ctx);

@@ -29,6 +29,7 @@ struct InstHost {
   Inst I;                      // device-pointer copy uploaded to the context's array
   int64_t q_bytes;             // bytes of stored Q read by one pass
   int64_t qp_bytes = 0;        // bytes of the packed tiles read by one packed pass
+  int64_t qpq_bytes = 0;       // ... of the quantised packed tiles (+ FP8 row scales)
 };
 
 }  // namespace
@@ -69,6 +70,7 @@ struct rapdb_ctx {
   int g_bodies = 0;
   int64_t launches = 0;        // kernels launched by the current call
   int pvar = 0;                // coupling-pass tile variant (kVarRPW / kVarUNR)
+  bool hyp = false;            // primal set with a hyperplane (two more kernels per body)
   int sym_grid = 0;            // pack_sym: CTAs of the row-streaming pass kernel (one resident wave)
   int sym_tile_grid = 0;       // ... and of the packed tile kernels (one CTA per SM)
   float tune_ms = 0.0f;        // autotuner: best pass time
@@ -126,6 +128,24 @@ void launch_plain(int storage, int vi, dim3 g, cudaStream_t s, const Inst* I, co
   if (storage == RAPDB_F32) launch_plain_f32(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
   else if (storage == RAPDB_BF16) launch_plain_bf16(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
   else launch_plain_fp8(vi, g, s, I, x, v, XS, VS, uold, U, W, part, level, xlo, Ulo, err);
+}
+
+// The packed tile kernels of a context's storage (the float32 tiles serve
+// every storage; the storage's own tiles serve the quantised level).
+void launch_sym_tiles(int storage, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C, const float* VS) {
+  if (storage == RAPDB_BF16) k_sym_tiles<RAPDB_BF16><<<g, NTS, sym_smem_bytes(), s>>>(I, S, C, VS);
+  else if (storage == RAPDB_FP8) k_sym_tiles<RAPDB_FP8><<<g, NTS, sym_smem_bytes(), s>>>(I, S, C, VS);
+  else k_sym_tiles<RAPDB_F32><<<g, NTS, sym_smem_bytes(), s>>>(I, S, C, VS);
+}
+void launch_sym_finish(int storage, dim3 g, cudaStream_t s, const Inst* I, State* S, Ctrl* C) {
+  if (storage == RAPDB_BF16) k_sym_finish<RAPDB_BF16><<<g, NT, 0, s>>>(I, S, C);
+  else if (storage == RAPDB_FP8) k_sym_finish<RAPDB_FP8><<<g, NT, 0, s>>>(I, S, C);
+  else k_sym_finish<RAPDB_F32><<<g, NT, 0, s>>>(I, S, C);
+}
+void launch_sym_plain(int storage, dim3 g, cudaStream_t s, const Inst* I, const float* v, int quant, int* err) {
+  if (storage == RAPDB_BF16) k_sym_plain<RAPDB_BF16><<<g, NTS, sym_smem_bytes(), s>>>(I, v, quant, err);
+  else if (storage == RAPDB_FP8) k_sym_plain<RAPDB_FP8><<<g, NTS, sym_smem_bytes(), s>>>(I, v, quant, err);
+  else k_sym_plain<RAPDB_F32><<<g, NTS, sym_smem_bytes(), s>>>(I, v, 0, err);
 }
 
 // NVTX range for the duration of a scope (set-up, solve, stand-alone pass
@@ -264,7 +284,7 @@ rapdb_status check_params(rapdb_ctx* ctx, const rapdb_params* p) {
 rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m64, int q0_kind, const float* Q,
                             const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
                             int rb_override, int64_t p_eq = 0, const float* A_eq = nullptr,
-                            const float* b_eq = nullptr) {
+                            const float* b_eq = nullptr, const float* hyp_a = nullptr, double hyp_beta = 0.0) {
   const rapdb_params& p = ctx->p;
   // inequalities 1..m_in with stored matrices, then p_eq linear equalities
   const int n = (int)n64, m_in = (int)m64, pe = (int)p_eq, m = m_in + pe;
@@ -390,15 +410,32 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
     CK(cudaMemcpy(dd + m_in, hdb.data(), (size_t)pe * 8, cudaMemcpyHostToDevice));
   }
   I.c = cc;
-  {
-    double* cdp = nullptr;
-    AL(cdp, (size_t)(m + 1) * ldv);
-    k_f2d<<<std::min<int64_t>(((int64_t)(m + 1) * ldv + 255) / 256, 4096), 256, 0, st>>>(cc, cdp, (int)((m + 1) * ldv));
-    I.cd = cdp;
-  }
   I.lb = lbp;
   I.ub = ubp;
   I.q0diag = q0d;
+  if (hyp_a) {
+    // primal set X = box with {a'x = beta}: a (padded with zeros), and the
+    // projection's and the cone residual's per-column pairs
+    std::vector<float> ha(n);
+    CK(cudaMemcpy(ha.data(), hyp_a, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    bool any = false;
+    for (float v : ha) {
+      if (!std::isfinite(v)) return fail(ctx, RAPDB_ERR_INVALID, "NaN or Inf in the hyperplane of X");
+      any = any || v != 0.0f;
+    }
+    if (!any || !std::isfinite(hyp_beta)) return fail(ctx, RAPDB_ERR_INVALID, "the hyperplane of X is degenerate");
+    float* da = nullptr;
+    AL(da, ldv);
+    CK(cudaMemcpyAsync(da, hyp_a, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    I.hyp_a = da;
+    I.hyp_beta = hyp_beta;
+    float2* hv = nullptr;
+    float2* hg = nullptr;
+    AL(hv, ldv);
+    AL(hg, ldv);
+    I.hv = hv;
+    I.hg = hg;
+  }
   I.dcon = dd;
   I.dnorm = sqrt(dn);
 
@@ -471,6 +508,20 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
     I.tsym = T;
     I.ntile = ntile;
     H.qp_bytes = (int64_t)M * ntile * STB * STB * 4;
+    if (p.storage != RAPDB_F32) {
+      // the stored BF16 / FP8 codes in the same tiles: the trial passes of
+      // the quantised level read these (a half / a quarter of the bytes)
+      const int EB = (p.storage == RAPDB_BF16) ? 2 : 1;
+      uint8_t* qq = nullptr;
+      AL(qq, (size_t)M * ntile * STB * STB * EB);
+      if (EB == 2)
+        k_pack_sym_codes<uint16_t><<<4096, 256, 0, st>>>((const uint16_t*)I.Q, I.ld, n, M, ntile, dtij, (uint16_t*)qq);
+      else
+        k_pack_sym_codes<uint8_t><<<4096, 256, 0, st>>>((const uint8_t*)I.Q, I.ld, n, M, ntile, dtij, qq);
+      CK(cudaGetLastError());
+      I.Qpq = qq;
+      H.qpq_bytes = (int64_t)M * ntile * STB * STB * EB + (EB == 1 ? (int64_t)M * n * 4 : 0);
+    }
   }
   I.P = make_devparams(p, ctx);
   return RAPDB_OK;
@@ -493,8 +544,8 @@ rapdb_status finalize_ctx(rapdb_ctx* ctx) {
   ctx->nvblk = (int)vmap.size();
   ctx->npblk = (int)pmap.size();
   ctx->mapped = B;
-  ctx->smem_vec = (size_t)2 * mmax * sizeof(double);
-  if (ctx->smem_vec > 200 * 1024) return fail(ctx, RAPDB_ERR_INVALID, "too many constraints (m > 12800)");
+  ctx->smem_vec = (size_t)mmax * VEC_SMEM_PER_CON;
+  if (mmax > RAPDB_MAX_CONSTRAINTS) return fail(ctx, RAPDB_ERR_INVALID, "too many constraints (m > 6400)");
   AL(ctx->d_vmap, vmap.size());
   AL(ctx->d_pmap, std::max<size_t>(pmap.size(), 1));
   CK(cudaMemcpyAsync(ctx->d_vmap, vmap.data(), vmap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -539,12 +590,18 @@ rapdb_status launch_body(rapdb_ctx* ctx, cudaStream_t s) {
   (void)blk;
   auto vec = [&]() { launch_vec(st, gv, sm, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_vmap, ctx->XS, ctx->VS); };
   vec();
+  if (ctx->hyp) {
+    // X with a hyperplane: the projection's scalar, then x column by column
+    k_hyp<0><<<1, NTH, 0, s>>>(ctx->d_inst, ctx->d_state);
+    vec();
+  }
   if (ctx->sym_grid > 0) {
     const Inst& I = ctx->hi[0].I;
     launch_pass_sym(st, dim3(ctx->sym_grid), s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS,
                     ctx->VS);
-    k_sym_tiles<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
-    k_sym_finish<0><<<I.M * I.tsym, NT, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
+    launch_sym_tiles(st, dim3(ctx->sym_tile_grid), s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->VS);
+    launch_sym_finish(st, dim3(I.M * I.tsym), s, ctx->d_inst, ctx->d_state, ctx->d_ctrl);
+    k_sym_ctrl<0><<<1, NT, 0, s>>>(ctx->d_inst, ctx->d_state, ctx->d_ctrl);
   } else if (ctx->npblk > 0)
     launch_pass(st, ctx->pvar, gp, s, ctx->d_inst, ctx->d_state, ctx->d_ctrl, ctx->d_pmap, ctx->XS, ctx->VS);
   if (ctx->variant == RAPDB_XY) vec();
@@ -629,7 +686,10 @@ rapdb_status run_loop(rapdb_ctx* ctx, int64_t max_bodies) {
       }
     }
     launched += per;
-    ctx->launches += (int64_t)per * (ctx->variant == RAPDB_XY ? 3 : 2);
+    // kernels per body: vector, pass (xy: a second vector kernel), and the
+    // packed tile, row-block and control kernels of a pack_sym context
+    ctx->launches +=
+        (int64_t)per * ((ctx->variant == RAPDB_XY ? 3 : 2) + (ctx->sym_grid > 0 ? 3 : 0) + (ctx->hyp ? 2 : 0));
     CK(cudaMemcpyAsync(&ctx->h_ctrl[slot], ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(ctx->ev[slot], st));
     pending++;
@@ -786,6 +846,106 @@ rapdb_status finish_standalone(rapdb_ctx* ctx) {
   return RAPDB_OK;
 }
 
+// Batched contexts: one tile variant for every instance's pass (the pass
+// kernel is launched once over all instances' blocks) and rows per block per
+// size class.  The instances are grouped by ceil(log2 n); for each class its
+// largest instance (M n^2) times every (variant, rows per block) on the pass
+// its trials run (the incremental compensated pass with refinement, else the
+// plain pass), CUDA events on the context's stream.  The variant with the
+// least time summed over the classes, weighted by their instance counts, is
+// kept, and each class takes its fastest rows per block for it.  The blocks
+// were sized for the smallest tile (32 rows).
+rapdb_status autotune_batched(rapdb_ctx* ctx) {
+  NvtxScope nvtx_scope("rapdb_autotune_batched");
+  cudaStream_t st = ctx->stream;
+  const int rbs[3] = {32, 64, 128};
+  std::map<int, std::vector<int>> cls;
+  for (int b = 0; b < ctx->B; ++b) {
+    int key = 0;
+    while ((1 << key) < ctx->hi[b].I.n) ++key;
+    cls[key].push_back(b);
+  }
+  std::vector<std::pair<int, int>> reps;            // (class key, representative instance)
+  for (auto& kv : cls) {
+    int best = kv.second[0];
+    for (int b : kv.second) {
+      const Inst& I = ctx->hi[b].I;
+      const Inst& J = ctx->hi[best].I;
+      if ((int64_t)I.M * I.n * I.n > (int64_t)J.M * J.n * J.n) best = b;
+    }
+    reps.push_back({kv.first, best});
+  }
+  const int nc = (int)reps.size();
+  std::vector<float> t((size_t)nc * NVAR * 3, 1e30f);
+  for (int c = 0; c < nc; ++c) {
+    const int b = reps[c].second;
+    Inst& I = ctx->hi[b].I;
+    const int rb0 = I.rb;
+    for (int ri = 0; ri < 3; ++ri) {
+      if (ri > 0 && rbs[ri] > 2 * I.n) break;
+      I.rb = rbs[ri];
+      I.nrb = (I.n + I.rb - 1) / I.rb;
+      CK(cudaMemcpyAsync(ctx->d_inst + b, &I, sizeof(Inst), cudaMemcpyHostToDevice, st));
+      const int grid = I.M * I.nrb;
+      const bool inc = I.P.refine && I.Ulo[0] != nullptr;
+      const int reps_n = 5;
+      for (int vi = 0; vi < NVAR; ++vi) {
+        auto go = [&]() {
+          if (inc)
+            launch_plain(RAPDB_F32, vi, dim3(grid), st, ctx->d_inst + b, I.xf[0], I.dv, nullptr, nullptr, I.U[0],
+                         ctx->tU, ctx->tW, ctx->tpart, 3, &ctx->d_ctrl->err, I.xl[0], ctx->tUo);
+          else
+            launch_plain(RAPDB_F32, vi, dim3(grid), st, ctx->d_inst + b, I.xf[0], I.dv, nullptr, nullptr, nullptr,
+                         ctx->tU, ctx->tW, ctx->tpart, 0, &ctx->d_ctrl->err);
+        };
+        go();
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->t0, st));
+        for (int r = 0; r < reps_n; ++r) go();
+        CK(cudaEventRecord(ctx->t1, st));
+        CK(cudaEventSynchronize(ctx->t1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+        t[((size_t)c * NVAR + vi) * 3 + ri] = ms / reps_n;
+      }
+    }
+    I.rb = rb0;
+    I.nrb = (I.n + I.rb - 1) / I.rb;
+  }
+  {
+    rapdb_status fs = finish_standalone(ctx);
+    if (fs != RAPDB_OK) return fs;
+  }
+  int best_v = 0;
+  double best_sum = 1e300;
+  for (int vi = 0; vi < NVAR; ++vi) {
+    double sum = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      float tmin = 1e30f;
+      for (int ri = 0; ri < 3; ++ri) tmin = std::min(tmin, t[((size_t)c * NVAR + vi) * 3 + ri]);
+      sum += (double)tmin * (double)cls[reps[c].first].size();
+    }
+    if (sum < best_sum) {
+      best_sum = sum;
+      best_v = vi;
+    }
+  }
+  ctx->pvar = best_v;
+  for (int c = 0; c < nc; ++c) {
+    int best_ri = 0;
+    for (int ri = 1; ri < 3; ++ri)
+      if (t[((size_t)c * NVAR + best_v) * 3 + ri] < t[((size_t)c * NVAR + best_v) * 3 + best_ri]) best_ri = ri;
+    for (int b : cls[reps[c].first]) {
+      Inst& I = ctx->hi[b].I;
+      I.rb = rbs[best_ri];
+      I.nrb = (I.n + I.rb - 1) / I.rb;
+    }
+  }
+  // block maps and the instance table over the tuned tiles (builds the graph)
+  return set_block_maps(ctx, std::vector<char>(ctx->B, 1));
+}
+
+
 static_assert(kVarRPW[SYM_ROW_VARIANT<RAPDB_F32>] == SYM_ROW_RPW<RAPDB_F32> &&
                   kVarUNR[SYM_ROW_VARIANT<RAPDB_F32>] == SYM_ROW_UNR<RAPDB_F32> &&
                   kVarRPW[SYM_ROW_VARIANT<RAPDB_FP8>] == SYM_ROW_RPW<RAPDB_FP8> &&
@@ -802,10 +962,15 @@ rapdb_status setup_sym(rapdb_ctx* ctx) {
   int dev = 0, nsm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK(cudaFuncSetAttribute(k_sym_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes()));
-  CK(cudaFuncSetAttribute(k_sym_plain<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes()));
+  const int smb = (int)sym_smem_bytes();
+  CK(cudaFuncSetAttribute(k_sym_tiles<RAPDB_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  CK(cudaFuncSetAttribute(k_sym_tiles<RAPDB_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  CK(cudaFuncSetAttribute(k_sym_tiles<RAPDB_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  CK(cudaFuncSetAttribute(k_sym_plain<RAPDB_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  CK(cudaFuncSetAttribute(k_sym_plain<RAPDB_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+  CK(cudaFuncSetAttribute(k_sym_plain<RAPDB_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
   int occ_tiles = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tiles, k_sym_tiles<0>, NTS, sym_smem_bytes()));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tiles, k_sym_tiles<RAPDB_F32>, NTS, sym_smem_bytes()));
   if (occ_tiles < 1) return fail(ctx, RAPDB_ERR_CUDA, "the packed tile kernel does not fit on an SM");
   const int64_t tiles = (int64_t)I.M * I.ntile;
   const int64_t items = (int64_t)I.M * I.nrb;
@@ -881,12 +1046,28 @@ rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_k
                              const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
                              int64_t p_eq, const float* A_eq, const float* b_eq, const rapdb_params* p,
                              void* stream) {
+  rapdb_extras ex{};
+  ex.p_eq = p_eq;
+  ex.A_eq = A_eq;
+  ex.b_eq = b_eq;
+  return rapdb_create_ex(out, n, m, q0_kind, Q, q0diag, c, d, lb, ub, &ex, p, stream);
+}
+
+rapdb_status rapdb_create_ex(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_kind, const float* Q,
+                             const float* q0diag, const float* c, const float* d, const float* lb, const float* ub,
+                             const rapdb_extras* ex, const rapdb_params* p, void* stream) {
   NvtxScope nvtx_scope("rapdb_create");
+  const int64_t p_eq = ex ? ex->p_eq : 0;
+  const float* A_eq = ex ? ex->A_eq : nullptr;
+  const float* b_eq = ex ? ex->b_eq : nullptr;
+  const float* hyp_a = ex ? ex->x_hyp_a : nullptr;
+  const double hyp_beta = ex ? ex->x_hyp_beta : 0.0;
   rapdb_ctx* ctx = nullptr;
   if (!out) return fail(nullptr, RAPDB_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (n <= 0 || m < 0 || n > (1 << 28) || m > 12800) return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes n, m");
-  if (p_eq < 0 || m + p_eq > 12800 || (p_eq > 0 && (!A_eq || !b_eq)))
+  if (n <= 0 || m < 0 || n > (1 << 28) || m > RAPDB_MAX_CONSTRAINTS)
+    return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes n, m");
+  if (p_eq < 0 || m + p_eq > RAPDB_MAX_CONSTRAINTS || (p_eq > 0 && (!A_eq || !b_eq)))
     return fail(nullptr, RAPDB_ERR_INVALID, "bad equality block (p_eq, A_eq, b_eq)");
   if (q0_kind < RAPDB_Q0_DENSE || q0_kind > RAPDB_Q0_ZERO) return fail(nullptr, RAPDB_ERR_INVALID, "bad q0_kind");
   const int64_t M = (q0_kind == RAPDB_Q0_DENSE) ? m + 1 : m;
@@ -907,7 +1088,8 @@ rapdb_status rapdb_create_eq(rapdb_ctx** out, int64_t n, int64_t m, int32_t q0_k
   rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
   if (s == RAPDB_OK)
     s = build_instance(ctx, ctx->hi[0], n, m, q0_kind, Q, q0diag, c, d, lb, ub, p->rows_per_block, p_eq, A_eq,
-                       b_eq);
+                       b_eq, hyp_a, hyp_beta);
+  ctx->hyp = hyp_a != nullptr;
   if (s == RAPDB_OK && p->storage == RAPDB_FP8) {
     const Inst& I = ctx->hi[0].I;
     s = dalloc(ctx, &ctx->XS, (size_t)std::max(I.M, 1) * I.ldv);
@@ -958,7 +1140,7 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
   if (p->storage != RAPDB_F32) return fail(nullptr, RAPDB_ERR_INVALID, "batched contexts use F32 storage");
   if (p->pack_sym) return fail(nullptr, RAPDB_ERR_INVALID, "pack_sym needs a single-instance context");
   for (int b = 0; b < B; ++b) {
-    if (n[b] <= 0 || m[b] < 0 || m[b] > 12800 || n[b] > (1 << 24))
+    if (n[b] <= 0 || m[b] < 0 || m[b] > RAPDB_MAX_CONSTRAINTS || n[b] > (1 << 24))
       return fail(nullptr, RAPDB_ERR_INVALID, "bad sizes in batch");
     if (!Q[b] || !c[b] || !lb[b] || !ub[b] || (m[b] > 0 && !d[b]))
       return fail(nullptr, RAPDB_ERR_INVALID, "NULL pointer in batch");
@@ -972,15 +1154,29 @@ rapdb_status rapdb_create_batched(rapdb_ctx** out, int32_t B, const int64_t* n, 
   ctx->batched = true;
   ctx->hi.resize(B);
   rapdb_status s = dalloc(ctx, &ctx->d_flags, 4);
+  // (with autotuning the blocks are sized for the smallest tile, 32 rows)
   for (int b = 0; b < B && s == RAPDB_OK; ++b)
     s = build_instance(ctx, ctx->hi[b], n[b], m[b], RAPDB_Q0_DENSE, Q[b], nullptr, c[b], d[b], lb[b], ub[b],
-                       p->rows_per_block > 0 ? p->rows_per_block : 64);
+                       p->rows_per_block > 0 ? p->rows_per_block : 32);
   if (s == RAPDB_OK) s = finalize_ctx(ctx);
-  // batched contexts take the tile from the parameters (rows_per_block > 0,
-  // pass_variant) or default to 64-row blocks of the pipelined register
-  // streaming variant (the fastest on the 256-instance workload)
-  if (s == RAPDB_OK) ctx->pvar = p->rows_per_block > 0 ? p->pass_variant : 6;
-  if (s == RAPDB_OK) s = build_graph(ctx, 32);
+  if (s == RAPDB_OK && p->rows_per_block > 0) {
+    // the tile from the parameters
+    ctx->pvar = p->pass_variant;
+    s = build_graph(ctx, 32);
+  } else if (s == RAPDB_OK) {
+    // autotuned tiles: stand-alone pass scratch for the largest instance
+    size_t mv = 1, mp = 1;
+    for (int b = 0; b < B; ++b) {
+      const Inst& I = ctx->hi[b].I;
+      mv = std::max(mv, (size_t)(I.m + 1) * I.ldv);
+      mp = std::max(mp, (size_t)std::max(I.M, 1) * NDOT * I.nrb);
+    }
+    s = dalloc(ctx, &ctx->tU, mv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tW, mv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tUo, mv);
+    if (s == RAPDB_OK) s = dalloc(ctx, &ctx->tpart, mp);
+    if (s == RAPDB_OK) s = autotune_batched(ctx);
+  }
   if (s != RAPDB_OK) {
     g_last_error = ctx->err;
     rapdb_destroy(ctx);
@@ -1013,7 +1209,8 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
     int flags[4];
     CK(cudaMemcpyAsync(flags, ctx->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (flags[0]) return fail(ctx, RAPDB_ERR_INVALID, "x0 outside the box");
+    if (flags[0] & 1) return fail(ctx, RAPDB_ERR_INVALID, "x0 outside the box");
+    if (flags[0] & 2) return fail(ctx, RAPDB_ERR_INVALID, "x0 not on the hyperplane of X");
     if (flags[1] & 1) return fail(ctx, RAPDB_ERR_INVALID, "y0 has a negative (or NaN) entry");
     if (flags[1] & 2) return fail(ctx, RAPDB_ERR_INVALID, "y0 is not on the dual simplex");
   }
@@ -1055,6 +1252,7 @@ static rapdb_status solve_common(rapdb_ctx* ctx, float* const* x, float* const* 
       o.trials = S.trials_total;
       o.restarts = S.restarts;
       o.precision_switches = S.switches;
+      o.switch_iter = S.switch_it;
       o.passes = S.passes;
       o.status = status;
       o.rel_kkt = S.rel_kkt;
@@ -1133,9 +1331,17 @@ rapdb_status rapdb_packed_pass(rapdb_ctx* ctx, const float* x, const float* v, c
   CK(cudaMemcpyAsync(vpad, v, rowb, cudaMemcpyDeviceToDevice, st));
   const size_t off = (size_t)I.s_off * I.ldv;
   CK(cudaMemcpy2DAsync(ctx->tUo + off, ldb, uold, rowb, rowb, (size_t)I.M, cudaMemcpyDeviceToDevice, st));
-  k_sym_plain<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), st>>>(ctx->d_inst, vpad, &ctx->d_ctrl->err);
+  // quantised contexts: the quantised tiles (the form of the trials at their
+  // quantised level); FP8 reads the pre-scaled right-hand sides s_s .* v
+  const int quant = I.Qpq ? 1 : 0;
+  const bool fp8 = quant && I.storage == RAPDB_FP8;
+  if (fp8)
+    k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, vpad, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS,
+                                      ctx->tvpart, 0);
+  launch_sym_plain(ctx->storage, dim3(ctx->sym_tile_grid), st, ctx->d_inst, fp8 ? ctx->VS : vpad, quant,
+                   &ctx->d_ctrl->err);
   k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, xpad, nullptr, vpad, ctx->tUo, nullptr, ctx->tU,
-                                                   nullptr, ctx->tW, I.spart);
+                                                   nullptr, ctx->tW, I.spart, fp8 ? I.qscale : nullptr);
   if (dots) {
     k_sym_dots<<<1, NT, 0, st>>>(ctx->d_inst, I.spart, ctx->tdots);
     CK(cudaMemcpyAsync(dots, ctx->tdots + (size_t)I.s_off * NDOT, (size_t)I.M * NDOT * sizeof(double),
@@ -1173,8 +1379,9 @@ rapdb_status rapdb_kkt_residual(rapdb_ctx* ctx, const float* x, const float* y, 
   launch_plain(I.storage, ctx->pvar, dim3(I.M * I.nrb), st, ctx->d_inst, xpad, xpad, ctx->XS, ctx->VS, nullptr, Ut,
                Wt, ctx->tpart, level, &ctx->d_ctrl->err, xzero, Ulo);
   k_dots_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tpart, ctx->tvpart, ctx->tdots, xpad, xpad);
+  if (I.hyp_a && level != 2) CK(cudaMemsetAsync(xzero, 0, (size_t)I.ldv * 4, st));
   k_kkt_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, ctx->ty, Ut, Ulo, ctx->tvpart);
-  k_kkt_final<<<1, 32, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout);
+  k_kkt_final<<<1, NT, 0, st>>>(ctx->d_inst, ctx->tvpart, ctx->tdots, ctx->ty, ctx->tg, ctx->tout, xpad, xzero);
   CK(cudaGetLastError());
   double out[4];
   CK(cudaMemcpyAsync(out, ctx->tout, sizeof(out), cudaMemcpyDeviceToHost, st));
@@ -1202,21 +1409,26 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     xcur = ctx->h_state[0].xcur;
     cur_level = ctx->h_state[0].precision;
   }
-  const int lv = level < 0 ? cur_level : level;
-  if (lv > 5 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
-      (lv == 1 && I.storage == RAPDB_F32) || (lv >= 4 && I.tsym == 0))
+  int lv = level < 0 ? cur_level : level;
+  if (level < 0 && cur_level == 3) lv = 7;     // the quantised level's trial pass
+  if (lv > 7 || (lv >= 1 && I.storage != RAPDB_F32 && !I.Q32) || (lv >= 2 && !I.Ulo[0]) ||
+      (lv == 1 && I.storage == RAPDB_F32) || (lv >= 4 && I.tsym == 0) || (lv >= 6 && !I.Qpq))
     return fail(ctx, RAPDB_ERR_INVALID, "precision level not available in this context");
   const float* x = I.xf[xcur];
   const float* v = I.dv;
-  if (I.storage == RAPDB_FP8 && lv == 0)
+  const bool fp8s = I.storage == RAPDB_FP8 && (lv == 0 || lv >= 6);   // pre-scaled right-hand sides
+  if (fp8s)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
   auto launch = [&]() {
     if (lv >= 4) {
-      k_sym_plain<0><<<ctx->sym_tile_grid, NTS, sym_smem_bytes(), st>>>(ctx->d_inst, v, &ctx->d_ctrl->err);
-      if (lv == 4)
+      const int quant = lv >= 6 ? 1 : 0;
+      launch_sym_plain(ctx->storage, dim3(ctx->sym_tile_grid), st, ctx->d_inst, (quant && fp8s) ? ctx->VS : v,
+                       quant, &ctx->d_ctrl->err);
+      if (lv == 4 || lv == 7)
         k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, x, I.xl[xcur], v, I.U[0], I.Ulo[0], ctx->tU,
-                                                         ctx->tUo, ctx->tW, I.spart);
+                                                         ctx->tUo, ctx->tW, I.spart,
+                                                         (quant && fp8s) ? I.qscale : nullptr);
     } else
       launch_plain(I.storage, ctx->pvar, dim3(grid), st, ctx->d_inst, x, v, ctx->XS, ctx->VS,
                    lv == 2 ? nullptr : I.U[0],
@@ -1241,6 +1453,7 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
     int64_t b = (int64_t)I.M * I.n * I.n * eb;
     if (I.storage == RAPDB_FP8 && lv == 0) b += (int64_t)I.M * I.n * 4;
     if (lv >= 4) b = ctx->hi[0].qp_bytes;
+    if (lv >= 6) b = ctx->hi[0].qpq_bytes;
     *bytes_per_pass = b;
   }
   return RAPDB_OK;
@@ -1276,6 +1489,14 @@ rapdb_status rapdb_set_log(rapdb_ctx* ctx, int32_t capacity, double* tau_log, in
   ctx->obj_log = capacity ? obj_log : nullptr;
   ctx->infeas_log = capacity ? infeas_log : nullptr;
   return upload_params(ctx);
+}
+
+rapdb_status rapdb_get_instance_tile(const rapdb_ctx* ctx, int32_t instance, int32_t* rows_per_block,
+                                     int32_t* variant) {
+  if (!ctx || instance < 0 || instance >= ctx->B) return RAPDB_ERR_INVALID;
+  if (rows_per_block) *rows_per_block = ctx->hi[instance].I.rb;
+  if (variant) *variant = ctx->pvar;
+  return RAPDB_OK;
 }
 
 rapdb_status rapdb_get_tile(const rapdb_ctx* ctx, int32_t* rows_per_block, int32_t* ctas, int32_t* rows_per_warp,

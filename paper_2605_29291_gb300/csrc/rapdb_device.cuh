@@ -34,6 +34,14 @@ constexpr int VCOL = 32;           // vector kernel: columns per CTA
 constexpr int NGRP = NT / VCOL;    // ... and constraint groups per column
 constexpr int NDOT = 5;            // dots per (matrix, row block)
 constexpr int NVP = 12;            // vector-kernel partials per column block
+static_assert(VCOL == 32, "constraint group 0 of the vector kernel is warp 0");
+// dynamic shared memory of the vector kernel per constraint: y and y~ in
+// float64 and as double-float pairs
+constexpr int VEC_SMEM_PER_CON = 2 * 8 + 2 * 8;
+// constraints (inequalities + equalities) per instance: the vector kernel's
+// per-constraint shared memory stays within 200 KB
+constexpr int RAPDB_MAX_CONSTRAINTS = 6400;
+static_assert(RAPDB_MAX_CONSTRAINTS * VEC_SMEM_PER_CON <= 200 * 1024, "vector kernel shared memory");
 
 // dot slots of one matrix i (pass output)
 enum DSlot : int { D_XU = 0, D_VW = 1, D_VUO = 2, D_CX = 3, D_CV = 4 };
@@ -49,6 +57,9 @@ enum Phase : int {
   PH_GAPP = 6,       // adaptive restart: power iterations for the x-subproblem's step
   PH_GAPF = 7,       // ... accelerated projected gradient on the x-subproblem
   PH_GAPV = 10,      // ... value of the smoothed gap and the restart decision
+  PH_ANCHOR = 11,    // compensated levels: U = Q x^k re-formed by a direct compensated product
+  PH_HYPN = 12,      // primal set with a hyperplane: the projection's scalar nu (one CTA) ...
+  PH_HYPX = 13,      // ... then x = clamp(v - nu a) and the column work of the phase it serves
   PH_DONE = 9
 };
 
@@ -97,10 +108,13 @@ struct Inst {
   const float* qscale;  // FP8: (M, ldv) symmetric scales s
   const float* q0diag;  // (ldv) diagonal of Q_0 when DIAG
   const float* c;       // (m+1, ldv)
-  const double* cd;     // (m+1, ldv): c in float64 (the vector kernel's constraint sums)
   const double* dcon;   // (m)
-  const float* lb;      // (ldv)
-  const float* ub;      // (ldv)
+  const float* lb;      // (ldv), may hold -inf
+  const float* ub;      // (ldv), may hold +inf
+  const float* hyp_a;   // (ldv) primal set X = box with {hyp_a'x = hyp_beta}; null: the box
+  double hyp_beta;
+  float2* hv;           // (ldv) the point to project onto X (double-float), vector kernel -> projection
+  float2* hg;           // (ldv) grad_x L at x^k (double-float), for dist(0, grad + N_X(x))
   double dnorm;         // ||d||_2 of the constants
   double* xb[2];        // x^k / x~ master copies (ldv each, padding zero)
   float* xf[2];         // float32 copies of xb: the pass right-hand side
@@ -121,7 +135,9 @@ struct Inst {
   const int* tij;       // (ntile) tile coordinates I << 16 | J, I <= J, row-major
   float* sp;            // (2, M, T, T * STB) tile products: slot J of the rows of block I,
                         // one set per right-hand side
-  double* spart;        // (M, NDOT, T) row-block dot partials of the packed pass
+  const void* Qpq;      // (M, ntile, STB, STB) BF16 / FP8 codes of the stored matrices in the same
+                        // tiles (quantised contexts with packing), read by the quantised level's trials
+  float2* spart;        // (M, NDOT, T) row-block dot partials of the packed pass (double-float pairs)
   int tsym, ntile;      // T = ceil(n / STB) (0: no packing), T (T + 1) / 2
   double* vpart;        // (ncb, NVP) vector partials
   double* dots;         // (m+1, NDOT) reduced dots
@@ -153,12 +169,20 @@ struct State {
   int k, it, trial, trials_total, passes, restarts, switches;
   int phase, status, fresh, restart_note, avg_pending;
   int xcur, ycur, ucur, gcur, gxcur;
-  int precision;        // 0: stored Q, 1: float32 Q, 2: float32 Q, compensated products
+  int precision;        // 0: stored Q, 1: float32 Q, 2: float32 Q, compensated products,
+                        // 3: compensated products whose trial increments Q~ d come from the
+                        //    quantised packed tiles (anchored by float32 compensated products)
+  int switch_it;        // iteration of the first precision switch (-1: none)
+  int hyp_ret;          // the phase a projection onto X serves (PH_TRIAL or PH_GAPF)
+  double hyp_nu;        // the last projection's nu (warm start of the next)
+  double hyp_t;         // the last normal-cone multiplier t of the KKT residual (warm start)
+  double gap_xval;      // smoothed gap: x-part objective at z_k, kept across the projection
   int gap_iter, gap_has_ref, gap_evals, trial_ready;
   int gap_it_done;      // iteration of the last smoothed-gap evaluation (-1: none)
   int check_level;      // precision level of the pending accurate KKT check (KKT32 / KKT32B)
   unsigned int arrive_vec, arrive_pass;
-  int anchor_age;       // level 2: accepted iterations since U was last formed by a direct product
+  int anchor_age;       // compensated levels: accepted iterations since U was last formed by a
+                        // direct product (an anchor pass follows after ANCHOR_EVERY)
   int check_due;        // a precision check runs at the next iteration's KKT test
 };
 
@@ -195,12 +219,115 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two
+// floats (about 48 significant bits).  This GPU runs float64 at a small
+// fraction of its float32 rate, so the per-row and per-column sums of the
+// solver's vector work use these pairs on the float32 pipe; float64 is kept
+// for the per-CTA partials and the scalar control.  The error-free
+// transformations are Knuth's TwoSum and the FMA-based TwoProduct; every
+// operation is an explicitly rounded intrinsic, so no contraction changes
+// them.  The accumulations follow the compensated dot product of Ogita, Rump
+// and Oishi (2005, Dot2): the rounding error of every addition and product is
+// summed alongside and folded in once at the end.
+// ---------------------------------------------------------------------------
+struct dflt {
+  float hi, lo;
+};
+// a + b = s + e exactly
+__device__ __forceinline__ void two_sumf(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// a + b = s + e exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ dflt fast_two_sumf(float a, float b) {
+  dflt r;
+  r.hi = __fadd_rn(a, b);
+  r.lo = __fsub_rn(b, __fsub_rn(r.hi, a));
+  return r;
+}
+__device__ __forceinline__ dflt df_norm(float hi, float lo) {
+  float s, e;
+  two_sumf(hi, lo, s, e);
+  return dflt{s, e};
+}
+__device__ __forceinline__ dflt df_from_double(double v) {
+  const float h = (float)v;
+  return dflt{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(dflt a) { return (double)a.hi + (double)a.lo; }
+// normalised sum of two pairs
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  float s, e;
+  two_sumf(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+// Compensated accumulator: acc.hi += p exactly up to the error term that goes
+// to acc.lo together with the caller's own error term pe.
+__device__ __forceinline__ void df_acc(dflt& acc, float p, float pe) {
+  float s, e;
+  two_sumf(acc.hi, p, s, e);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+// acc += a * b for pairs a, b (the lo * lo term is below the pair's precision)
+__device__ __forceinline__ void df_acc_mul(dflt& acc, dflt a, dflt b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  df_acc(acc, p, pe);
+}
+// acc += a * f for a pair a and a float f
+__device__ __forceinline__ void df_acc_mulf(dflt& acc, dflt a, float f) {
+  const float p = __fmul_rn(a.hi, f);
+  const float pe = __fmaf_rn(a.lo, f, __fmaf_rn(a.hi, f, -p));
+  df_acc(acc, p, pe);
+}
+// Sum of len >= 1 pairs src[0..len-1] in index order (L2 loads issued eight
+// at a time, so the adds do not wait on one load after another).
+__device__ __forceinline__ dflt df_sum_pairs(const float2* __restrict__ src, int len) {
+  float2 p0 = __ldcg(src);
+  dflt t = {p0.x, p0.y};
+  int r = 1;
+  for (; r + 8 <= len; r += 8) {
+    float2 b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) b[u] = __ldcg(src + r + u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t = df_add(t, dflt{b[u].x, b[u].y});
+  }
+  for (; r < len; ++r) {
+    const float2 p = __ldcg(src + r);
+    t = df_add(t, dflt{p.x, p.y});
+  }
+  return t;
+}
+
+// Fixed-order sum over the 32 lanes (xor butterfly); every lane gets the same
+// sum (df_add is symmetric in its arguments: TwoSum's error term is exact).
+__device__ __forceinline__ dflt df_warp_sum(dflt a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dflt b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a = df_add(a, b);
+  }
+  return a;
+}
+
 // Deterministic CTA sum of K doubles per thread; result valid in thread 0.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* NWARP*K */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // a warp whose lanes all hold zero skips its float64 butterfly (the sum is
+  // zero either way); the control steps often have data in one or two warps
 #pragma unroll
-  for (int q = 0; q < K; ++q) v[q] = warp_sum(v[q]);
+  for (int q = 0; q < K; ++q)
+    if (__any_sync(0xffffffffu, v[q] != 0.0)) v[q] = warp_sum(v[q]);
   if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < K; ++q) smem[warp * K + q] = v[q];
@@ -297,6 +424,179 @@ __device__ __forceinline__ double simplex_cone_t_serial(const double* g, const d
     if (c == 0) break;
   }
   return t;
+}
+
+// ---------------------------------------------------------------------------
+// Primal set with one hyperplane, X = {lb <= x <= ub, a'x = beta} (the
+// kernel-learning problem of Sec. 5.2 minimises over {x >= 0, b'x = 0}).
+// Block-wide routines (any blockDim that is a multiple of 32) in
+// double-float arithmetic; `sm` holds blockDim/32 + 2 float2 and `sb` 2
+// doubles of shared memory.
+// ---------------------------------------------------------------------------
+// Fixed-order CTA sum of a pair and of a float; every thread gets both.
+__device__ __forceinline__ void df_block_allsum(dflt& a, float& f, float2* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = df_warp_sum(a);
+  f = warp_sumf(f);
+  if (lane == 0) sm[warp] = make_float2(a.hi, a.lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dflt t = {sm[0].x, sm[0].y};
+    for (int w = 1; w < nw; ++w) t = df_add(t, dflt{sm[w].x, sm[w].y});
+    sm[nw] = make_float2(t.hi, t.lo);
+  }
+  __syncthreads();
+  if (lane == 0) sm[warp] = make_float2(f, 0.f);
+  const float2 r = sm[nw];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = sm[0].x;
+    for (int w = 1; w < nw; ++w) t += sm[w].x;
+    sm[nw + 1] = make_float2(t, 0.f);
+  }
+  __syncthreads();
+  a = dflt{r.x, r.y};
+  f = sm[nw + 1].x;
+  __syncthreads();
+}
+
+// x at a bound of the box, compared in double-float (x = xh + xl)
+__device__ __forceinline__ bool df_at_or_below(float xh, float xl, float b) { return xh < b || (xh == b && xl <= 0.f); }
+__device__ __forceinline__ bool df_at_or_above(float xh, float xl, float b) { return xh > b || (xh == b && xl >= 0.f); }
+
+// phi(nu) = a'clamp(v - nu a, lb, ub) - beta over the CTA (v = I.hv as pairs),
+// the slope -sum over the free coordinates of a_j^2, and sum |a_j x_j|.
+__device__ __forceinline__ void hyp_phi(const Inst& I, dflt nu, dflt& phi, float& slope, float& mag, float2* sm) {
+  dflt acc = {0.f, 0.f};
+  float sl = 0.f, mg = 0.f;
+  for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+    const float aj = I.hyp_a[j];
+    const float2 vv = I.hv[j];
+    dflt na = {0.f, 0.f};
+    df_acc_mulf(na, nu, aj);
+    const dflt t = df_add(dflt{vv.x, vv.y}, dflt{-na.hi, -na.lo});
+    const float lo = I.lb[j], hi = I.ub[j];
+    dflt x;
+    if (df_at_or_below(t.hi, t.lo, lo)) x = dflt{lo, 0.f};
+    else if (df_at_or_above(t.hi, t.lo, hi)) x = dflt{hi, 0.f};
+    else {
+      x = t;
+      sl = fmaf(aj, aj, sl);
+    }
+    df_acc_mulf(acc, x, aj);
+    mg = fmaf(fabsf(aj), fabsf(x.hi), mg);
+  }
+  dflt a2 = df_norm(acc.hi, acc.lo);
+  df_block_allsum(a2, sl, sm);
+  dflt m2 = {0.f, 0.f};
+  df_block_allsum(m2, mg, sm);
+  phi = df_add(a2, df_from_double(-I.hyp_beta));
+  slope = -sl;
+  mag = mg;
+}
+
+// The scalar nu of the projection onto X: the root of phi, continuous,
+// piecewise linear and non-increasing, by Newton steps on its current piece
+// safeguarded by a bracket (bisection when a step leaves it, doubling while
+// one side is open), from the warm start nu0.  It stops when |phi| is below
+// 1e-13 of sum |a_j x_j| + |beta| (the pair arithmetic's precision), or after
+// 200 steps.  Every thread returns the same nu.
+__device__ __forceinline__ double hyp_proj_nu(const Inst& I, double nu0, float2* sm, double* sb) {
+  double nu = nu0, lo = -INFINITY, hi = INFINITY;
+  for (int it = 0; it < 200; ++it) {
+    dflt ph;
+    float sl, mg;
+    hyp_phi(I, df_from_double(nu), ph, sl, mg, sm);
+    if (threadIdx.x == 0) {
+      const double phi = df_to_double(ph);
+      int done = fabs(phi) <= 1e-13 * ((double)mg + fabs(I.hyp_beta)) || !(phi == phi);
+      double cand = nu;
+      if (!done) {
+        if (phi > 0.0) lo = nu;
+        else hi = nu;
+        cand = (sl < 0.f) ? nu - phi / (double)sl : NAN;
+        if (!(cand > lo && cand < hi)) {
+          if (isfinite(lo) && isfinite(hi)) cand = 0.5 * (lo + hi);
+          else if (isfinite(lo)) cand = lo + fmax(1.0, 2.0 * fabs(lo));
+          else cand = hi - fmax(1.0, 2.0 * fabs(hi));
+        }
+        if (cand == nu) done = 1;
+      }
+      sb[0] = cand;
+      sb[1] = done ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    nu = sb[0];
+    const bool done = sb[1] != 0.0;
+    __syncthreads();
+    if (done) break;
+  }
+  return nu;
+}
+
+// ||r_stat||^2 = min over t of sum_j rho_j(g_j + t a_j)^2 for X with the
+// hyperplane: rho_j(h) = max(-h, 0) at a lower bound, max(h, 0) at an upper
+// bound, |h| inside (dist(0, g + N_X(x)), N_X(x) = {t a + N_box(x)}).  The
+// function of t is convex and continuously differentiable; its derivative's
+// root is found by safeguarded Newton steps from the warm start t0.  g = I.hg
+// (pairs), x = xh + xl.  Every thread returns the value; *t_out the t.
+__device__ __forceinline__ double hyp_cone_rs2(const Inst& I, const float* __restrict__ xh,
+                                               const float* __restrict__ xl, double t0, double* t_out,
+                                               float2* sm, double* sb) {
+  double t = t0, lo = -INFINITY, hi = INFINITY;
+  float F = 0.f;
+  for (int it = 0; it < 200; ++it) {
+    const dflt td = df_from_double(t);
+    dflt d1 = {0.f, 0.f};
+    float d2 = 0.f, f = 0.f;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+      const float aj = I.hyp_a[j];
+      const float2 g = I.hg[j];
+      dflt ta = {0.f, 0.f};
+      df_acc_mulf(ta, td, aj);
+      const float h = df_add(dflt{g.x, g.y}, ta).hi;
+      const bool at_lo = df_at_or_below(xh[j], xl[j], I.lb[j]);
+      const bool at_hi = df_at_or_above(xh[j], xl[j], I.ub[j]);
+      const bool act = !(at_lo || at_hi) || (at_lo && h < 0.f) || (at_hi && h > 0.f);
+      if (act) {
+        const float p = __fmul_rn(aj, h);
+        df_acc(d1, p, __fmaf_rn(aj, h, -p));
+        d2 = fmaf(aj, aj, d2);
+        f = fmaf(h, h, f);
+      }
+    }
+    dflt D = df_norm(d1.hi, d1.lo);
+    df_block_allsum(D, d2, sm);
+    dflt z = {0.f, 0.f};
+    df_block_allsum(z, f, sm);
+    F = f;
+    if (threadIdx.x == 0) {
+      const double Dv = df_to_double(D);
+      int done = !(Dv != 0.0) || !(d2 > 0.f);
+      double cand = t;
+      if (!done) {
+        if (Dv < 0.0) lo = t;
+        else hi = t;
+        cand = t - Dv / (double)d2;
+        if (!(cand > lo && cand < hi)) {
+          if (isfinite(lo) && isfinite(hi)) cand = 0.5 * (lo + hi);
+          else if (isfinite(lo)) cand = lo + fmax(1.0, 2.0 * fabs(lo));
+          else cand = hi - fmax(1.0, 2.0 * fabs(hi));
+        }
+        // stop once the step no longer moves t (the piece's minimiser)
+        if (fabs(cand - t) <= 1e-12 * (1.0 + fabs(t))) done = 1;
+      }
+      sb[0] = done ? t : cand;
+      sb[1] = done ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    t = sb[0];
+    const bool done = sb[1] != 0.0;
+    __syncthreads();
+    if (done) break;
+  }
+  if (t_out) *t_out = t;
+  return (double)F;
 }
 
 // Arrival on a per-instance counter after this CTA's partials are written.
@@ -1045,10 +1345,10 @@ __device__ __forceinline__ void pass_block_prec2(const float* __restrict__ Qf, i
 // storage), for trial points x~ = x^k + d: U' = U^k + Q d, with U^k the
 // double-float products at x^k (uoh + uol) and Q d formed in float32 (one
 // right-hand side).  Algebraically U' = Q x~; the float32 rounding of Q d is
-// of the order of eps_32 |Q||d|, so it vanishes with the step, and the
-// caller re-forms U by a direct compensated product every ANCHOR_EVERY
-// accepted iterations so that these roundings cannot add up.  Outputs and
-// dots as in pass_block_prec2.
+// of the order of eps_32 |Q||d|, so it vanishes with the step, and after
+// every ANCHOR_EVERY accepted iterations an anchor pass re-forms U at the
+// accepted iterate by a direct compensated product, so that these roundings
+// cannot add up.  Outputs and dots as in pass_block_prec2.
 constexpr int ANCHOR_EVERY = 64;
 template <int RPW, int UNR>
 __device__ __forceinline__ void pass_block_incr(const float* __restrict__ Qf, int ld, int row0, int rows,

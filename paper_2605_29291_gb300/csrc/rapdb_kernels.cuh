@@ -32,11 +32,11 @@ namespace rapdb_dev {
 
 __device__ __forceinline__ bool vec_phase(int ph) {
   return ph == PH_INIT || ph == PH_TRIAL || ph == PH_XY2 || ph == PH_AVG || ph == PH_KKT32B || ph == PH_GAPP ||
-         ph == PH_GAPF || ph == PH_GAPV;
+         ph == PH_GAPF || ph == PH_GAPV || ph == PH_HYPX;
 }
 __device__ __forceinline__ bool pass_phase(int ph) {
   return ph == PH_INIT || ph == PH_TRIAL || ph == PH_AVGP || ph == PH_KKT32 || ph == PH_GAPP || ph == PH_GAPF ||
-         ph == PH_GAPV;
+         ph == PH_GAPV || ph == PH_ANCHOR;
 }
 __device__ __forceinline__ bool gap_phase(int ph) { return ph == PH_GAPP || ph == PH_GAPF || ph == PH_GAPV; }
 
@@ -99,11 +99,14 @@ static __device__ void restart_scalars(const DevParams& P, State& S) {
 
 // Precision refinement: level 0 = the stored Q (float32, bfloat16 or FP8),
 // 1 = float32 Q (from quantised storage), 2 = float32 Q with compensated
-// (double-float) products.  At restart boundaries, and when the current level
-// reports convergence, the residual is checked one level up; a stall (or a
-// disagreement at convergence) switches to that level.
+// (double-float) products, 3 = level 2 whose trial increments Q~ d come from
+// the quantised packed tiles (U^k stays a compensated float32 product,
+// re-anchored at each check).  At restart boundaries (levels 0, 1), every
+// ANCHOR_EVERY accepted iterations (level 3), and when the current level
+// reports convergence, the residual is checked at level 2; a stall (or a
+// disagreement at convergence) switches to level 2.
 __device__ __forceinline__ bool can_refine(const Inst& I, const State& S) {
-  return I.P.refine && S.precision < 2 && (I.storage == RAPDB_F32 || I.Q32 != nullptr);
+  return I.P.refine && (S.precision < 2 || S.precision == 3) && (I.storage == RAPDB_F32 || I.Q32 != nullptr);
 }
 // The next level is always the compensated one: its trial products are
 // incremental (U^k + Q d, one float32 right-hand side), so they cost what a
@@ -181,9 +184,9 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
     if (P.tau_log) P.tau_log[S.it] = tau;
     if (P.trials_log) P.trials_log[S.it] = trials_this;
   }
-  // level 2: the accepted products came from U^k + Q d while anchor_age <
-  // ANCHOR_EVERY, else from a direct compensated product
-  if (S.precision == 2) S.anchor_age = (S.anchor_age < ANCHOR_EVERY) ? S.anchor_age + 1 : 0;
+  // compensated levels: the accepted products came from U^k + Q d; after
+  // ANCHOR_EVERY of them an anchor pass re-forms U at the new iterate
+  if (S.precision >= 2) S.anchor_age += 1;
   S.tau_prev = tau;
   S.sigma_prev = sigma;
   S.alpha_k = alpha_next;
@@ -209,17 +212,26 @@ static __device__ void accept_scalars(const Inst& I, State& S, double sigma, dou
     }
   }
   S.phase = PH_TRIAL;
+  // levels 0 and 1 are checked at restart boundaries and every
+  // restart_period / 4 iterations; level 3 at its anchors (below)
+  const bool periodic = can_refine(I, S) && S.precision < 2;
   if (P.restart == RAPDB_RESTART_FIXED && S.k == P.restart_period) {
     if (P.restart_from_average) {
       S.avg_pending = 1;
     } else {
       restart_scalars(P, S);
       S.restart_note = 1;
-      if (can_refine(I, S)) S.check_due = 1;
+      if (periodic) S.check_due = 1;
     }
-  } else if (can_refine(I, S) && P.restart_period > 0 && S.it % max(1, P.restart_period / 4) == 0) {
-    // the precision check also runs every restart_period / 4 iterations
+  } else if (periodic && P.restart_period > 0 && S.it % max(1, P.restart_period / 4) == 0) {
     S.check_due = 1;
+  }
+  // the anchor pass comes first (a restart from the average forms U
+  // directly); at level 3 the precision check is the anchor: its direct
+  // compensated pass at x^k replaces U^k unless the check ends the solve
+  if (S.precision >= 2 && S.anchor_age >= ANCHOR_EVERY && !S.avg_pending) {
+    if (S.precision == 3) S.check_due = 1;
+    else S.phase = PH_ANCHOR;
   }
 }
 
@@ -242,12 +254,13 @@ template <int ST>
 __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, State* __restrict__ states,
                                             Ctrl* __restrict__ ctrl, const int* __restrict__ vmap,
                                             float* __restrict__ XS, float* __restrict__ VS) {
-  extern __shared__ double sm[];            // ys[m], yts[m]
+  extern __shared__ double sm[];            // ys[m], yts[m] (float64), then ydf[m], ytdf[m] (double-float)
   __shared__ double red[NWARP * NVP];
   __shared__ double vfin[NVP];
-  __shared__ double pg[3][NGRP][VCOL];
+  __shared__ float2 pg[3][NGRP][VCOL];      // the groups' double-float constraint sums
   __shared__ float sx[VCOL], sd[VCOL];
   __shared__ int s_dec;
+  __shared__ __align__(16) State Sc;        // the control step's copy of the state
   const int b = vmap[blockIdx.x];
   const Inst& I = insts[b];
   State& S = states[b];
@@ -260,7 +273,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
 #ifdef RAPDB_CHECKED
   {
     const int code = !(cb >= 0 && cb < I.ncb) ? CHK_VEC_RANGE
-                     : (dyn_smem_bytes() < (unsigned)(2 * m) * 8u ? CHK_VEC_SMEM : 0);
+                     : (dyn_smem_bytes() < (unsigned)m * (unsigned)VEC_SMEM_PER_CON ? CHK_VEC_SMEM : 0);
     if (code) {
       if (tid == 0) atomicCAS(&ctrl->err, 0, code);
       return;
@@ -272,6 +285,8 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const int k = S.k, it = S.it;
   double* ys = sm;
   double* yts = sm + m;
+  float2* ydf = reinterpret_cast<float2*>(sm + 2 * m);
+  float2* ytdf = ydf + m;
 
   const double tau = S.tau;
   const double sigma = S.gamma * tau;
@@ -296,6 +311,14 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   if (P.dual_simplex && phase == PH_TRIAL && P.variant == RAPDB_YX) proj_simplex_block(yts, I.m_ineq, P.dual_r, red);
   if (cb == 0 && phase == PH_TRIAL && P.variant == RAPDB_YX)
     for (int i = tid; i < m; i += NT) I.yb[ycur0 ^ 1][i] = yts[i];
+  // double-float copies of the multipliers for the column sums (XY2: of y~ - y)
+  for (int i = tid; i < m; i += NT) {
+    const dflt a = df_from_double(ys[i]);
+    const dflt b = df_from_double(phase == PH_XY2 ? yts[i] - ys[i] : yts[i]);
+    ydf[i] = make_float2(a.hi, a.lo);
+    ytdf[i] = make_float2(b.hi, b.lo);
+  }
+  __syncthreads();
 
   const bool kkt_due = (phase == PH_TRIAL && fresh &&
                         ((P.kkt_every > 0 && it % P.kkt_every == 0) || it >= P.max_iter)) ||
@@ -312,73 +335,153 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   const float* Uc = I.U[S.ucur];
   float* Un = I.U[S.ucur ^ 1];
   // low parts of U when the products were formed with compensation
-  const float* Uclo = (S.precision == 2) ? I.Ulo[S.ucur] : nullptr;
-  const float* Unlo = (phase == PH_KKT32B ? S.check_level == 2 : (S.precision == 2 && phase == PH_XY2))
+  const bool comp_lv = S.precision >= 2;
+  const float* Uclo = comp_lv ? I.Ulo[S.ucur] : nullptr;
+  const float* Unlo = (phase == PH_KKT32B ? S.check_level == 2 : (comp_lv && phase == PH_XY2))
                           ? I.Ulo[S.ucur ^ 1] : nullptr;
   const float* c = I.c;
-  const double* cdb = I.cd;
   double acc[NVP];
 #pragma unroll
   for (int q = 0; q < NVP; ++q) acc[q] = 0.0;
 
   const int j = cb * VCOL + lc;
   // ---- constraint sums, split over the NGRP groups ----
+  // Compensated double-float accumulation: each term y_i * (U_ij + Ulo_ij +
+  // c_ij) is a TwoProduct of pairs, its rounding errors summed alongside.
   {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    dflt s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
     if (j < n) {
-      if (phase == PH_TRIAL || phase == PH_KKT32B) {
-        const float* Us = (phase == PH_KKT32B) ? Un : Uc;
-        const float* Ul = (phase == PH_KKT32B) ? Unlo : Uclo;
+      if (phase == PH_TRIAL || phase == PH_KKT32B || phase == PH_XY2) {
+        // TRIAL / KKT32B: sum y_i (u_i + c_i) and sum y~_i (u_i + c_i);
+        // XY2: sum (y~_i - y_i)(u~_i + c_i) and sum y_i w_i
+        const bool xy2 = phase == PH_XY2;
+        const float* Us = (phase == PH_TRIAL) ? Uc : Un;
+        const float* Ul = (phase == PH_TRIAL) ? Uclo : Unlo;
         for (int i = 1 + grp; i <= m; i += NGRP) {
-          const double v = (double)Us[(size_t)i * ldv + j] + (Ul ? (double)Ul[(size_t)i * ldv + j] : 0.0) +
-                           cdb[(size_t)i * ldv + j];
-          s0 += ys[i - 1] * v;
-          s1 += yts[i - 1] * v;
-        }
-      } else if (phase == PH_XY2) {
-        for (int i = 1 + grp; i <= m; i += NGRP) {
-          const double dy = yts[i - 1] - ys[i - 1];
-          s0 += dy * ((double)Un[(size_t)i * ldv + j] + (Unlo ? (double)Unlo[(size_t)i * ldv + j] : 0.0) +
-                      cdb[(size_t)i * ldv + j]);
-          s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
+          const size_t o = (size_t)i * ldv + j;
+          float vh, ve;
+          two_sumf(Us[o], c[o], vh, ve);
+          const dflt v = {vh, __fadd_rn(ve, Ul ? Ul[o] : 0.f)};
+          const float2 a = ydf[i - 1], b = ytdf[i - 1];
+          if (xy2) {
+            df_acc_mul(s0, dflt{b.x, b.y}, v);
+            df_acc_mulf(s1, dflt{a.x, a.y}, I.W[o]);
+          } else {
+            df_acc_mul(s0, dflt{a.x, a.y}, v);
+            df_acc_mul(s1, dflt{b.x, b.y}, v);
+          }
         }
       } else if (gap_phase(phase)) {
         // sum_i y_i (Q_i w)_j, sum_i y_i (Q_i z)_j, sum_i y_i c_ij
         for (int i = 1 + grp; i <= m; i += NGRP) {
-          s0 += ys[i - 1] * (double)Un[(size_t)i * ldv + j];
-          s1 += ys[i - 1] * (double)I.W[(size_t)i * ldv + j];
-          s2 += ys[i - 1] * cdb[(size_t)i * ldv + j];
+          const size_t o = (size_t)i * ldv + j;
+          const float2 a = ydf[i - 1];
+          df_acc_mulf(s0, dflt{a.x, a.y}, Un[o]);
+          df_acc_mulf(s1, dflt{a.x, a.y}, I.W[o]);
+          df_acc_mulf(s2, dflt{a.x, a.y}, c[o]);
         }
       }
     }
-    pg[0][grp][lc] = s0;
-    pg[1][grp][lc] = s1;
-    pg[2][grp][lc] = s2;
+    pg[0][grp][lc] = make_float2(s0.hi, s0.lo);
+    pg[1][grp][lc] = make_float2(s1.hi, s1.lo);
+    pg[2][grp][lc] = make_float2(s2.hi, s2.lo);
   }
   __syncthreads();
 
   if (grp == 0 && j < n) {
-    double gc = 0.0, gt = 0.0, g2 = 0.0;
+    double gc, gt, g2;
+    {
+      dflt a = df_norm(pg[0][0][lc].x, pg[0][0][lc].y), b = df_norm(pg[1][0][lc].x, pg[1][0][lc].y),
+           e = df_norm(pg[2][0][lc].x, pg[2][0][lc].y);
 #pragma unroll
-    for (int g = 0; g < NGRP; ++g) {
-      gc += pg[0][g][lc];
-      gt += pg[1][g][lc];
-      g2 += pg[2][g][lc];
+      for (int g = 1; g < NGRP; ++g) {
+        a = df_add(a, dflt{pg[0][g][lc].x, pg[0][g][lc].y});
+        b = df_add(b, dflt{pg[1][g][lc].x, pg[1][g][lc].y});
+        e = df_add(e, dflt{pg[2][g][lc].x, pg[2][g][lc].y});
+      }
+      gc = df_to_double(a);
+      gt = df_to_double(b);
+      g2 = df_to_double(e);
     }
     const double xj = xk[j];
     const float xj32 = I.xf[S.xcur][j];
     const double c0 = c[j];
     const double q0d = (I.q0_kind == RAPDB_Q0_DIAG) ? (double)I.q0diag[j] : 0.0;
-    if (phase == PH_TRIAL || phase == PH_KKT32B) {
+    // The trial point x~ and its column work (the pass's right-hand sides,
+    // ||d||^2, the diagonal Q_0 row and the i = 0 dots).  u0 = (Q_0 x^k)_j.
+    auto trial_final = [&](double xt, double u0) {
+      // the iterate is kept in float64 (steps far below one float32 ulp of
+      // x still move it); the pass reads float32 copies of x~ and of d
+      const float xt32 = (float)xt;
+      const float d32 = (float)(xt - xj);
+      xt_out[j] = xt;
+      xt_out32[j] = xt32;
+      xt_outlo[j] = (float)(xt - (double)xt32);
+      I.dv[j] = d32;
+      sx[lc] = xt32;
+      sd[lc] = d32;
+      acc[V_DD] = (double)d32 * (double)d32;
+      if (I.s_off) {
+        const double u0d = q0d * (comp_lv ? xt : (double)xt32);
+        const float u0n = (float)u0d;
+        const float w0 = (float)(q0d * (double)d32);
+        Un[j] = u0n;
+        if (comp_lv) I.Ulo[S.ucur ^ 1][j] = (float)(u0d - (double)u0n);
+        I.W[j] = w0;
+        acc[V_XU0] = (comp_lv ? xt : (double)xt32) * u0d;
+        acc[V_DW0] = (double)d32 * (double)w0;
+        acc[V_DU0] = (double)d32 * u0;
+      }
+      acc[V_CX0] = c0 * (double)xt32;
+      acc[V_CD0] = c0 * (double)d32;
+    };
+    // One accelerated-gradient step of the smoothed gap's x-subproblem, from
+    // z_k, w_k to z_{k+1} = zn (already projected onto X).
+    auto gapf_final = [&](double zn) {
+      const double zk = I.gz[j];
+      const float wj = I.gwf[j];
+      const double wn = zn + S.gap_beta * (zn - zk);                  // momentum of this step
+      I.gz[j] = zn;
+      I.gzf[j] = (float)zn;
+      I.gwf[j] = (float)wn;
+      sx[lc] = (float)wn;
+      sd[lc] = (float)zn;
+      acc[0] = (zn - zk) * (zn - zk);
+      acc[1] = zn * zn;
+      acc[5] = (zn - (double)wj) * (zn - (double)wj);                // |z+ - w|^2 (gradient mapping / L)
+    };
+    // the point to project onto X with the hyperplane, kept as a pair
+    auto keep_for_projection = [&](double v) {
+      const dflt vd = df_from_double(v);
+      I.hv[j] = make_float2(vd.hi, vd.lo);
+    };
+    if (phase == PH_HYPX) {
+      // projection onto X: x = clamp(v - nu a) with the nu of the projection kernel
+      const float2 vv = I.hv[j];
+      const dflt nu = df_from_double(S.hyp_nu);
+      dflt na = {0.f, 0.f};
+      df_acc_mulf(na, nu, I.hyp_a[j]);
+      const dflt t = df_add(dflt{vv.x, vv.y}, dflt{-na.hi, -na.lo});
+      const double xp = df_at_or_below(t.hi, t.lo, I.lb[j]) ? (double)I.lb[j]
+                        : (df_at_or_above(t.hi, t.lo, I.ub[j]) ? (double)I.ub[j] : df_to_double(t));
+      if (S.hyp_ret == PH_TRIAL) trial_final(xp, I.s_off ? q0d * xj : 0.0);
+      else gapf_final(xp);
+    } else if (phase == PH_TRIAL || phase == PH_KKT32B) {
       const float* Us = (phase == PH_KKT32B) ? Un : Uc;
       const float* Ul = (phase == PH_KKT32B) ? Unlo : Uclo;
       const double u0 = (I.s_off ? q0d * xj : (double)Us[j] + (Ul ? (double)Ul[j] : 0.0));
       const double gf = u0 + c0;
       const double grad = gf + gc;
       if (kkt_due) {
-        const double lo = I.lb[j], hi = I.ub[j];
-        const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
-        acc[V_RS] = rs * rs;
+        if (I.hyp_a) {
+          // dist(0, grad + N_X(x)) needs every column: the control CTA forms it
+          const dflt gd = df_from_double(grad);
+          I.hg[j] = make_float2(gd.hi, gd.lo);
+        } else {
+          const double lo = I.lb[j], hi = I.ub[j];
+          const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
+          acc[V_RS] = rs * rs;
+        }
         acc[V_GF] = gf * gf;
         acc[V_GC] = gc * gc;
       }
@@ -398,31 +501,8 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
           step = (1.0 + theta) * grad - theta * gprev;
         }
         const double lo = I.lb[j], hi = I.ub[j];
-        const double xt = fmin(fmax(xj - tau * step, lo), hi);
-        // the iterate is kept in float64 (steps far below one float32 ulp of
-        // x still move it); the pass reads float32 copies of x~ and of d
-        const float xt32 = (float)xt;
-        const float d32 = (float)(xt - xj);
-        xt_out[j] = xt;
-        xt_out32[j] = xt32;
-        xt_outlo[j] = (float)(xt - (double)xt32);
-        I.dv[j] = d32;
-        sx[lc] = xt32;
-        sd[lc] = d32;
-        acc[V_DD] = (double)d32 * (double)d32;
-        if (I.s_off) {
-          const double u0d = q0d * (S.precision == 2 ? xt : (double)xt32);
-          const float u0n = (float)u0d;
-          const float w0 = (float)(q0d * (double)d32);
-          Un[j] = u0n;
-          if (S.precision == 2) I.Ulo[S.ucur ^ 1][j] = (float)(u0d - (double)u0n);
-          I.W[j] = w0;
-          acc[V_XU0] = (S.precision == 2 ? xt : (double)xt32) * u0d;
-          acc[V_DW0] = (double)d32 * (double)w0;
-          acc[V_DU0] = (double)d32 * u0;
-        }
-        acc[V_CX0] = c0 * (double)xt32;
-        acc[V_CD0] = c0 * (double)d32;
+        if (I.hyp_a) keep_for_projection(xj - tau * step);     // finished in phase HYPX
+        else trial_final(fmin(fmax(xj - tau * step, lo), hi), u0);
         if (gap_due && S.gap_evals == 0) I.gpf[j] = hash_unit((uint32_t)j);
         if (fresh) {
           if (P.log_cap > 0 && it >= 1 && it <= P.log_cap && P.x_log)
@@ -452,8 +532,7 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         sd[lc] = xj32;
       }
     } else if (phase == PH_GAPF || phase == PH_GAPV) {
-      // x-subproblem min_{z in box} Phi(z, y) + xi |z - x|^2 (Hessian Q(y) + 2 xi I)
-      const double zk = I.gz[j];
+      // x-subproblem min_{z in X} Phi(z, y) + xi |z - x|^2 (Hessian Q(y) + 2 xi I)
       const float zk32 = I.gzf[j];
       const double cl = c0 + g2;                                       // c(y)_j
       const double hz = (I.s_off ? q0d * (double)zk32 : (double)I.W[j]) + gt;  // (Q(y) z)_j
@@ -464,16 +543,9 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         const float wj = I.gwf[j];
         const double hw = (I.s_off ? q0d * (double)wj : (double)Un[j]) + gc;   // (Q(y) w)_j
         const double grad = hw + 2.0 * P.xi * ((double)wj - xj) + cl;
-        const double zn = fmin(fmax((double)wj - grad / S.gap_L, (double)I.lb[j]), (double)I.ub[j]);
-        const double wn = zn + S.gap_beta * (zn - zk);                  // momentum of this step
-        I.gz[j] = zn;
-        I.gzf[j] = (float)zn;
-        I.gwf[j] = (float)wn;
-        sx[lc] = (float)wn;
-        sd[lc] = (float)zn;
-        acc[0] = (zn - zk) * (zn - zk);
-        acc[1] = zn * zn;
-        acc[5] = (zn - (double)wj) * (zn - (double)wj);                // |z+ - w|^2 (gradient mapping / L)
+        const double zu = (double)wj - grad / S.gap_L;
+        if (I.hyp_a) keep_for_projection(zu);                         // finished in phase HYPX
+        else gapf_final(fmin(fmax(zu, (double)I.lb[j]), (double)I.ub[j]));
       }
     } else if (phase == PH_XY2) {
       // a = sum_i dy_i (u~_i + c_i),  b = Q(y^k) d = w_0 + sum_i y_i w_i
@@ -499,8 +571,10 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       acc[V_CX0] = c0 * (double)xt32;
     }
   }
-  if (ST == RAPDB_FP8 && (phase == PH_TRIAL || phase == PH_INIT || phase == PH_AVG || phase == PH_GAPP ||
-                           phase == PH_GAPF)) {
+  // (with the hyperplane the trial and gradient-step right-hand sides are
+  // written in phase HYPX, after the projection)
+  if (ST == RAPDB_FP8 && ((phase == PH_TRIAL && (!I.hyp_a || gap_due)) || phase == PH_INIT || phase == PH_AVG ||
+                           phase == PH_GAPP || (phase == PH_GAPF && !I.hyp_a) || phase == PH_HYPX)) {
     // pre-scaled right-hand sides s_i .* (first, second right-hand side) of every stored matrix
     __syncthreads();
     if (j < n) {
@@ -522,263 +596,364 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
     for (int i = 0; i < m; ++i) P.y_log[(size_t)(it - 1) * m + i] = (float)ys[i];
   }
 
-  block_sum<NVP>(acc, red);
-  if (tid == 0) {
+  // every column's partials are in warp 0 (constraint group 0): a warp sum
+  // in a fixed order suffices
+  if (tid < 32) {
 #pragma unroll
-    for (int q = 0; q < NVP; ++q) I.vpart[(size_t)cb * NVP + q] = acc[q];
+    for (int q = 0; q < NVP; ++q) acc[q] = warp_sum(acc[q]);
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < NVP; ++q) I.vpart[(size_t)cb * NVP + q] = acc[q];
+    }
   }
   if (!arrive_last(&S.arrive_vec, (unsigned)I.ncb)) return;
 
-  // ---- last CTA of this instance: fixed-order reduction + control ----
-  // (one warp per partial slot, lanes striding over the column blocks)
+  // ---- last CTA of this instance: the control step, on a shared-memory copy
+  // of the state (its serial scalar updates then cost no global round trips;
+  // written back at the end) ----
   {
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int q = warp; q < NVP; q += NWARP) {
-      double s = 0.0;
-      for (int bq = lane; bq < I.ncb; bq += 32) s += __ldcg(&I.vpart[(size_t)bq * NVP + q]);
-      s = warp_sum(s);
-      if (lane == 0) vfin[q] = s;
-    }
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&states[b]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&Sc);
+    for (int w = tid; w < (int)(sizeof(State) / 4); w += NT) dst[w] = src[w];
   }
   __syncthreads();
+  // (every barrier below is reached by all threads before any of them leaves)
+  auto control = [&](State& S) {
 
-  if (phase == PH_INIT || phase == PH_AVG || phase == PH_TRIAL) {
-    if (tid == 0) {
-      S.dd = vfin[V_DD];
-      for (int q = 0; q < NDOT; ++q) S.dots0[q] = vfin[V_XU0 + q];
-      if (phase == PH_AVG) S.phase = PH_AVGP;   // the pass of this body forms U = Q xbar
+    // ---- last CTA of this instance: fixed-order reduction + control ----
+    // (one warp per partial slot, lanes striding over the column blocks)
+    {
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int q = warp; q < NVP; q += NWARP) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int bq = lane; bq < I.ncb; bq += 32) s += __ldcg(&I.vpart[(size_t)bq * NVP + q]);
+        s = warp_sum(s);
+        if (lane == 0) vfin[q] = s;
+      }
     }
-  }
-  if (phase == PH_TRIAL && fresh) {
-    double fe[2] = {0.0, 0.0};
-    if (kkt_due) {
-      kkt_feas_terms(I, gk, ys, fe[0], fe[1], red);
-      block_allsum<2>(fe, red);
+    __syncthreads();
+
+    const bool hyp_trial_x = phase == PH_HYPX && S.hyp_ret == PH_TRIAL;
+    if (phase == PH_INIT || phase == PH_AVG || (phase == PH_TRIAL && !I.hyp_a) || hyp_trial_x) {
+      if (tid == 0) {
+        S.dd = vfin[V_DD];
+        for (int q = 0; q < NDOT; ++q) S.dots0[q] = vfin[V_XU0 + q];
+        if (phase == PH_AVG) S.phase = PH_AVGP;   // the pass of this body forms U = Q xbar
+      }
     }
-    if (tid != 0) return;
-    if (kkt_due) {
-      double rel, rs, rf;
-      kkt_finish(I, vfin[V_RS], vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
-      S.rel_kkt = rel;
-      S.r_stat = rs;
-      S.r_feas = rf;
-      if (P.kkt_log && it < P.log_cap) P.kkt_log[it] = rel;
-      if (!(rel == rel)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
-      if (can_refine(I, S)) {
-        S.rel_q = rel;
-        // the check runs at this x^k, after the stored level's residual at
-        // the same point (rel_q) has been formed
-        if (rel <= P.tol || S.check_due) {
-          S.check_due = 0;
-          start_check(I, S);
+    if (hyp_trial_x) {              // the projected trial point is ready for the pass
+      if (tid == 0) {
+        S.phase = PH_TRIAL;
+        S.trial_ready = 1;
+      }
+      return;
+    }
+    // shared scratch of the hyperplane routines (red holds NWARP * NVP doubles)
+    float2* hsm = reinterpret_cast<float2*>(red);
+    double* hsb = red + NWARP + 2;
+    if (phase == PH_TRIAL && fresh) {
+      double fe[2] = {0.0, 0.0};
+      double rs2 = vfin[V_RS];
+      if (kkt_due) {
+        kkt_feas_terms(I, gk, ys, fe[0], fe[1], red);
+        block_allsum<2>(fe, red);
+        if (I.hyp_a) {   // dist(0, grad + N_X(x^k)) with the hyperplane's direction
+          double t_new;
+          rs2 = hyp_cone_rs2(I, I.xf[S.xcur], I.xl[S.xcur], S.hyp_t, &t_new, hsm, hsb);
+          if (tid == 0) S.hyp_t = t_new;
+        }
+      }
+      if (tid != 0) return;
+      if (kkt_due) {
+        double rel, rs, rf;
+        kkt_finish(I, rs2, vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
+        S.rel_kkt = rel;
+        S.r_stat = rs;
+        S.r_feas = rf;
+        if (P.kkt_log && it < P.log_cap) P.kkt_log[it] = rel;
+        if (!(rel == rel)) { finish(S, ctrl, RAPDB_ERR_NUMERIC); return; }
+        if (can_refine(I, S)) {
+          S.rel_q = rel;
+          // the check runs at this x^k, after the stored level's residual at
+          // the same point (rel_q) has been formed
+          if (rel <= P.tol || S.check_due) {
+            S.check_due = 0;
+            start_check(I, S);
+            return;
+          }
+        } else if (rel <= P.tol) {
+          finish(S, ctrl, RAPDB_OK);
           return;
         }
-      } else if (rel <= P.tol) {
-        finish(S, ctrl, RAPDB_OK);
+      }
+      if (it >= P.max_iter) { finish(S, ctrl, RAPDB_ERR_MAXITER); return; }
+      if (S.deadline_ns > 0 && (long long)globaltimer() > S.deadline_ns) {
+        finish(S, ctrl, RAPDB_ERR_TIMEOUT);
         return;
       }
-    }
-    if (it >= P.max_iter) { finish(S, ctrl, RAPDB_ERR_MAXITER); return; }
-    if (S.deadline_ns > 0 && (long long)globaltimer() > S.deadline_ns) {
-      finish(S, ctrl, RAPDB_ERR_TIMEOUT);
-      return;
-    }
-    if (S.avg_pending) {          // restart from the average: the trial is discarded
-      S.avg_pending = 0;
+      if (S.avg_pending) {          // restart from the average: the trial is discarded
+        S.avg_pending = 0;
+        S.fresh = 0;
+        S.phase = PH_AVG;
+        return;
+      }
+      if (gap_due) {                // smoothed-gap evaluation first: the trial is discarded
+        S.fresh = 0;
+        S.gap_it_done = it;
+        S.gap_iter = 1;             // the pass of this body is power pass #1 (right-hand side p_0)
+        S.gap_pnorm = 1.0;
+        S.phase = PH_GAPP;
+        return;
+      }
+      S.restarts += S.restart_note;
+      S.restart_note = 0;
       S.fresh = 0;
-      S.phase = PH_AVG;
-      return;
-    }
-    if (gap_due) {                // smoothed-gap evaluation first: the trial is discarded
-      S.fresh = 0;
-      S.gap_it_done = it;
-      S.gap_iter = 1;             // the pass of this body is power pass #1 (right-hand side p_0)
-      S.gap_pnorm = 1.0;
-      S.phase = PH_GAPP;
-      return;
-    }
-    S.restarts += S.restart_note;
-    S.restart_note = 0;
-    S.fresh = 0;
-    S.trial_ready = 1;
-    return;
-  }
-  if (phase == PH_TRIAL) {        // a further trial of the same iteration
-    if (tid == 0) S.trial_ready = 1;
-    return;
-  }
-  if (phase == PH_GAPP) {
-    if (gap_iter == 1) {
-      // y-part of G_xi in closed form, y' = proj_Y(y + g(x)/(2 xi)) (max(0, .), or
-      // the simplex projection): fixed during the evaluation
-      for (int i = tid; i < m; i += NT) {
-        const double v = ys[i] + gk[i] / (2.0 * P.xi);
-        yts[i] = (P.dual_simplex || i >= I.m_ineq) ? v : fmax(0.0, v);
-      }
-      __syncthreads();
-      if (P.dual_simplex) proj_simplex_block(yts, I.m_ineq, P.dual_r, red);
-      double yp[2] = {0.0, 0.0};
-      for (int i = tid; i < m; i += NT) {
-        const double lp = yts[i];
-        yp[0] += lp * gk[i];
-        yp[1] += (lp - ys[i]) * (lp - ys[i]);
-      }
-      block_allsum<2>(yp, red);
-      if (tid == 0) S.gap_ypart = S.obj + yp[0] - P.xi * yp[1];
-    }
-    if (tid != 0) return;
-    const double mu = vfin[V_AA] / vfin[V_BB];
-    S.gap_pnorm = sqrt(vfin[V_X2]);
-    if (!(S.gap_pnorm > 0.0) || !(mu == mu)) S.gap_pnorm = 1.0;
-    if (gap_iter < gap_P) {
-      S.gap_iter = gap_iter + 1;
-      return;
-    }
-    // step constant of the accelerated gradient: L = 2 mu + 2 xi (the
-    // Rayleigh quotient mu bounds lambda_max(Q(y)) from below), constant
-    // momentum (sqrt(L) - sqrt(2 xi)) / (sqrt(L) + sqrt(2 xi)) for the
-    // 2 xi-strongly convex subproblem
-    const double lq = fmax(mu, 0.0);
-    S.gap_L = 2.0 * lq + 2.0 * P.xi;
-    const double sl = sqrt(S.gap_L), sm = sqrt(2.0 * P.xi);
-    S.gap_mu = (sl - sm) / (sl + sm);
-    S.gap_beta = S.gap_mu;
-    S.gap_prev = INFINITY;
-    S.gap_iter = 0;
-    S.phase = PH_GAPF;
-    return;
-  }
-  if (phase == PH_GAPF || phase == PH_GAPV) {
-    // x-subproblem objective at z_k: 0.5 z'Q(y)z + c(y)'z + y'd + xi |z - x|^2
-    double yd[1] = {0.0};
-    for (int i = tid; i < m; i += NT) yd[0] += ys[i] * I.dcon[i];
-    block_allsum<1>(yd, red);
-    const double xval = 0.5 * vfin[2] + vfin[3] + yd[0] + P.xi * vfin[4];
-    if (phase == PH_GAPF) {
-      if (tid != 0) return;
-      // function-value restart of the momentum: after an increase of the
-      // subproblem objective the next step is a plain projected gradient step
-      S.gap_beta = (gap_iter > 0 && xval > S.gap_prev) ? 0.0 : S.gap_mu;
-      S.gap_prev = xval;
-      const int k1 = gap_iter + 1;
-      const bool small = vfin[0] <= 1e-20 * (1.0 + vfin[1]);
-      // objective error bound of the strongly convex subproblem from the
-      // gradient mapping L (w - z+): <= L^2 |z+ - w|^2 / (2 * 2 xi); the
-      // restart rule compares G with q G_ref, so 1e-3 of the current gap
-      // estimate suffices
-      const double err = S.gap_L * S.gap_L * vfin[5] / (4.0 * P.xi);
-      const double gest = S.gap_ypart - xval;
-      const bool accurate = gap_iter >= 3 && gest > 0.0 && err <= 1e-3 * gest + 1e-13 * (1.0 + fabs(xval));
-      if (k1 >= P.gap_inner_max || small || accurate) {
-        S.phase = PH_GAPV;       // the pass of this body forms Q z_K
+      if (I.hyp_a) {                // the trial point is projected onto X first
+        S.hyp_ret = PH_TRIAL;
+        S.phase = PH_HYPN;
       } else {
-        S.gap_iter = k1;
+        S.trial_ready = 1;
       }
       return;
     }
-    // PH_GAPV: G = y-part (closed form, computed at the first power step) - x-part
-    if (tid != 0) return;
-    const double G = S.gap_ypart - xval;
-    S.gap_val = G;
-    if (P.gap_log && S.gap_evals < P.log_cap) P.gap_log[S.gap_evals] = G;
-    S.gap_evals += 1;
-    bool fire = false;
-    if (!S.gap_has_ref) {
-      S.gap_ref = G;
-      S.gap_has_ref = 1;
-    } else if (G <= P.q * S.gap_ref) {
-      fire = true;
-      S.gap_ref = G;
-    }
-    S.gap_iter = 0;
-    S.phase = PH_TRIAL;          // the next body's vector kernel prepares the trial
-    if (fire) {
-      restart_scalars(P, S);
-      S.restarts += 1;
-      if (can_refine(I, S)) {
-        S.fresh = 1;
-        S.check_due = 1;
-      }
-    }
-    return;
-  }
-  if (phase == PH_XY2) {
-    double dy2[1] = {0.0};
-    for (int i = tid; i < m; i += NT) { const double t = yts[i] - ys[i]; dy2[0] += t * t; }
-    block_allsum<1>(dy2, red);
-    const double sig = sigma, an = P.c_alpha / tau, bn = P.gamma0 * P.c_beta / sig;
-    const int k0 = S.k;
-    const double t_acc = sig / (k0 == 0 ? sig : S.sigma0);
-    if (tid == 0) {
-      const double ddy = 0.5 * dy2[0];
-      const double dp = 0.5 * S.dd;
-      const double bterm = (bn > 0.0) ? vfin[V_BB] / (2.0 * bn) : (vfin[V_BB] == 0.0 ? 0.0 : INFINITY);
-      const double E = vfin[V_AA] / (2.0 * an) - ddy / sig + bterm - (1.0 / tau - theta * (S.alpha_k + S.beta_k)) * dp;
-      const bool ok = E <= -P.delta / tau * dp - P.delta / sig * ddy;
-      S.trials_total += 1;
-      s_dec = !(E == E) ? 2 : ((ok || !P.backtracking) ? 1 : 0);
-    }
-    __syncthreads();
-    const int dec = s_dec;
-    if (dec == 1) {
-      accept_vectors(I, k0, gcur0, ycur0, t_acc);
-      __syncthreads();
-      if (tid == 0) accept_scalars(I, S, sig, an, bn);
-    } else if (tid == 0) {
-      if (dec == 2) finish(S, ctrl, RAPDB_ERR_NUMERIC);
-      else reject_trial(I, S, ctrl);
-    }
-    return;
-  }
-  if (phase == PH_KKT32B) {
-    // the residual one precision level up (check_level) at x^k
-    double fe[2] = {0.0, 0.0};
-    kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1], red);
-    block_allsum<2>(fe, red);
-    if (tid == 0) {
-      double rel, rs, rf;
-      kkt_finish(I, vfin[V_RS], vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
-      S.rel_kkt = rel;
-      S.r_stat = rs;
-      S.r_feas = rf;
-      int dec = 0;
-      if (rel <= P.tol) {
-        dec = 2;
-      } else {
-        const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
-        S.kkt_ref = rel;
-        // switch when the true residual stalls, when the stored matrices'
-        // problem is solved, or when the storage error already dominates
-        // (the true residual is more than twice the stored level's)
-        if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) dec = 1;
-      }
-      s_dec = dec;
-    }
-    __syncthreads();
-    const int dec = s_dec;
-    if (dec == 1) {   // switch to the float32 Q: the KKT pass output becomes the current U
-      double* gd = I.gb[gcur0];
-      for (int i = tid; i < m; i += NT) gd[i] = I.gnew[i];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      if (dec == 2) {
-        finish(S, ctrl, RAPDB_OK);
-      } else {
-        if (dec == 1) {
-          // the products' precision changes, the iteration's state does not:
-          // step sizes, momentum and the counter carry on from x^k (a check
-          // at a restart boundary follows the restart that happened there)
-          S.precision = S.check_level;
-          S.switches += 1;
-          S.ucur ^= 1;
-          S.anchor_age = 0;       // the check pass formed U directly
+    if (phase == PH_TRIAL) {        // a further trial of the same iteration
+      if (tid == 0) {
+        if (I.hyp_a) {
+          S.hyp_ret = PH_TRIAL;
+          S.phase = PH_HYPN;
+        } else {
+          S.trial_ready = 1;
         }
-        S.fresh = 1;
-        S.phase = PH_TRIAL;
       }
+      return;
     }
-    return;
+    if (phase == PH_GAPP) {
+      if (gap_iter == 1) {
+        // y-part of G_xi in closed form, y' = proj_Y(y + g(x)/(2 xi)) (max(0, .), or
+        // the simplex projection): fixed during the evaluation
+        for (int i = tid; i < m; i += NT) {
+          const double v = ys[i] + gk[i] / (2.0 * P.xi);
+          yts[i] = (P.dual_simplex || i >= I.m_ineq) ? v : fmax(0.0, v);
+        }
+        __syncthreads();
+        if (P.dual_simplex) proj_simplex_block(yts, I.m_ineq, P.dual_r, red);
+        double yp[2] = {0.0, 0.0};
+        for (int i = tid; i < m; i += NT) {
+          const double lp = yts[i];
+          yp[0] += lp * gk[i];
+          yp[1] += (lp - ys[i]) * (lp - ys[i]);
+        }
+        block_allsum<2>(yp, red);
+        if (tid == 0) S.gap_ypart = S.obj + yp[0] - P.xi * yp[1];
+      }
+      if (tid != 0) return;
+      const double mu = vfin[V_AA] / vfin[V_BB];
+      S.gap_pnorm = sqrt(vfin[V_X2]);
+      if (!(S.gap_pnorm > 0.0) || !(mu == mu)) S.gap_pnorm = 1.0;
+      if (gap_iter < gap_P) {
+        S.gap_iter = gap_iter + 1;
+        return;
+      }
+      // step constant of the accelerated gradient: L = 2 mu + 2 xi (the
+      // Rayleigh quotient mu bounds lambda_max(Q(y)) from below), constant
+      // momentum (sqrt(L) - sqrt(2 xi)) / (sqrt(L) + sqrt(2 xi)) for the
+      // 2 xi-strongly convex subproblem
+      const double lq = fmax(mu, 0.0);
+      S.gap_L = 2.0 * lq + 2.0 * P.xi;
+      const double sl = sqrt(S.gap_L), sm = sqrt(2.0 * P.xi);
+      S.gap_mu = (sl - sm) / (sl + sm);
+      S.gap_beta = S.gap_mu;
+      S.gap_prev = INFINITY;
+      S.gap_iter = 0;
+      S.phase = PH_GAPF;
+      return;
+    }
+    if (phase == PH_GAPF || phase == PH_GAPV || phase == PH_HYPX) {
+      // x-subproblem objective at z_k: 0.5 z'Q(y)z + c(y)'z + y'd + xi |z - x|^2
+      double xval;
+      if (phase == PH_HYPX) {
+        xval = S.gap_xval;          // formed before the projection of the step
+      } else {
+        double yd[1] = {0.0};
+        for (int i = tid; i < m; i += NT) yd[0] += ys[i] * I.dcon[i];
+        block_allsum<1>(yd, red);
+        xval = 0.5 * vfin[2] + vfin[3] + yd[0] + P.xi * vfin[4];
+      }
+      if (phase == PH_GAPF && I.hyp_a) {   // the step is projected onto X first
+        if (tid == 0) {
+          S.gap_xval = xval;
+          S.hyp_ret = PH_GAPF;
+          S.phase = PH_HYPN;
+        }
+        return;
+      }
+      if (phase == PH_GAPF || phase == PH_HYPX) {
+        if (tid != 0) return;
+        if (phase == PH_HYPX) S.phase = PH_GAPF;
+        // function-value restart of the momentum: after an increase of the
+        // subproblem objective the next step is a plain projected gradient step
+        S.gap_beta = (gap_iter > 0 && xval > S.gap_prev) ? 0.0 : S.gap_mu;
+        S.gap_prev = xval;
+        const int k1 = gap_iter + 1;
+        const bool small = vfin[0] <= 1e-20 * (1.0 + vfin[1]);
+        // objective error bound of the strongly convex subproblem from the
+        // gradient mapping L (w - z+): <= L^2 |z+ - w|^2 / (2 * 2 xi); the
+        // restart rule compares G with q G_ref, so 1e-3 of the current gap
+        // estimate suffices
+        const double err = S.gap_L * S.gap_L * vfin[5] / (4.0 * P.xi);
+        const double gest = S.gap_ypart - xval;
+        const bool accurate = gap_iter >= 3 && gest > 0.0 && err <= 1e-3 * gest + 1e-13 * (1.0 + fabs(xval));
+        if (k1 >= P.gap_inner_max || small || accurate) {
+          S.phase = PH_GAPV;       // the pass of this body forms Q z_K
+        } else {
+          S.gap_iter = k1;
+        }
+        return;
+      }
+      // PH_GAPV: G = y-part (closed form, computed at the first power step) - x-part
+      if (tid != 0) return;
+      const double G = S.gap_ypart - xval;
+      S.gap_val = G;
+      if (P.gap_log && S.gap_evals < P.log_cap) P.gap_log[S.gap_evals] = G;
+      S.gap_evals += 1;
+      bool fire = false;
+      if (!S.gap_has_ref) {
+        S.gap_ref = G;
+        S.gap_has_ref = 1;
+      } else if (G <= P.q * S.gap_ref) {
+        fire = true;
+        S.gap_ref = G;
+      }
+      S.gap_iter = 0;
+      S.phase = PH_TRIAL;          // the next body's vector kernel prepares the trial
+      if (fire) {
+        restart_scalars(P, S);
+        S.restarts += 1;
+        if (can_refine(I, S) && S.precision < 2) {
+          S.fresh = 1;
+          S.check_due = 1;
+        }
+      }
+      return;
+    }
+    if (phase == PH_XY2) {
+      double dy2[1] = {0.0};
+      for (int i = tid; i < m; i += NT) { const double t = yts[i] - ys[i]; dy2[0] += t * t; }
+      block_allsum<1>(dy2, red);
+      const double sig = sigma, an = P.c_alpha / tau, bn = P.gamma0 * P.c_beta / sig;
+      const int k0 = S.k;
+      const double t_acc = sig / (k0 == 0 ? sig : S.sigma0);
+      if (tid == 0) {
+        const double ddy = 0.5 * dy2[0];
+        const double dp = 0.5 * S.dd;
+        const double bterm = (bn > 0.0) ? vfin[V_BB] / (2.0 * bn) : (vfin[V_BB] == 0.0 ? 0.0 : INFINITY);
+        const double E = vfin[V_AA] / (2.0 * an) - ddy / sig + bterm - (1.0 / tau - theta * (S.alpha_k + S.beta_k)) * dp;
+        const bool ok = E <= -P.delta / tau * dp - P.delta / sig * ddy;
+        S.trials_total += 1;
+        s_dec = !(E == E) ? 2 : ((ok || !P.backtracking) ? 1 : 0);
+      }
+      __syncthreads();
+      const int dec = s_dec;
+      if (dec == 1) {
+        accept_vectors(I, k0, gcur0, ycur0, t_acc);
+        __syncthreads();
+        if (tid == 0) accept_scalars(I, S, sig, an, bn);
+      } else if (tid == 0) {
+        if (dec == 2) finish(S, ctrl, RAPDB_ERR_NUMERIC);
+        else reject_trial(I, S, ctrl);
+      }
+      return;
+    }
+    if (phase == PH_KKT32B) {
+      // the residual one precision level up (check_level) at x^k
+      double fe[2] = {0.0, 0.0};
+      kkt_feas_terms(I, I.gnew, ys, fe[0], fe[1], red);
+      block_allsum<2>(fe, red);
+      double rs2 = vfin[V_RS];
+      if (I.hyp_a) {
+        double t_new;
+        rs2 = hyp_cone_rs2(I, I.xf[S.xcur], I.xl[S.xcur], S.hyp_t, &t_new, hsm, hsb);
+        if (tid == 0) S.hyp_t = t_new;
+      }
+      if (tid == 0) {
+        double rel, rs, rf;
+        kkt_finish(I, rs2, vfin[V_GF], vfin[V_GC], fe[0], fe[1], rel, rs, rf);
+        S.rel_kkt = rel;
+        S.r_stat = rs;
+        S.r_feas = rf;
+        int dec = 0;
+        if (rel <= P.tol) {
+          dec = 2;
+        } else {
+          const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
+          S.kkt_ref = rel;
+          // switch when the true residual stalls, when the stored matrices'
+          // problem is solved, or when the storage error already dominates
+          // (the true residual is more than twice the stored level's)
+          if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) dec = 1;
+        }
+        s_dec = dec;
+      }
+      __syncthreads();
+      const int dec = s_dec;
+      // the check pass output becomes the current U on a switch, and at level 3
+      // always (the check is its anchor)
+      const bool adopt = dec == 1 || (dec == 0 && S.precision == 3);
+      if (adopt) {   // (row 0 of a Q_0 that is not stored was formed above, at x^k)
+        double* gd = I.gb[gcur0];
+        for (int i = tid; i < m; i += NT) gd[i] = I.gnew[i];
+        __syncthreads();
+      }
+      if (tid == 0) {
+        if (dec == 2) {
+          finish(S, ctrl, RAPDB_OK);
+        } else {
+          if (dec == 1) {
+            // the products' precision changes, the iteration's state does not:
+            // step sizes, momentum and the counter carry on from x^k (a check
+            // at a restart boundary follows the restart that happened there)
+            S.precision = S.check_level;
+            S.switches += 1;
+            if (S.switch_it < 0) S.switch_it = S.it;
+          }
+          if (adopt) {
+            S.ucur ^= 1;
+            S.anchor_age = 0;       // the check pass formed U directly
+          }
+          S.fresh = 1;
+          S.phase = PH_TRIAL;
+        }
+      }
+      return;
+    }
+  };
+  control(Sc);
+  __syncthreads();
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&Sc);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&states[b]);
+    for (int w = tid; w < (int)(sizeof(State) / 4); w += NT) dst[w] = src[w];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projection onto X with the hyperplane (phase HYPN): the scalar nu of
+// x = clamp(v - nu a) with a'x = beta, on one CTA of NTH threads; the vector
+// kernel of phase HYPX then forms x column by column.
+// ---------------------------------------------------------------------------
+constexpr int NTH = 1024;
+template <int DUMMY>
+__global__ void __launch_bounds__(NTH) k_hyp(const Inst* __restrict__ insts, State* __restrict__ states) {
+  __shared__ float2 sm[NTH / 32 + 2];
+  __shared__ double sb[2];
+  const Inst& I = insts[0];
+  State& S = states[0];
+  if (S.phase != PH_HYPN) return;
+  const double nu = hyp_proj_nu(I, S.hyp_nu, sm, sb);
+  if (threadIdx.x == 0) {
+    S.hyp_nu = nu;
+    S.phase = PH_HYPX;
   }
 }
 
@@ -839,6 +1014,8 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
 // ---------------------------------------------------------------------------
 static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, int i, const double* part, int nb,
                                    int phase, bool comp, const float* x, const float* v, double* red, int& s_dec);
+static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int phase, bool comp, const float* x,
+                                    const float* v, double* red, int& s_dec);
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
 __device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State* __restrict__ states,
@@ -870,11 +1047,12 @@ __device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State*
   }
 #endif
   const int level = (phase == PH_KKT32) ? S.check_level : S.precision;
-  const bool comp = (level == 2) && !gap_phase(phase);               // compensated products
+  const bool comp = (level >= 2) && !gap_phase(phase);               // compensated products
   const bool use32 = (ST != RAPDB_F32) && (level >= 1);
+  const bool at_xk = phase == PH_KKT32 || phase == PH_ANCHOR;       // products at the accepted iterate
   const float* x;
   const float* v;
-  if (phase == PH_KKT32) {
+  if (at_xk) {
     x = I.xf[S.xcur];
     v = x;
   } else if (phase == PH_GAPP) {
@@ -887,7 +1065,7 @@ __device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State*
     x = I.xf[S.xcur ^ 1];
     v = I.dv;
   }
-  const float* uold = (phase == PH_KKT32 || gap_phase(phase)) ? nullptr : I.U[S.ucur] + (size_t)i * ldv;
+  const float* uold = (at_xk || gap_phase(phase)) ? nullptr : I.U[S.ucur] + (size_t)i * ldv;
   float* Uo = I.U[S.ucur ^ 1] + (size_t)i * ldv;
   float* Wo = I.W + (size_t)i * ldv;
   double* out = I.part + (size_t)s * NDOT * I.nrb + r;
@@ -895,8 +1073,8 @@ __device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State*
   if (comp) {
     const float* Qb = (ST == RAPDB_F32) ? (const float*)I.Q : I.Q32;
     const int ldq = (ST == RAPDB_F32) ? I.ld : I.ld32;
-    const float* xlo = (phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1];
-    if (phase == PH_TRIAL && S.anchor_age < ANCHOR_EVERY)   // U' = U^k + Q d
+    const float* xlo = at_xk ? I.xl[S.xcur] : I.xl[S.xcur ^ 1];
+    if (phase == PH_TRIAL)   // U' = U^k + Q d
       pass_block_incr<INC_RPW<ST, RPW>, INC_UNR<UNR>>(Qb + (size_t)s * I.n * ldq, ldq, row0, rows, x, xlo, v, uold,
                                                      I.Ulo[S.ucur] + (size_t)i * ldv, crow, Uo,
                                                      I.Ulo[S.ucur ^ 1] + (size_t)i * ldv, Wo, out, I.nrb, red);
@@ -943,18 +1121,29 @@ static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, i
   if (warp < NDOT) {
     const double* src = part + ((size_t)s * NDOT + warp) * nb;
     double t = 0.0;
+#pragma unroll 4
     for (int rr = lane; rr < nb; rr += 32) t += __ldcg(src + rr);
     t = warp_sum(t);
     if (lane == 0) I.dots[(size_t)i * NDOT + warp] = t;
   }
   // ---- last matrix of the instance: control ----
   if (!arrive_last(&S.arrive_pass, (unsigned)I.M)) return;
+  pass_control(I, S, ctrl, phase, comp, x, v, red, s_dec);
+}
+
+// The control step after a pass, on one CTA, once every matrix's dots are in
+// I.dots: the equality dots, g at the pass point, and the phase's decision
+// (the yx backtracking test and step rule, the xy dual step, or the set-up,
+// restart, check and anchor bookkeeping).
+static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int phase, bool comp, const float* x,
+                                    const float* v, double* red, int& s_dec) {
   const int tid = threadIdx.x;
   const int ldv = I.ldv;
   if (I.s_off && tid < NDOT) I.dots[tid] = S.dots0[tid];
   if (I.m > I.m_ineq && !gap_phase(phase)) {
     // linear equalities (no stored matrix): u = w = 0, c'x and c'v here
-    const float* xlo_e = comp ? ((phase == PH_KKT32) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1]) : nullptr;
+    const float* xlo_e =
+        comp ? ((phase == PH_KKT32 || phase == PH_ANCHOR) ? I.xl[S.xcur] : I.xl[S.xcur ^ 1]) : nullptr;
     for (int ie = I.m_ineq + 1; ie <= I.m; ++ie) {
       const float* ci = I.c + (size_t)ie * ldv;
       double sv[2] = {0.0, 0.0};
@@ -1046,7 +1235,7 @@ static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, i
     }
     return;
   }
-  // INIT / AVGP / KKT32: g at the pass point
+  // INIT / AVGP / KKT32 / ANCHOR: g at the pass point
   double* gd = I.gb[gcur0];
   const double T0 = S.T;
   for (int ii = tid; ii < m; ii += NT) {
@@ -1056,11 +1245,28 @@ static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, i
     if (phase != PH_KKT32) gd[ii] = g;
     if (phase == PH_AVGP) I.yb[ycur0][ii] = I.ycum[ii] / T0;
   }
+  if (phase == PH_ANCHOR && I.s_off) {
+    // Q_0 is not stored: its row of U (q0 .* x^k with the low part the
+    // vector kernel formed) carries over to the anchored buffer
+    const int uc = S.ucur;
+    for (int jj = tid; jj < I.n; jj += NT) {
+      I.U[uc ^ 1][jj] = I.U[uc][jj];
+      if (I.Ulo[0]) I.Ulo[uc ^ 1][jj] = I.Ulo[uc][jj];
+    }
+  }
   __syncthreads();
   if (tid != 0) return;
   S.passes += 1;
   if (phase == PH_KKT32) {
     S.phase = PH_KKT32B;
+    return;
+  }
+  if (phase == PH_ANCHOR) {
+    // the anchored products replace the incremental ones at the same iterate;
+    // the iteration's KKT test and restart checks follow (fresh is kept)
+    S.ucur ^= 1;
+    S.anchor_age = 0;
+    S.phase = PH_TRIAL;
     return;
   }
   S.xcur ^= 1;

@@ -31,13 +31,20 @@ constexpr int STB = 128;             // tile edge (rows of a row block)
 static_assert(NT == 2 * STB, "the row-block reduction splits the T slots over two halves of the CTA");
 
 // The passes the packed tiles serve: 1 = the incremental compensated trial
-// pass (U' = U^k + Q d, one right-hand side), 2 = a smoothed-gap pass over
-// the float32 matrices (U = Q x, W = Q v, plain float32 products, two
-// right-hand sides); 0 = any other pass (the row-streaming tile runs it).
+// pass (U' = U^k + Q d, one right-hand side) over the float32 tiles, 2 = a
+// smoothed-gap pass over the float32 tiles (U = Q x, W = Q v, plain float32
+// products, two right-hand sides), 3 = the incremental trial pass of the
+// quantised level (U' = U^k + Q~ d over the BF16 / FP8 tiles); 0 = any other
+// pass (the row-streaming tile runs it).
 __device__ __forceinline__ int sym_kind(const Inst& I, const State& S) {
   if (I.tsym == 0) return 0;
   const int ph = S.phase;
-  if (ph == PH_TRIAL) return (S.trial_ready && S.precision == 2 && S.anchor_age < ANCHOR_EVERY) ? 1 : 0;
+  if (ph == PH_TRIAL) {
+    if (!S.trial_ready) return 0;
+    if (S.precision == 2) return 1;
+    if (S.precision == 3 && I.Qpq) return 3;
+    return 0;
+  }
   if (gap_phase(ph)) return (I.storage == RAPDB_F32 || S.precision >= 1) ? 2 : 0;
   return 0;
 }
@@ -46,13 +53,16 @@ __device__ __forceinline__ int sym_kind(const Inst& I, const State& S) {
 // slots in slot order, apply the incremental update and write the block's dot
 // partials to out[q * T].  The slot sums are compensated float32 sums
 // (Knuth's TwoSum per addition, the rounding errors summed alongside): within
-// 2u of the exact sum plus O(T^2 u^2) of the sum of |slots|, with no float64
-// work (float64 runs at a small fraction of the float32 rate on this GPU).
-// The two halves of the CTA take half the slots each; the low half's sum
-// absorbs the high half's with one more TwoSum.  The update and the five dots
-// are float64; the dots are summed over the 128 rows through shared memory
-// (four rows per lane, then a fixed warp tree).  xl, uol and Uol may be null
-// (zero low parts, no low output).  `sh` = NDOT x STB doubles.
+// 2u of the exact sum plus O(T^2 u^2) of the sum of |slots|.  The two halves
+// of the CTA take half the slots each; the low half's sum absorbs the high
+// half's with one more TwoSum.  The update u = U^k + w and the five dots run
+// in double-float arithmetic on the float32 pipe (float64 runs at a small
+// fraction of the float32 rate on this GPU): the per-row products are
+// TwoProducts, summed over the block's 128 rows by compensated accumulation
+// and a fixed lane / warp tree, and only the block's five sums become
+// float64.  xl, uol and Uol may be null (zero low parts, no low output);
+// rscale (FP8 tiles) multiplies the slot sums by the matrix's row scales.
+// `sh` = NDOT x STB doubles of shared memory (its first 2.2 KB are used).
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float a) {
   const float t = s + a;
   const float z = t - s;
@@ -60,11 +70,34 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float a) {
   s = t;
 }
 
+// The block's five double-float dot partials (valid in warps 0..3, the low
+// half) -> out[q * T] as pairs, in a fixed order.
+__device__ __forceinline__ void sym_dots_out(dflt (&dq)[NDOT], float2* __restrict__ out, int T, double* sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* shd = reinterpret_cast<float2*>(sh + 2 * STB);   // NDOT x 4 pairs, after the 2 KB slot exchange area
+  if (tid < STB) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q) {
+      const dflt r = df_warp_sum(dq[q]);
+      if (lane == 0) shd[q * 4 + warp] = make_float2(r.hi, r.lo);
+    }
+  }
+  __syncthreads();
+  if (tid < NDOT) {
+    dflt a = {shd[tid * 4].x, shd[tid * 4].y};
+#pragma unroll
+    for (int w = 1; w < STB / 32; ++w) a = df_add(a, dflt{shd[tid * 4 + w].x, shd[tid * 4 + w].y});
+    out[(size_t)tid * T] = make_float2(a.hi, a.lo);
+  }
+  __syncthreads();   // sh is reused by the caller
+}
+
 static __device__ void sym_rows(const Inst& I, const float* __restrict__ Ps, int R, int i,
                                 const float* __restrict__ x, const float* __restrict__ xl,
                                 const float* __restrict__ v, const float* __restrict__ uoh,
                                 const float* __restrict__ uol, float* __restrict__ Uoh, float* __restrict__ Uol,
-                                float* __restrict__ W, double* __restrict__ out, double* sh) {
+                                float* __restrict__ W, float2* __restrict__ out, double* sh,
+                                const float* __restrict__ rscale = nullptr) {
   const int T = I.tsym;
   const size_t ldp = (size_t)T * STB;
   const int tid = threadIdx.x, t = tid & (STB - 1), half = tid / STB;
@@ -77,54 +110,45 @@ static __device__ void sym_rows(const Inst& I, const float* __restrict__ Ps, int
   float2* shf = reinterpret_cast<float2*>(sh);
   if (half) shf[t] = make_float2(sa, ca);
   __syncthreads();
-  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  dflt dq[NDOT] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   const int j = R * STB + t;
   if (!half) {
     const float2 hi = shf[t];
     two_sum_acc(sa, ca, hi.x);
     ca += hi.y;
     if (j < I.n) {
-      const double w = (double)sa + (double)ca;
       const size_t o = (size_t)i * I.ldv + j;
-      const double uo = (double)uoh[o] + (uol ? (double)uol[o] : 0.0);
-      const double u = uo + w;
-      const float uh = (float)u;
-      Uoh[o] = uh;
-      if (Uol) Uol[o] = (float)(u - (double)uh);
-      W[o] = (float)w;
-      const double xj = (double)x[j] + (xl ? (double)xl[j] : 0.0), vj = v[j], cj = I.c[o];
-      dsum[0] = xj * u;
-      dsum[1] = vj * w;
-      dsum[2] = vj * uo;
-      dsum[3] = cj * xj;
-      dsum[4] = cj * vj;
+      dflt w = df_norm(sa, ca);
+      if (rscale) {   // FP8 tiles: the slot sums are C (s .* d); w_j = s_j (C (s .* d))_j
+        dflt ws = {0.f, 0.f};
+        df_acc_mulf(ws, w, rscale[j]);
+        w = df_norm(ws.hi, ws.lo);
+      }
+      const dflt uo = {uoh[o], uol ? uol[o] : 0.f};
+      const dflt u = df_add(uo, w);
+      Uoh[o] = u.hi;
+      if (Uol) Uol[o] = u.lo;
+      W[o] = w.hi;
+      const dflt xj = {x[j], xl ? xl[j] : 0.f};
+      const float vj = v[j], cj = I.c[o];
+      df_acc_mul(dq[0], xj, u);
+      df_acc_mulf(dq[1], w, vj);
+      df_acc_mulf(dq[2], uo, vj);
+      df_acc_mulf(dq[3], xj, cj);
+      const float p = __fmul_rn(cj, vj);
+      df_acc(dq[4], p, __fmaf_rn(cj, vj, -p));
     }
   }
-  __syncthreads();   // shf is read
-  if (!half) {
-#pragma unroll
-    for (int q = 0; q < NDOT; ++q) sh[q * STB + t] = dsum[q];
-  }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  if (warp < NDOT) {
-    const double* r = sh + warp * STB;
-    double a = r[lane];
-#pragma unroll
-    for (int k = 1; k < STB / 32; ++k) a += r[lane + 32 * k];
-    a = warp_sum(a);
-    if (lane == 0) out[(size_t)warp * T] = a;
-  }
-  __syncthreads();   // sh is reused by the caller
+  sym_dots_out(dq, out, T, sh);
 }
 
 // The same for a two-right-hand-side pass (kind 2): U = Q_i x and W = Q_i v
 // from the two slot sets Px, Pv (compensated float32 slot sums, one final
-// rounding each), dots x'U, v'W, 0, c'x, c'v in float64 as the row-streaming
-// pass forms them.
+// rounding each), dots x'U, v'W, 0, c'x, c'v of the float32 values, summed
+// as exact TwoProducts in double-float.
 static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, const float* __restrict__ Pv, int R,
                                  int i, const float* __restrict__ x, const float* __restrict__ v,
-                                 float* __restrict__ U, float* __restrict__ W, double* __restrict__ out, double* sh) {
+                                 float* __restrict__ U, float* __restrict__ W, float2* __restrict__ out, double* sh) {
   const int T = I.tsym;
   const size_t ldp = (size_t)T * STB;
   const int tid = threadIdx.x, t = tid & (STB - 1), half = tid / STB;
@@ -140,7 +164,7 @@ static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, co
   float4* shf = reinterpret_cast<float4*>(sh);
   if (half) shf[t] = make_float4(sa, ca, sb, cb);
   __syncthreads();
-  double dsum[NDOT] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  dflt dq[NDOT] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   const int j = R * STB + t;
   if (!half) {
     const float4 hi = shf[t];
@@ -153,35 +177,25 @@ static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, co
       const float u = sa + ca, w = sb + cb;
       U[o] = u;
       W[o] = w;
-      const double xj = x[j], vj = v[j], cj = I.c[o];
-      dsum[0] = xj * (double)u;
-      dsum[1] = vj * (double)w;
-      dsum[3] = cj * xj;
-      dsum[4] = cj * vj;
+      const float xj = x[j], vj = v[j], cj = I.c[o];
+      float p = __fmul_rn(xj, u);
+      df_acc(dq[0], p, __fmaf_rn(xj, u, -p));
+      p = __fmul_rn(vj, w);
+      df_acc(dq[1], p, __fmaf_rn(vj, w, -p));
+      p = __fmul_rn(cj, xj);
+      df_acc(dq[3], p, __fmaf_rn(cj, xj, -p));
+      p = __fmul_rn(cj, vj);
+      df_acc(dq[4], p, __fmaf_rn(cj, vj, -p));
     }
   }
-  __syncthreads();   // shf is read
-  if (!half) {
-#pragma unroll
-    for (int q = 0; q < NDOT; ++q) sh[q * STB + t] = dsum[q];
-  }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  if (warp < NDOT) {
-    const double* r = sh + warp * STB;
-    double a = r[lane];
-#pragma unroll
-    for (int k = 1; k < STB / 32; ++k) a += r[lane + 32 * k];
-    a = warp_sum(a);
-    if (lane == 0) out[(size_t)warp * T] = a;
-  }
-  __syncthreads();
+  sym_dots_out(dq, out, T, sh);
 }
 
 // One CTA's share of the tile products of a packed pass: tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... of the (M x ntile) list.  Each 64 KB tile is
-// contiguous: one bulk copy (TMA unit) moves it into a shared-memory stage,
-// SNST stages in flight, completed on the stage's mbarrier.  The CTA has
+// blockIdx.x + gridDim.x, ... of the (M x ntile) list.  Each tile (64 KB of
+// float32, 32 KB of BF16 or 16 KB of FP8 codes) is contiguous: one bulk copy
+// (TMA unit) moves it into a shared-memory stage, 3 / 6 / 12 stages in
+// flight, completed on the stage's mbarrier.  The CTA has
 // NTS = 512 threads: warp w takes rows 8w .. 8w+7 of the tile, lane l columns
 // 4l .. 4l+3 (row partials halved over the lanes, column partials summed over
 // the 16 warps in order: at most 8 + 15 float32 roundings per partial).  The
@@ -190,16 +204,53 @@ static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, co
 // global fences: the row-block reduction runs in the next kernel.  Every wait
 // is bounded; on a timeout the CTA sets *err, waits (bounded) for its copies
 // in flight and returns.
-// `dsm` = [SNST mbarriers (128 B) | 2 x NWS x STB floats | SNST x 64 KB stages].
+// `dsm` = [stage mbarriers (128 B) | 2 x NWS x STB floats | 192 KB of stages].
 constexpr int NTS = 512;
 constexpr int NWS = NTS / 32;
 constexpr int SRW8 = STB / NWS;      // tile rows per warp (8)
 static_assert(SRW8 == 8, "warp_rows8 reduces 8 rows per warp");
-constexpr int SNST = 3;
+constexpr int SNST = 3;                          // float32 stages of 64 KB
 constexpr uint32_t STILE = (uint32_t)STB * STB * 4;
 __host__ __device__ constexpr size_t sym_smem_bytes() {
   return (size_t)128 + (size_t)2 * NWS * STB * 4 + (size_t)SNST * STILE;
 }
+
+// Stored tile elements: a thread reads 4 consecutive entries of each of its
+// 8 rows (16, 8 or 4 bytes) and decodes them to float32.  The quantised
+// tiles use the same 192 KB of stages: more, smaller stages in flight.
+template <int ST> struct TileElt;
+template <> struct TileElt<RAPDB_F32> {
+  using raw = uint4;
+  static constexpr int B = 4;
+  __device__ __forceinline__ static void dec(const raw& r, float (&o)[4]) {
+    o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+    o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+  }
+};
+template <> struct TileElt<RAPDB_BF16> {
+  using raw = uint2;
+  static constexpr int B = 2;
+  __device__ __forceinline__ static void dec(const raw& r, float (&o)[4]) {
+    o[0] = __uint_as_float(r.x << 16); o[1] = __uint_as_float(r.x & 0xffff0000u);
+    o[2] = __uint_as_float(r.y << 16); o[3] = __uint_as_float(r.y & 0xffff0000u);
+  }
+};
+template <> struct TileElt<RAPDB_FP8> {
+  using raw = uint32_t;
+  static constexpr int B = 1;
+  __device__ __forceinline__ static void dec(const raw& r, float (&o)[4]) {
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+template <int ST>
+__host__ __device__ constexpr uint32_t sym_tile_bytes() { return (uint32_t)STB * STB * TileElt<ST>::B; }
+template <int ST>
+__host__ __device__ constexpr int sym_stages() { return SNST * 4 / TileElt<ST>::B; }
+static_assert(sym_stages<RAPDB_FP8>() * 8 <= 128, "mbarriers of the stages fit their 128-byte area");
 
 // Lane l returns the sum over the 32 lanes of a[r] for r = sym_row8(l) (the
 // four lanes that share l >> 2 return the same value).
@@ -240,13 +291,39 @@ __device__ __forceinline__ void sym_dslices(const float* __restrict__ v, int n, 
 }
 
 // NR right-hand sides r0 (and r1): the products of r_k go to slot set k,
-// I.sp + k * M * T * T * STB.
-template <int NR>
+// I.sp + k * M * T * T * STB.  ST selects the tiles: the float32 ones (I.Qp)
+// or the quantised ones (I.Qpq, BF16 or FP8 codes).  The right-hand side of
+// stored matrix s is r + s * rstride (FP8: its pre-scaled copy s_s .* d;
+// otherwise rstride = 0).
+// Tile t of the upper block triangle (row-major over I <= J, the order of
+// the tile table): row I is the largest with I T - I(I-1)/2 <= t.  Computed
+// from t (a float square root, then an exact integer correction), so the
+// tile loop issues no dependent table load.
+__device__ __forceinline__ void sym_tile_coords(int t, int T, int& TI, int& TJ) {
+  const float b = 2.0f * (float)T + 1.0f;
+  int i = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)t, 0.0f))));
+  i = max(0, min(i, T - 1));
+  auto off = [&](int r) { return r * T - (r * (r - 1)) / 2; };
+  while (i > 0 && off(i) > t) --i;
+  while (i + 1 < T && off(i + 1) <= t) ++i;
+  TI = i;
+  TJ = i + (t - off(i));
+}
+
+template <int NR, int ST>
 __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict__ r0, const float* __restrict__ r1,
-                                          uint8_t* dsm, int* err) {
-  const int T = I.tsym, nt = I.ntile;
+                                          size_t rstride, uint8_t* dsm, int* err) {
+  using TE = TileElt<ST>;
+  constexpr uint32_t TB = sym_tile_bytes<ST>();
+  constexpr int NSG = sym_stages<ST>();
+  // the instance's fields in registers (re-reading them after each barrier
+  // would put a dependent load into every tile)
+  const uint8_t* Qt = (ST == RAPDB_F32) ? reinterpret_cast<const uint8_t*>(I.Qp)
+                                        : reinterpret_cast<const uint8_t*>(I.Qpq);
+  const int T = I.tsym, nt = I.ntile, M = I.M, n = I.n;
+  float* const sp = I.sp;
   const size_t ldp = (size_t)T * STB;
-  const int total = I.M * nt;
+  const int total = M * nt;
   const int first = blockIdx.x, G = gridDim.x;
   if (first >= total) return;
   const int K = (total - first + G - 1) / G;          // tiles of this CTA
@@ -256,40 +333,45 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
   float* sred = reinterpret_cast<float*>(dsm + 128);
   uint8_t* stg = dsm + 128 + (size_t)2 * NWS * STB * 4;
   if (tid == 0) {
-    for (int k = 0; k < SNST; ++k) mbar_init(&full[k], 1);
+    for (int k = 0; k < NSG; ++k) mbar_init(&full[k], 1);
     fence_proxy_async();
   }
   __syncthreads();
   // the tiles are read once per pass: first out of L2, so that the slot
   // partials stay there for the row-block kernel
   const uint64_t pol = l2_policy_evict_first();
-  auto issue = [&](int k) {   // thread 0: tile k of this CTA -> stage k % SNST
-    const int st = k % SNST;
+  auto issue = [&](int k) {   // thread 0: tile k of this CTA -> stage k % NSG
+    const int st = k % NSG;
     const size_t it = (size_t)first + (size_t)k * G;
-    mbar_expect_tx(&full[st], STILE);
-    bulk_g2s_evict_first(stg + (size_t)st * STILE, I.Qp + it * STB * STB, STILE, &full[st], pol);
+    mbar_expect_tx(&full[st], TB);
+    bulk_g2s_evict_first(stg + (size_t)st * TB, Qt + it * TB, TB, &full[st], pol);
   };
   if (tid == 0)
-    for (int k = 0; k < SNST && k < K; ++k) issue(k);
+    for (int k = 0; k < NSG && k < K; ++k) issue(k);
   auto coords = [&](int k, int& s, int& TI, int& TJ) {
     const int it = first + k * G;
     s = it / nt;
-    const int ij = __ldg(I.tij + (it - s * nt));
-    TI = ij >> 16;
-    TJ = ij & 0xffff;
+    sym_tile_coords(it - s * nt, T, TI, TJ);
   };
-  int s, TI, TJ;
+  // right-hand-side slices two tiles ahead: those of tile k (cur) and k + 1 (nxt)
+  int s, TI, TJ, ns = 0, nI = 0, nJ = 0;
   coords(0, s, TI, TJ);
-  float dj[NR][4], dil[NR];
+  float dj[NR][4], dil[NR], nj[NR][4], nil[NR];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) sym_dslices(rhs[r], I.n, TI, TJ, dj[r], dil[r]);
+  for (int r = 0; r < NR; ++r) sym_dslices(rhs[r] + (size_t)s * rstride, n, TI, TJ, dj[r], dil[r]);
+  if (K > 1) {
+    coords(1, ns, nI, nJ);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sym_dslices(rhs[r] + (size_t)ns * rstride, n, nI, nJ, nj[r], nil[r]);
+  }
   for (int k = 0; k < K; ++k) {
-    const int st = k % SNST;
-    const bool got = mbar_wait_bounded(&full[st], (uint32_t)((k / SNST) & 1), err);
+    const int st = k % NSG;
+    // (this barrier also ends the previous tile's column sums: sred is free)
+    const bool got = mbar_wait_bounded(&full[st], (uint32_t)((k / NSG) & 1), err);
     if (!__syncthreads_and(got)) {
       if (tid == 0)
-        for (int k2 = k; k2 < K && k2 < k + SNST; ++k2)
-          mbar_wait_bounded(&full[k2 % SNST], (uint32_t)((k2 / SNST) & 1), err);
+        for (int k2 = k; k2 < K && k2 < k + NSG; ++k2)
+          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
       __syncthreads();
       return;
     }
@@ -297,8 +379,8 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
     if (!__syncthreads_and(TI >= 0 && TI <= TJ && TJ < T)) {
       if (tid == 0) {
         if (err) atomicCAS(err, 0, CHK_SYM_RANGE);
-        for (int k2 = k + 1; k2 < K && k2 < k + SNST; ++k2)
-          mbar_wait_bounded(&full[k2 % SNST], (uint32_t)((k2 / SNST) & 1), err);
+        for (int k2 = k + 1; k2 < K && k2 < k + NSG; ++k2)
+          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
       }
       __syncthreads();
       return;
@@ -309,14 +391,16 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
 #pragma unroll
     for (int r = 0; r < NR; ++r) cp[r][0] = cp[r][1] = cp[r][2] = cp[r][3] = 0.f;
     {
-      const uint8_t* sp = stg + (size_t)st * STILE + ((size_t)warp * SRW8 * STB + lane * 4) * 4;
-      uint4 raw[SRW8];
+      const uint8_t* stp = stg + (size_t)st * TB + ((size_t)warp * SRW8 * STB + lane * 4) * TE::B;
+      typename TE::raw raw[SRW8];
 #pragma unroll
-      for (int q = 0; q < SRW8; ++q) raw[q] = *reinterpret_cast<const uint4*>(sp + (size_t)q * STB * 4);
+      for (int q = 0; q < SRW8; ++q)
+        raw[q] = *reinterpret_cast<const typename TE::raw*>(stp + (size_t)q * STB * TE::B);
 #pragma unroll
       for (int q = 0; q < SRW8; ++q) {
-        const float b0 = __uint_as_float(raw[q].x), b1 = __uint_as_float(raw[q].y);
-        const float b2 = __uint_as_float(raw[q].z), b3 = __uint_as_float(raw[q].w);
+        float bq[4];
+        TE::dec(raw[q], bq);
+        const float b0 = bq[0], b1 = bq[1], b2 = bq[2], b3 = bq[3];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           rp[r][q] = fmaf(b3, dj[r][3], fmaf(b2, dj[r][2], fmaf(b1, dj[r][1], b0 * dj[r][0])));
@@ -328,37 +412,209 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
         }
       }
     }
-    __syncthreads();   // the stage is consumed (and sred of the previous tile read)
-    if (tid == 0 && k + SNST < K) {
-      fence_proxy_async();
-      issue(k + SNST);
-    }
-    const int cs = s, cI = TI, cJ = TJ;
-    if (k + 1 < K) {   // the next tile's slices, in flight during the reduction
-      coords(k + 1, s, TI, TJ);
-#pragma unroll
-      for (int r = 0; r < NR; ++r) sym_dslices(rhs[r], I.n, TI, TJ, dj[r], dil[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      float* Ps = I.sp + ((size_t)r * I.M + cs) * T * ldp;
-      const float rv = warp_rows8(rp[r]);
-      if (!(lane & 3)) Ps[(size_t)cJ * ldp + (size_t)cI * STB + warp * SRW8 + sym_row8(lane)] = rv;
-    }
-    if (cI != cJ) {
+    const bool offd = TI != TJ;
+    if (offd) {   // column partials of an off-diagonal tile, summed over the warps below
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         *reinterpret_cast<float4*>(sred + (r * NWS + warp) * STB + lane * 4) =
             make_float4(cp[r][0], cp[r][1], cp[r][2], cp[r][3]);
-      __syncthreads();
-      if (tid < NR * STB) {
-        const int r = tid / STB, c0 = tid - r * STB;
-        const float* sr = sred + r * NWS * STB + c0;
-        float c = sr[0];
+    }
+    __syncthreads();   // the stage is consumed and the column partials are in sred
+    if (tid == 0 && k + NSG < K) {
+      fence_proxy_async();
+      issue(k + NSG);
+    }
+    const int cs = s, cI = TI, cJ = TJ;
+    // advance the slices: tile k + 1's are in flight already, tile k + 2's start now
+    s = ns;
+    TI = nI;
+    TJ = nJ;
 #pragma unroll
-        for (int w = 1; w < NWS; ++w) c += sr[w * STB];
-        I.sp[(((size_t)r * I.M + cs) * T + cI) * ldp + (size_t)cJ * STB + c0] = c;
+    for (int r = 0; r < NR; ++r) {
+      dil[r] = nil[r];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dj[r][e] = nj[r][e];
+    }
+    if (k + 2 < K) {
+      coords(k + 2, ns, nI, nJ);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) sym_dslices(rhs[r] + (size_t)ns * rstride, n, nI, nJ, nj[r], nil[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      float* Ps = sp + ((size_t)r * M + cs) * T * ldp;
+      const float rv = warp_rows8(rp[r]);
+      if (!(lane & 3)) Ps[(size_t)cJ * ldp + (size_t)cI * STB + warp * SRW8 + sym_row8(lane)] = rv;
+    }
+    if (offd && tid < NR * STB) {
+      const int r = tid / STB, c0 = tid - r * STB;
+      const float* sr = sred + r * NWS * STB + c0;
+      float v[NWS];
+#pragma unroll
+      for (int w = 0; w < NWS; ++w) v[w] = sr[w * STB];
+      float c = v[0];
+#pragma unroll
+      for (int w = 1; w < NWS; ++w) c += v[w];
+      sp[(((size_t)r * M + cs) * T + cI) * ldp + (size_t)cJ * STB + c0] = c;
+    }
+  }
+}
+
+// The quantised tiles (BF16 / FP8, one right-hand side) two at a time: a
+// 16- or 32-KB tile takes as much arithmetic as a 64-KB float32 one, and one
+// tile per loop iteration leaves the CTA waiting on its own barriers and
+// shuffle chains (latency-bound at about half the copy bandwidth).  Each
+// warp takes its 8 rows of tiles k and k + 1 together (independent
+// instruction streams), with one pair of barriers per two tiles; the column
+// partials of the two tiles go to the two halves of sred and are summed by
+// the two halves of the CTA.  Same arithmetic per tile as sym_tiles<1, ST>.
+template <int ST>
+__device__ __forceinline__ void sym_tiles_q(const Inst& I, const float* __restrict__ r0, size_t rstride,
+                                            uint8_t* dsm, int* err) {
+  using TE = TileElt<ST>;
+  constexpr uint32_t TB = sym_tile_bytes<ST>();
+  constexpr int NSG = sym_stages<ST>();
+  static_assert(NSG % 2 == 0, "pairs of stages");
+  const uint8_t* Qt = reinterpret_cast<const uint8_t*>(I.Qpq);
+  const int T = I.tsym, nt = I.ntile, M = I.M, n = I.n;
+  float* const sp = I.sp;
+  const size_t ldp = (size_t)T * STB;
+  const int total = M * nt;
+  const int first = blockIdx.x, G = gridDim.x;
+  if (first >= total) return;
+  const int K = (total - first + G - 1) / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
+  float* sred = reinterpret_cast<float*>(dsm + 128);
+  uint8_t* stg = dsm + 128 + (size_t)2 * NWS * STB * 4;
+  if (tid == 0) {
+    for (int k = 0; k < NSG; ++k) mbar_init(&full[k], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const uint64_t pol = l2_policy_evict_first();
+  auto issue = [&](int k) {
+    const int st = k % NSG;
+    const size_t it = (size_t)first + (size_t)k * G;
+    mbar_expect_tx(&full[st], TB);
+    bulk_g2s_evict_first(stg + (size_t)st * TB, Qt + it * TB, TB, &full[st], pol);
+  };
+  if (tid == 0)
+    for (int k = 0; k < NSG && k < K; ++k) issue(k);
+  auto coords = [&](int k, int& s, int& TI, int& TJ) {
+    const int it = first + k * G;
+    s = it / nt;
+    sym_tile_coords(it - s * nt, T, TI, TJ);
+  };
+  auto slices = [&](int k, int& s, int& TI, int& TJ, float (&dj)[4], float& dil) {
+    if (k < K) {
+      coords(k, s, TI, TJ);
+      sym_dslices(r0 + (size_t)s * rstride, n, TI, TJ, dj, dil);
+    } else {
+      s = 0; TI = 0; TJ = 0; dil = 0.f;
+      dj[0] = dj[1] = dj[2] = dj[3] = 0.f;
+    }
+  };
+  // slices of the current pair (a: k, b: k + 1) and the next (k + 2, k + 3)
+  int sa, ia, ja, sb, ib, jb, nsa, nia, nja, nsb, nib, njb;
+  float dja[4], dila, djb[4], dilb, nja4[4], nila, njb4[4], nilb;
+  slices(0, sa, ia, ja, dja, dila);
+  slices(1, sb, ib, jb, djb, dilb);
+  slices(2, nsa, nia, nja, nja4, nila);
+  slices(3, nsb, nib, njb, njb4, nilb);
+  for (int k = 0; k < K; k += 2) {
+    const bool hb = k + 1 < K;
+    const int sta = k % NSG, stb = (k + 1) % NSG;
+    bool got = mbar_wait_bounded(&full[sta], (uint32_t)((k / NSG) & 1), err);
+    if (hb) got = got && mbar_wait_bounded(&full[stb], (uint32_t)(((k + 1) / NSG) & 1), err);
+    if (!__syncthreads_and(got)) {
+      if (tid == 0)
+        for (int k2 = k; k2 < K && k2 < k + NSG; ++k2)
+          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
+      __syncthreads();
+      return;
+    }
+#ifdef RAPDB_CHECKED
+    if (!__syncthreads_and(ia >= 0 && ia <= ja && ja < T && (!hb || (ib >= 0 && ib <= jb && jb < T)))) {
+      if (tid == 0) {
+        if (err) atomicCAS(err, 0, CHK_SYM_RANGE);
+        for (int k2 = k + 2; k2 < K && k2 < k + NSG; ++k2)
+          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
       }
+      __syncthreads();
+      return;
+    }
+#endif
+    float rpa[SRW8], rpb[SRW8], cpa[4] = {0.f, 0.f, 0.f, 0.f}, cpb[4] = {0.f, 0.f, 0.f, 0.f};
+    {
+      const size_t off = ((size_t)warp * SRW8 * STB + lane * 4) * TE::B;
+      const uint8_t* pa = stg + (size_t)sta * TB + off;
+      const uint8_t* pb = stg + (size_t)stb * TB + off;
+      typename TE::raw ra[SRW8], rb_[SRW8];
+#pragma unroll
+      for (int q = 0; q < SRW8; ++q) {
+        ra[q] = *reinterpret_cast<const typename TE::raw*>(pa + (size_t)q * STB * TE::B);
+        rb_[q] = hb ? *reinterpret_cast<const typename TE::raw*>(pb + (size_t)q * STB * TE::B) : ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < SRW8; ++q) {
+        float ba[4], bb[4];
+        TE::dec(ra[q], ba);
+        TE::dec(rb_[q], bb);
+        rpa[q] = fmaf(ba[3], dja[3], fmaf(ba[2], dja[2], fmaf(ba[1], dja[1], ba[0] * dja[0])));
+        rpb[q] = fmaf(bb[3], djb[3], fmaf(bb[2], djb[2], fmaf(bb[1], djb[1], bb[0] * djb[0])));
+        const float da = __shfl_sync(0xffffffffu, dila, q);
+        const float db = __shfl_sync(0xffffffffu, dilb, q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          cpa[e] = fmaf(ba[e], da, cpa[e]);
+          cpb[e] = fmaf(bb[e], db, cpb[e]);
+        }
+      }
+    }
+    const bool offa = ia != ja, offb = hb && ib != jb;
+    if (offa)
+      *reinterpret_cast<float4*>(sred + warp * STB + lane * 4) = make_float4(cpa[0], cpa[1], cpa[2], cpa[3]);
+    if (offb)
+      *reinterpret_cast<float4*>(sred + (NWS + warp) * STB + lane * 4) = make_float4(cpb[0], cpb[1], cpb[2], cpb[3]);
+    __syncthreads();   // both stages consumed, both tiles' column partials in sred
+    if (tid == 0) {
+      fence_proxy_async();
+      if (k + NSG < K) issue(k + NSG);
+      if (k + 1 + NSG < K) issue(k + 1 + NSG);
+    }
+    const int csa = sa, cia = ia, cja = ja, csb = sb, cib = ib, cjb = jb;
+    sa = nsa; ia = nia; ja = nja; dila = nila;
+    sb = nsb; ib = nib; jb = njb; dilb = nilb;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      dja[e] = nja4[e];
+      djb[e] = njb4[e];
+    }
+    slices(k + 4, nsa, nia, nja, nja4, nila);
+    slices(k + 5, nsb, nib, njb, njb4, nilb);
+    {
+      const float rv = warp_rows8(rpa);
+      if (!(lane & 3))
+        sp[(size_t)csa * T * ldp + (size_t)cja * ldp + (size_t)cia * STB + warp * SRW8 + sym_row8(lane)] = rv;
+    }
+    if (hb) {
+      const float rv = warp_rows8(rpb);
+      if (!(lane & 3))
+        sp[(size_t)csb * T * ldp + (size_t)cjb * ldp + (size_t)cib * STB + warp * SRW8 + sym_row8(lane)] = rv;
+    }
+    // column sums: the low half of the CTA for tile k, the high half for k + 1
+    const int half = tid / STB, c0 = tid - half * STB;
+    if (half < 2 && (half == 0 ? offa : offb)) {
+      const float* sr = sred + half * NWS * STB + c0;
+      float v[NWS];
+#pragma unroll
+      for (int w = 0; w < NWS; ++w) v[w] = sr[w * STB];
+      float c = v[0];
+#pragma unroll
+      for (int w = 1; w < NWS; ++w) c += v[w];
+      const int cs = half ? csb : csa, cI = half ? cib : cia, cJ = half ? cjb : cja;
+      sp[((size_t)cs * T + cI) * ldp + (size_t)cJ * STB + c0] = c;
     }
   }
 }
@@ -380,26 +636,34 @@ __device__ __forceinline__ void gap_rhs(const Inst& I, int phase, const float*& 
 // right-hand sides); outside such a phase every CTA returns at once.  The row
 // blocks, dots and control follow in k_sym_finish.  One persistent CTA per
 // SM.
-template <int DUMMY>
+// ST is the context's storage: a quantised context's trials at the quantised
+// level (kind 3) read its BF16 / FP8 tiles; the FP8 right-hand sides are the
+// pre-scaled copies VS (s_s .* d per stored matrix) the vector kernel wrote.
+template <int ST>
 __global__ void __launch_bounds__(NTS, 1) k_sym_tiles(const Inst* __restrict__ insts, const State* __restrict__ states,
-                                                     Ctrl* __restrict__ ctrl) {
+                                                     Ctrl* __restrict__ ctrl, const float* __restrict__ VS) {
   extern __shared__ __align__(128) uint8_t dsm[];
   const Inst& I = insts[0];
   const State& S = states[0];
   const int kind = sym_kind(I, S);
   if (kind == 0) return;
 #ifdef RAPDB_CHECKED
-  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes()) {
+  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes() || (kind == 3 && (ST == RAPDB_F32 || I.storage != ST))) {
     if (threadIdx.x == 0) atomicCAS(&ctrl->err, 0, CHK_SYM_RANGE);
     return;
   }
 #endif
   if (kind == 1) {
-    sym_tiles<1>(I, I.dv, nullptr, dsm, &ctrl->err);
-  } else {
+    sym_tiles<1, RAPDB_F32>(I, I.dv, nullptr, 0, dsm, &ctrl->err);
+  } else if (kind == 2) {
     const float *x, *v;
     gap_rhs(I, S.phase, x, v);
-    sym_tiles<2>(I, x, v, dsm, &ctrl->err);
+    sym_tiles<2, RAPDB_F32>(I, x, v, 0, dsm, &ctrl->err);
+  } else if constexpr (ST != RAPDB_F32) {
+    if (ST == RAPDB_FP8)
+      sym_tiles_q<ST>(I, VS, (size_t)I.ldv, dsm, &ctrl->err);
+    else
+      sym_tiles_q<ST>(I, I.dv, 0, dsm, &ctrl->err);
   }
 }
 
@@ -435,19 +699,17 @@ __global__ void __launch_bounds__(NT, 2) k_pass_sym(const Inst* __restrict__ ins
 }
 
 // Second kernel of a packed pass: one CTA per row block (grid M x T) sums
-// the block's slots, forms its products (kind 1: the incremental update; kind
-// 2: U = Q x, W = Q v) and goes on to the pass's fixed-order dot reduction
-// and control step.  Every CTA reads the phase before it arrives, so none can
-// see the state the control step leaves; outside a packed pass all return at
-// once.
-template <int DUMMY>
+// the block's slots and forms its products (kind 1 / 3: the incremental
+// update; kind 2: U = Q x, W = Q v) and the block's dot partials.  No
+// arrival counters and no fences: the third kernel (k_sym_ctrl) reduces the
+// partials and runs the control step after the kernel boundary.  Outside a
+// packed pass every CTA returns at once.
+template <int ST>
 __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ insts, State* __restrict__ states,
                                                    Ctrl* __restrict__ ctrl) {
-  __shared__ double red[NWARP * NDOT];
   __shared__ __align__(16) double sh[NDOT * STB];   // (read as float2 / float4 by the slot sums)
-  __shared__ int s_dec;
   const Inst& I = insts[0];
-  State& S = states[0];
+  const State& S = states[0];
   const int kind = sym_kind(I, S);
   if (kind == 0) return;
   const int T = I.tsym;
@@ -456,40 +718,90 @@ __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ inst
     if (threadIdx.x == 0) atomicCAS(&ctrl->err, 0, CHK_SYM_RANGE);
     return;
   }
+#else
+  (void)ctrl;
 #endif
   const int s = blockIdx.x / T, R = blockIdx.x - s * T;
   const int i = s + I.s_off;
-  const int phase = S.phase;
   const float* Ps = I.sp + (size_t)s * T * T * STB;
-  double* out = I.spart + (size_t)s * NDOT * T + R;
-  if (kind == 1) {
-    const float* x = I.xf[S.xcur ^ 1];
-    sym_rows(I, Ps, R, i, x, I.xl[S.xcur ^ 1], I.dv, I.U[S.ucur], I.Ulo[S.ucur], I.U[S.ucur ^ 1],
-             I.Ulo[S.ucur ^ 1], I.W, out, sh);
-    pass_finish(I, S, ctrl, s, i, I.spart, T, phase, true, x, I.dv, red, s_dec);
+  float2* out = I.spart + (size_t)s * NDOT * T + R;
+  if (kind == 1 || kind == 3) {
+    // kind 3 with FP8 tiles: the slot sums carry the row scales of matrix s
+    const float* rs = (kind == 3 && ST == RAPDB_FP8) ? I.qscale + (size_t)s * I.ldv : nullptr;
+    sym_rows(I, Ps, R, i, I.xf[S.xcur ^ 1], I.xl[S.xcur ^ 1], I.dv, I.U[S.ucur], I.Ulo[S.ucur], I.U[S.ucur ^ 1],
+             I.Ulo[S.ucur ^ 1], I.W, out, sh, rs);
   } else {
     const float *x, *v;
-    gap_rhs(I, phase, x, v);
+    gap_rhs(I, S.phase, x, v);
     sym_rows2(I, Ps, Ps + (size_t)I.M * T * T * STB, R, i, x, v, I.U[S.ucur ^ 1], I.W, out, sh);
-    pass_finish(I, S, ctrl, s, i, I.spart, T, phase, false, x, v, red, s_dec);
+  }
+}
+
+// Third kernel of a packed pass (one CTA): each matrix's row-block partials
+// summed in row-block order (double-float, one thread per matrix and dot)
+// into I.dots, then the pass's control step.
+// The control step works on a shared-memory copy of the state (written back
+// at the end): its serial scalar updates then cost no global round trips.
+template <int DUMMY>
+__global__ void __launch_bounds__(NT) k_sym_ctrl(const Inst* __restrict__ insts, State* __restrict__ states,
+                                                 Ctrl* __restrict__ ctrl) {
+  __shared__ double red[NWARP * NDOT];
+  __shared__ int s_dec;
+  __shared__ __align__(16) State S;
+  const Inst& I = insts[0];
+  {
+    static_assert(sizeof(State) % 4 == 0, "state copy in words");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&states[0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&S);
+    for (int w = threadIdx.x; w < (int)(sizeof(State) / 4); w += NT) dst[w] = src[w];
+  }
+  __syncthreads();
+  const int kind = sym_kind(I, S);
+  if (kind == 0) return;
+  const int T = I.tsym, phase = S.phase;
+  for (int pq = threadIdx.x; pq < I.M * NDOT; pq += NT) {
+    const int s = pq / NDOT, q = pq - s * NDOT;
+    I.dots[(size_t)(s + I.s_off) * NDOT + q] = df_to_double(df_sum_pairs(I.spart + ((size_t)s * NDOT + q) * T, T));
+  }
+  __syncthreads();
+  if (kind == 2) {
+    const float *x, *v;
+    gap_rhs(I, phase, x, v);
+    pass_control(I, S, ctrl, phase, false, x, v, red, s_dec);
+  } else {
+    pass_control(I, S, ctrl, phase, true, I.xf[S.xcur ^ 1], I.dv, red, s_dec);
+  }
+  __syncthreads();
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&S);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&states[0]);
+    for (int w = threadIdx.x; w < (int)(sizeof(State) / 4); w += NT) dst[w] = src[w];
   }
 }
 
 // Stand-alone packed pass (no control), in two kernels like the solver's:
 // the tile products, then W = Q_i v and U = uold + W per row block with the
 // block's dot partials in spart.  Arrays are (m+1, ldv) bases indexed by the
-// constraint row; xl, uol, Ulo may be null.
-template <int DUMMY>
+// constraint row; xl, uol, Ulo may be null.  quant = 1 reads the quantised
+// tiles of a BF16 / FP8 context (FP8: v is the pre-scaled (M, ldv) array
+// s_s .* v and the row-block kernel gets the row scales).
+template <int ST>
 __global__ void __launch_bounds__(NTS, 1) k_sym_plain(const Inst* __restrict__ insts, const float* __restrict__ v,
-                                                     int* err) {
+                                                     int quant, int* err) {
   extern __shared__ __align__(128) uint8_t dsm[];
 #ifdef RAPDB_CHECKED
-  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes()) {
+  if (dyn_smem_bytes() < (unsigned)sym_smem_bytes() || (quant && (ST == RAPDB_F32 || insts[0].storage != ST))) {
     if (threadIdx.x == 0 && err) atomicCAS(err, 0, CHK_SYM_RANGE);
     return;
   }
 #endif
-  sym_tiles<1>(insts[0], v, nullptr, dsm, err);
+  if constexpr (ST != RAPDB_F32) {
+    if (quant) {
+      sym_tiles_q<ST>(insts[0], v, ST == RAPDB_FP8 ? (size_t)insts[0].ldv : 0, dsm, err);
+      return;
+    }
+  }
+  sym_tiles<1, RAPDB_F32>(insts[0], v, nullptr, 0, dsm, err);
 }
 
 template <int DUMMY>
@@ -497,14 +809,15 @@ __global__ void __launch_bounds__(NT) k_sym_rows_plain(const Inst* __restrict__ 
                                                        const float* __restrict__ xl, const float* __restrict__ v,
                                                        const float* __restrict__ uoh, const float* __restrict__ uol,
                                                        float* __restrict__ U, float* __restrict__ Ulo,
-                                                       float* __restrict__ W, double* __restrict__ spart) {
+                                                       float* __restrict__ W, float2* __restrict__ spart,
+                                                       const float* __restrict__ rscale) {
   __shared__ __align__(16) double sh[NDOT * STB];   // (read as float2 / float4 by the slot sums)
   const Inst& I = insts[0];
   const int T = I.tsym;
   if (blockIdx.x >= (unsigned)(I.M * T)) return;
   const int s = blockIdx.x / T, R = blockIdx.x - s * T;
   sym_rows(I, I.sp + (size_t)s * T * T * STB, R, s + I.s_off, x, xl, v, uoh, uol, U, Ulo, W,
-           spart + (size_t)s * NDOT * T + R, sh);
+           spart + (size_t)s * NDOT * T + R, sh, rscale ? rscale + (size_t)s * I.ldv : nullptr);
 }
 
 }  // namespace rapdb_dev

@@ -20,8 +20,10 @@ __global__ void k_quant_bf16(const float* __restrict__ Q, int n, long long rows,
 }
 
 // FP8 symmetric Jacobi scaling: r_j = 1/sqrt(Q_jj) (1 when Q_jj <= 0),
-// C_jk = ((Q_jk r_j) r_k) 256 rounded to E4M3 (nearest even, saturating),
-// s_j = sqrt(Q_jj)/16 (1/16 when Q_jj <= 0), so Q~ = S dec(C) S.
+// C_jk = (Q_jk (r_j r_k)) 256 rounded to E4M3 (nearest even, saturating),
+// s_j = sqrt(Q_jj)/16 (1/16 when Q_jj <= 0), so Q~ = S dec(C) S.  The factor
+// r_j r_k is formed first, so C (and Q~) is exactly symmetric, which the
+// packed upper block triangle relies on.
 __global__ void k_fp8_scales(const float* __restrict__ Q, int n, int M, int ldv, float* __restrict__ rinv,
                              float* __restrict__ scale) {
   const long long total = (long long)M * n;
@@ -45,8 +47,8 @@ __global__ void k_quant_fp8(const float* __restrict__ Q, int n, int M, int ld, i
     const int col = (int)(e - r * n);
     const int s = (int)(r / n);
     const int j = (int)(r - (long long)s * n);
-    const float a = __fmul_rn(Q[e], rinv[(size_t)s * ldv + j]);
-    const float cval = __fmul_rn(__fmul_rn(a, rinv[(size_t)s * ldv + col]), 256.0f);
+    const float rr = __fmul_rn(rinv[(size_t)s * ldv + j], rinv[(size_t)s * ldv + col]);
+    const float cval = __fmul_rn(__fmul_rn(Q[e], rr), 256.0f);
     out[r * ld + col] = __nv_cvt_float_to_fp8(cval, __NV_SATFINITE, __NV_E4M3);
   }
 }
@@ -96,22 +98,35 @@ __global__ void k_pack_sym(const float* __restrict__ Q, int ld, int n, int M, in
   }
 }
 
+// The same tiles of the quantised stored matrices (EB-byte codes, row
+// stride ld): Qp[s][t] = codes of Q~_s[I*STB .., J*STB ..], zero outside n x n
+// (a zero code is 0.0 in BF16 and in E4M3).
+template <typename T_>
+__global__ void k_pack_sym_codes(const T_* __restrict__ Q, int ld, int n, int M, int ntile,
+                                 const int* __restrict__ tij, T_* __restrict__ Qp) {
+  const int64_t total = (int64_t)M * ntile * STB * STB;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % STB);
+    const int r = (int)((e / STB) % STB);
+    const int64_t st = e / ((int64_t)STB * STB);
+    const int t = (int)(st % ntile);
+    const int s = (int)(st / ntile);
+    const int ij = tij[t];
+    const int row = (ij >> 16) * STB + r, col = (ij & 0xffff) * STB + c;
+    Qp[e] = (row < n && col < n) ? Q[(size_t)s * n * ld + (size_t)row * ld + col] : T_(0);
+  }
+}
+
 // dots[(s + s_off) * NDOT + q] = sum over the T row blocks of spart[s][q][.]
-// (the same fixed order as the solver's per-matrix reduction).
-__global__ void __launch_bounds__(NT) k_sym_dots(const Inst* __restrict__ insts, const double* __restrict__ spart,
+// (the same row-block order and double-float sums as the solver's control
+// kernel).
+__global__ void __launch_bounds__(NT) k_sym_dots(const Inst* __restrict__ insts, const float2* __restrict__ spart,
                                                 double* __restrict__ dots) {
   const Inst& I = insts[0];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int T = I.tsym;
-  for (int pq = warp; pq < I.M * NDOT; pq += NWARP) {
-    const double* src = spart + (size_t)pq * T;
-    double t = 0.0;
-    for (int rr = lane; rr < T; rr += 32) t += src[rr];
-    t = warp_sum(t);
-    if (lane == 0) {
-      const int ss = pq / NDOT, q = pq - ss * NDOT;
-      dots[(size_t)(ss + I.s_off) * NDOT + q] = t;
-    }
+  for (int pq = threadIdx.x; pq < I.M * NDOT; pq += NT) {
+    const int ss = pq / NDOT, q = pq - ss * NDOT;
+    dots[(size_t)(ss + I.s_off) * NDOT + q] = df_to_double(df_sum_pairs(spart + (size_t)pq * T, T));
   }
 }
 
@@ -133,8 +148,9 @@ __global__ void k_validate(const float* __restrict__ Q, int n, int M, const floa
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(m + 1) * n; e += stride)
     if (!isfinite(c[e])) bad_nan = 1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
-    if (!isfinite(lb[e]) || !isfinite(ub[e])) bad_nan = 1;
-    if (lb[e] > ub[e]) bad_box = 1;
+    // bounds may be infinite (lb = -inf, ub = +inf), not NaN
+    if (isnan(lb[e]) || isnan(ub[e])) bad_nan = 1;
+    if (lb[e] > ub[e] || lb[e] == INFINITY || ub[e] == -INFINITY) bad_box = 1;
     if (q0diag) {
       if (!isfinite(q0diag[e])) bad_nan = 1;
       if (q0diag[e] < 0.0f) bad_diag = 1;
@@ -156,16 +172,29 @@ __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int l
 
 // Start-of-solve state: x^0 into slot 0 (checked against the box), y^0 into
 // slot 0 (checked >= 0), Algorithm 1's initial scalars, deadline.
-__global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ states, int B, double time_limit_s,
-                             int* __restrict__ flags) {
+__global__ void __launch_bounds__(NT) k_init_state(Inst* __restrict__ insts, State* __restrict__ states, int B,
+                                                   double time_limit_s, int* __restrict__ flags) {
+  __shared__ double red[NWARP];
   const int b = blockIdx.x;
   if (b >= B) return;
   const Inst& I = insts[b];
+  double ax[1] = {0.0}, axa[1] = {0.0};
   for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
     const float x = I.xf[0][j];
     I.xb[0][j] = (double)x;
     I.xl[0][j] = 0.0f;
     if (!(x >= I.lb[j] && x <= I.ub[j])) atomicOr(&flags[0], 1);
+    if (I.hyp_a) {
+      ax[0] += (double)I.hyp_a[j] * (double)x;
+      axa[0] += fabs((double)I.hyp_a[j] * (double)x);
+    }
+  }
+  if (I.hyp_a) {
+    // x0 must lie on the hyperplane of X (to the float32 rounding of its data)
+    block_allsum<1>(ax, red);
+    block_allsum<1>(axa, red);
+    if (threadIdx.x == 0 && !(fabs(ax[0] - I.hyp_beta) <= 1e-6 * (1.0 + axa[0] + fabs(I.hyp_beta))))
+      atomicOr(&flags[0], 2);
   }
   for (int i = threadIdx.x; i < I.m; i += blockDim.x)
     if (i < I.m_ineq ? !(I.yb[0][i] >= 0.0) : !(fabs(I.yb[0][i]) < INFINITY)) atomicOr(&flags[1], 1);
@@ -182,8 +211,11 @@ __global__ void k_init_state(Inst* __restrict__ insts, State* __restrict__ state
   restart_scalars(I.P, S);
   S.sigma0 = S.sigma_prev;
   S.phase = PH_INIT;
-  // float32 storage with refinement runs the compensated level from the start
+  // float32 storage with refinement runs the compensated level from the
+  // start; quantised storage with packed tiles its quantised-increment level
   if (I.P.refine && I.storage == RAPDB_F32 && I.Ulo[0]) S.precision = 2;
+  else if (I.P.refine && I.Qpq && I.Ulo[0]) S.precision = 3;
+  S.switch_it = -1;
   S.rel_kkt = S.r_stat = S.r_feas = NAN;
   S.rel_q = INFINITY;
   S.gap_it_done = -1;
@@ -288,9 +320,14 @@ __global__ void __launch_bounds__(NT) k_kkt_plain(const Inst* __restrict__ insts
       gc += y[i - 1] * ((double)U[(size_t)i * I.ldv + j] + (Ulo ? (double)Ulo[(size_t)i * I.ldv + j] : 0.0) +
                         (double)I.c[(size_t)i * I.ldv + j]);
     const double grad = gf + gc;
-    const double lo = I.lb[j], hi = I.ub[j];
-    const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
-    acc[0] = rs * rs;
+    if (I.hyp_a) {   // dist(0, grad + N_X(x)) needs every column: formed in k_kkt_final
+      const dflt gd = df_from_double(grad);
+      I.hg[j] = make_float2(gd.hi, gd.lo);
+    } else {
+      const double lo = I.lb[j], hi = I.ub[j];
+      const double rs = (xj <= lo) ? fmax(-grad, 0.0) : ((xj >= hi) ? fmax(grad, 0.0) : fabs(grad));
+      acc[0] = rs * rs;
+    }
     acc[1] = gf * gf;
     acc[2] = gc * gc;
   }
@@ -299,14 +336,22 @@ __global__ void __launch_bounds__(NT) k_kkt_plain(const Inst* __restrict__ insts
     for (int q = 0; q < 3; ++q) vpart[(size_t)blockIdx.x * 3 + q] = acc[q];
 }
 
-__global__ void k_kkt_final(const Inst* __restrict__ insts, const double* __restrict__ vpart,
-                            const double* __restrict__ dots, const double* __restrict__ y, double* __restrict__ g,
-                            double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+// (one CTA of NT threads; x, xlo: the point as a float pair, for the
+// hyperplane's cone residual)
+__global__ void __launch_bounds__(NT) k_kkt_final(const Inst* __restrict__ insts, const double* __restrict__ vpart,
+                                                  const double* __restrict__ dots, const double* __restrict__ y,
+                                                  double* __restrict__ g, double* __restrict__ out,
+                                                  const float* __restrict__ x, const float* __restrict__ xlo) {
+  __shared__ float2 hsm[NWARP + 2];
+  __shared__ double hsb[2];
   const Inst& I = insts[0];
+  double rs2h = 0.0;
+  if (I.hyp_a) rs2h = hyp_cone_rs2(I, x, xlo, 0.0, nullptr, hsm, hsb);
+  if (threadIdx.x != 0) return;
   double p[3] = {0.0, 0.0, 0.0};
   for (int bq = 0; bq < I.ncb; ++bq)
     for (int q = 0; q < 3; ++q) p[q] += vpart[(size_t)bq * 3 + q];
+  if (I.hyp_a) p[0] = rs2h;
   for (int i = 1; i <= I.m; ++i) g[i - 1] = 0.5 * dots[i * NDOT + D_XU] + dots[i * NDOT + D_CX] + I.dcon[i - 1];
   double rf2 = 0.0, gd2 = 0.0;
   const double tc = I.P.dual_simplex ? simplex_cone_t_serial(g, y, I.m_ineq) : 0.0;

@@ -1,13 +1,15 @@
 """Time the fused coupling pass on a synthetic random QCQP of a chosen size.
 
     python -m paper_2605_29291_gb300.passbench --n 4096 --m 10 [--storage 0|1|2]
-        [--rows-per-block 0|32|64|...] [--variant 0..9] [--reps 3] [--level -1|0|1|2|3|4]
+        [--rows-per-block 0|32|64|...] [--variant 0..9] [--reps 3] [--level -1..7]
         [--pack]
 
 The instance is ``workloads.random_qcqp(n, m, rows=n/2)`` built on the GPU.
 With ``--rows-per-block 0`` the library's autotuner picks the tile; otherwise
 the given rows per CTA and tile variant are used; ``--pack`` builds the
-symmetric block packing (level 4 times the packed incremental pass).  The
+symmetric block packing (level 4 times the packed incremental pass, level 5
+its tile kernel alone; with ``--storage 1|2`` levels 6 and 7 time the same
+over the packed BF16 / FP8 tiles; see rapdb_time_pass).  The
 pass is launched once
 to warm up, then ``--reps`` times between two CUDA events on the context's
 stream; the line printed gives the tile, the time per launch and the

@@ -41,12 +41,18 @@ class CParams(C.Structure):
     ]
 
 
+class CExtras(C.Structure):
+    _fields_ = [("p_eq", C.c_int64), ("A_eq", C.c_void_p), ("b_eq", C.c_void_p), ("x_hyp_a", C.c_void_p),
+                ("x_hyp_beta", C.c_double)]
+
+
 class CInfo(C.Structure):
     _fields_ = [
         ("iters", C.c_int32), ("trials", C.c_int32), ("restarts", C.c_int32), ("precision_switches", C.c_int32),
         ("passes", C.c_int32), ("status", C.c_int32),
         ("rel_kkt", C.c_double), ("r_stat", C.c_double), ("r_feas", C.c_double),
         ("obj", C.c_double), ("seconds", C.c_double), ("launches", C.c_int64),
+        ("switch_iter", C.c_int32), ("reserved_", C.c_int32),
     ]
 
 
@@ -61,6 +67,8 @@ def _load():
         "rapdb_create": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp, P, vp]),
         "rapdb_create_eq": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int64,
                                       vp, vp, P, vp]),
+        "rapdb_create_ex": (C.c_int, [ctxpp, C.c_int64, C.c_int64, C.c_int32, vp, vp, vp, vp, vp, vp,
+                                      C.POINTER(CExtras), P, vp]),
         "rapdb_solve": (C.c_int, [vp, vp, vp, I]),
         "rapdb_kkt_residual": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
@@ -76,6 +84,7 @@ def _load():
         "rapdb_resume": (C.c_int, [vp, vp, vp, I]),
         "rapdb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]),
+        "rapdb_get_instance_tile": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "rapdb_time_pass": (C.c_int, [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "rapdb_get_solution_f64": (C.c_int, [vp, vp, vp]),
         "rapdb_coupling_pass_noalloc": (C.c_int, [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -165,7 +174,7 @@ def _stream_handle(device):
 
 
 def _info_dict(ci: CInfo) -> dict:
-    return {f[0]: getattr(ci, f[0]) for f in CInfo._fields_}
+    return {f[0]: getattr(ci, f[0]) for f in CInfo._fields_ if not f[0].endswith("_")}
 
 
 def _check(st, ctx=None):
@@ -183,20 +192,22 @@ class Solver:
         import torch
         self.params = params or Params.default()
         A_eq, b_eq = getattr(data, "A_eq", None), getattr(data, "b_eq", None)
+        hyp_a = getattr(data, "hyp_a", None)
         self.p_eq = 0 if A_eq is None else int(A_eq.shape[0])
         # m counts the equalities too: the dual vector has m entries, the
         # equality multipliers last
         self.n, self.m = int(data.n), int(data.m) + self.p_eq
-        self._keep = [data.Q, data.c, data.d, data.lb, data.ub, data.q0diag, A_eq, b_eq]
+        self._keep = [data.Q, data.c, data.d, data.lb, data.ub, data.q0diag, A_eq, b_eq, hyp_a]
         for t in self._keep:
             if t is not None:
                 assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
         self.device = data.Q.device
         self.ctx = C.c_void_p()
         cp = self.params.to_c()
-        st = lib.rapdb_create_eq(C.byref(self.ctx), self.n, int(data.m), int(data.q0_kind), _ptr(data.Q),
+        ex = CExtras(self.p_eq, _ptr(A_eq), _ptr(b_eq), _ptr(hyp_a), float(getattr(data, "hyp_beta", 0.0)))
+        st = lib.rapdb_create_ex(C.byref(self.ctx), self.n, int(data.m), int(data.q0_kind), _ptr(data.Q),
                                  _ptr(data.q0diag), _ptr(data.c), _ptr(data.d), _ptr(data.lb), _ptr(data.ub),
-                                 self.p_eq, _ptr(A_eq), _ptr(b_eq), C.byref(cp), _stream_handle(self.device))
+                                 C.byref(ex), C.byref(cp), _stream_handle(self.device))
         _check(st, None)
         self._log = None
 
@@ -378,6 +389,12 @@ class BatchedSolver:
             self.close()
         except Exception:
             pass
+
+    def tile(self, b: int) -> dict:
+        """Instance b's rows per block and the batch's tile variant."""
+        rb, vi = C.c_int32(0), C.c_int32(0)
+        _check(lib.rapdb_get_instance_tile(self.ctx, int(b), C.byref(rb), C.byref(vi)), self.ctx)
+        return {"rows_per_block": rb.value, "variant": vi.value}
 
     def solve(self, xs, ys) -> list:
         infos = (CInfo * self.B)()

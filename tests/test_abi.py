@@ -30,6 +30,17 @@ def test_library_builds_and_exports_every_symbol():
     assert not missing, missing
 
 
+def test_info_and_extras_struct_layouts():
+    """rapdb_info: six int32 counters, five doubles, the int64 launch count,
+    the switch iteration and its padding; rapdb_extras: the equality block,
+    the hyperplane pointer and its constant."""
+    from paper_2605_29291_gb300 import rapdb as R
+    assert ctypes.sizeof(R.CInfo) == 6 * 4 + 5 * 8 + 8 + 2 * 4
+    assert R.CInfo.switch_iter.offset == 6 * 4 + 5 * 8 + 8
+    assert ctypes.sizeof(R.CExtras) == 8 + 3 * 8 + 8
+    assert R.CExtras.x_hyp_beta.offset == 32
+
+
 def test_binding_loads_and_mirrors_defaults():
     from paper_2605_29291_gb300 import rapdb as R
     import json

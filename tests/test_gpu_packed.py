@@ -27,6 +27,7 @@ import pytest
 import torch
 
 import oracle as O
+from oracle import quant as QZ
 from paper_2605_29291_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -54,12 +55,31 @@ def zeros(data, cuda):
             torch.zeros(max(data.m, 1), dtype=torch.float32, device=cuda))
 
 
-def check_packed_pass(R, data, seed, rows=None):
+def stored_rows(data, si, rows, storage):
+    """float64 rows of stored matrix si as the context stores it: the float32
+    data, or its BF16 / Jacobi-scaled FP8 quantisation (the oracle's
+    quantisers)."""
+    dev = data.Q.device
+    idx = torch.as_tensor(rows, device=dev)
+    if storage == 0:
+        return data.Q[si].index_select(0, idx).cpu().numpy().astype(np.float64)
+    Qi = data.Q[si].cpu().numpy()
+    if storage == 1:
+        return QZ.bf16_round(Qi[rows]).astype(np.float64)
+    codes, sc = QZ.fp8_jacobi_quantize(Qi)
+    return QZ.fp8_dequantize(codes, sc)[rows]
+
+
+def check_packed_pass(R, data, seed, rows=None, storage=0):
     """rapdb_packed_pass against float64 products on every (or the sampled)
     row of every stored matrix, under the gamma_23 bound; the dots against
-    float64 sums of the same quantities; a second call bit-identical."""
+    float64 sums of the same quantities; a second call bit-identical.  With
+    BF16 / FP8 storage the pass reads the quantised tiles (the trials of the
+    quantised level) and the products are those of the stored matrices; FP8
+    adds one rounding per term (the pre-scaled s_k v_k) and one for the row
+    scale."""
     dev = data.Q.device
-    s = R.Solver(data, packed(R))
+    s = R.Solver(data, packed(R, storage=storage))
     n, M = data.n, int(data.Q.shape[0])
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
@@ -76,15 +96,15 @@ def check_packed_pass(R, data, seed, rows=None):
     U, Wt, dots = U.cpu().numpy().astype(np.float64), Wt.cpu().numpy().astype(np.float64), dots.cpu().numpy()
     c = data.c.cpu().numpy().astype(np.float64)
     off = 0 if data.q0_kind == W.Q0_DENSE else 1
-    idx = torch.as_tensor(rows, device=dev)
+    gam = G23 if storage != 2 else G23 + 3 * U32
     for si in range(M):
-        Qr = data.Q[si].index_select(0, idx).cpu().numpy().astype(np.float64)   # (k, n)
+        Qr = stored_rows(data, si, rows, storage)   # (k, n)
         w_ex = Qr @ v64
         aw = np.abs(Qr) @ np.abs(v64)
         u_ex = uo[si, rows] + w_ex
         # error of the unrounded w: partials + compensated slot sum (the
         # O(T^2 u^2) term and the float64 roundings are inside the 1e-3 slack)
-        ew = (G23 * aw + 2 * U32 * np.abs(w_ex)) * 1.001
+        ew = (gam * aw + 2 * U32 * np.abs(w_ex)) * 1.001
         assert np.all(np.abs(Wt[si, rows] - w_ex) <= ew + U32 * np.abs(w_ex) * 1.001 + 1e-30), si
         assert np.all(np.abs(U[si, rows] - u_ex) <= ew + U32 * np.abs(u_ex) * 1.001 + 1e-30), si
         if len(rows) == n:
@@ -112,6 +132,20 @@ def test_packed_pass_diag_q0(R, cuda):
     data = W.kml_qcqp(120, 5, 8, seed=2).to(cuda)
     assert data.q0_kind == W.Q0_DIAG
     check_packed_pass(R, data, seed=3)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("n,m", [(128, 2), (129, 3), (200, 10), (1000, 6)])
+def test_quantised_packed_pass_matches_float64(R, cuda, storage, n, m):
+    """The BF16 / FP8 tiles: products of the stored (quantised) matrices."""
+    data = W.random_qcqp(n, m, seed=n + 3 * m).to(cuda)
+    check_packed_pass(R, data, seed=n + 1, storage=storage)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_quantised_packed_pass_diag_q0(R, cuda, storage):
+    data = W.kml_qcqp(120, 5, 8, seed=2).to(cuda)
+    check_packed_pass(R, data, seed=4, storage=storage)
 
 
 @pytest.mark.parametrize("variant", [0, 1])
@@ -251,33 +285,24 @@ def test_simplex_dual_with_equality_and_diag_q0(R, cuda):
     assert rel <= 1.1e-6, rel
 
 
-def test_bf16_storage_packs_the_float32_copy(R, cuda):
-    """BF16 storage with refinement: stored-precision trials first, then (after
-    the precision switch) packed float32 trials; ends at rel KKT 1e-6 of the
-    float32 problem by the oracle's residual."""
-    data = W.kml_qcqp(200, 6, 8, seed=4)
-    p = packed(R, storage=1, refine=1, tol=1e-6, restart_period=100)
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("case", ["kml", "random"])
+def test_quantised_level_solve_meets_tolerance(R, cuda, storage, case):
+    """BF16 / FP8 storage with refinement and packing: the trials add the
+    increments Q~ d of the quantised tiles to float32 compensated products,
+    re-anchored at the check every 64 accepted iterations; a stall there
+    switches to the float32 tiles.  The solve ends at rel KKT 1e-6 of the
+    float32 problem by the oracle's float64 residual, whether or not it
+    switched (switch_iter says when it did)."""
+    data = W.kml_qcqp(200, 6, 8, seed=4 + storage) if case == "kml" else W.random_qcqp(300, 8, seed=7)
+    p = packed(R, storage=storage, refine=1, tol=1e-6, restart_period=100, max_iter=20000)
     s = R.Solver(data.to(cuda), p)
     x, y = zeros(data, cuda)
     info = s.solve(x, y)
     x64, y64 = s.solution_f64()
     s.close()
-    assert info["status"] == R.OK and info["precision_switches"] >= 1, info
-    rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
-    assert rel <= 1.1e-6, rel
-
-
-def test_fp8_storage_packs_the_float32_copy(R, cuda):
-    """FP8 (Jacobi-scaled E4M3) storage with refinement and packing: the
-    stored-precision trials, then packed float32 trials after the switch."""
-    data = W.kml_qcqp(200, 6, 8, seed=5)
-    p = packed(R, storage=2, refine=1, tol=1e-6, restart_period=100)
-    s = R.Solver(data.to(cuda), p)
-    x, y = zeros(data, cuda)
-    info = s.solve(x, y)
-    x64, y64 = s.solution_f64()
-    s.close()
-    assert info["status"] == R.OK and info["precision_switches"] >= 1, info
+    assert info["status"] == R.OK, info
+    assert (info["switch_iter"] >= 0) == (info["precision_switches"] >= 1), info
     rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
     assert rel <= 1.1e-6, rel
 
@@ -285,9 +310,9 @@ def test_fp8_storage_packs_the_float32_copy(R, cuda):
 @pytest.mark.parametrize("storage", [1, 2])
 def test_quantised_storage_adaptive_restart_packed_gap(R, cuda, storage):
     """BF16 / FP8 storage with refinement, adaptive restart and packing: the
-    smoothed gap's passes read the stored matrices before the precision
-    switch and the packed float32 tiles after it; the solve ends at rel KKT
-    1e-6 by the oracle's float64 residual."""
+    smoothed gap's passes read the packed float32 tiles, the trials the
+    quantised ones; the solve ends at rel KKT 1e-6 by the oracle's float64
+    residual."""
     data = W.kml_qcqp(200, 6, 8, seed=4)
     p = packed(R, storage=storage, refine=1, tol=1e-6, restart=R.RESTART_GAP, gap_first=20, gap_every=20,
                restart_period=100, max_iter=20000)
@@ -296,7 +321,7 @@ def test_quantised_storage_adaptive_restart_packed_gap(R, cuda, storage):
     info = s.solve(x, y)
     x64, y64 = s.solution_f64()
     s.close()
-    assert info["status"] == R.OK and info["precision_switches"] >= 1, info
+    assert info["status"] == R.OK, info
     assert info["passes"] > info["trials"] + 20, info          # gap passes ran
     rel, _, _ = O.kkt_residual(O.Problem.from_data(data), x64.cpu().numpy(), y64.cpu().numpy())
     assert rel <= 1.1e-6, rel
@@ -322,11 +347,21 @@ def test_time_pass_level_4(R, cuda):
     ms3, b3 = s.time_pass(reps=3, level=3)
     assert b3 == 5 * 300 * 300 * 4
     s.close()
+    with pytest.raises(R.RapdbError):
+        s.time_pass(reps=1, level=6)      # a float32 context has no quantised tiles
+    s.close()
     s = R.Solver(data, R.Params.default())
     for lv in (4, 5):
         with pytest.raises(R.RapdbError):
             s.time_pass(reps=1, level=lv)
     s.close()
+    for storage, eb in ((1, 2), (2, 1)):
+        s = R.Solver(data, packed(R, storage=storage))
+        ms6, b6 = s.time_pass(reps=3, level=6)
+        ms7, b7 = s.time_pass(reps=3, level=7)
+        q = 5 * T * (T + 1) // 2 * 128 * 128 * eb + (5 * 300 * 4 if storage == 2 else 0)
+        assert ms6 > 0 and ms7 > 0 and b6 == q and b7 == q
+        s.close()
 
 
 # ---------------------------------------------------------------------------
@@ -341,10 +376,11 @@ def c2(cuda):
     torch.cuda.empty_cache()
 
 
-def test_dense_4096x50_packed_pass_sampled_rows(R, c2):
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_dense_4096x50_packed_pass_sampled_rows(R, c2, storage):
     rng = np.random.default_rng(5)
     rows = np.sort(np.concatenate([[0, 127, 128, c2.n - 1], rng.choice(np.arange(129, c2.n - 1), 36, False)]))
-    check_packed_pass(R, c2, seed=5, rows=rows)
+    check_packed_pass(R, c2, seed=5, rows=rows, storage=storage)
 
 
 def test_dense_4096x50_packed_solve_meets_tolerance(R, cuda, c2):

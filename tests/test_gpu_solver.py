@@ -273,12 +273,19 @@ def test_batched_matches_single(R, cuda):
     xs = [torch.zeros(d.n, device=cuda) for d in datas]
     ys = [torch.zeros(max(d.m, 1), device=cuda) for d in datas]
     infos = bs.solve(xs, ys)
-    # a single-instance context with the batched context's tile (64 rows, the
-    # pipelined register-streaming variant) performs the same floating-point
-    # operations
-    p1 = R.Params.default(tol=1e-6, rows_per_block=64, pass_variant=6)
-    for d, dv, xb, yb, ib in zip(datas, devs, xs, ys, infos):
+    # the autotuner's tiles: one variant for the batch, rows per block per size class
+    tiles = [bs.tile(b) for b in range(len(datas))]
+    assert len({t["variant"] for t in tiles}) == 1
+    assert all(t["rows_per_block"] in (32, 64, 128) for t in tiles)
+    by_class = {}
+    for d, t in zip(datas, tiles):
+        by_class.setdefault(int(np.ceil(np.log2(d.n))), set()).add(t["rows_per_block"])
+    assert all(len(v) == 1 for v in by_class.values())
+    # a single-instance context with the instance's tile performs the same
+    # floating-point operations
+    for d, dv, xb, yb, ib, t in zip(datas, devs, xs, ys, infos, tiles):
         assert ib["status"] == R.OK and ib["rel_kkt"] <= 1e-6
+        p1 = R.Params.default(tol=1e-6, rows_per_block=t["rows_per_block"], pass_variant=t["variant"])
         s = R.Solver(dv, p1)
         x, y = gpu_vecs(d, cuda)
         i1 = s.solve(x, y)
