@@ -99,8 +99,11 @@ typedef struct {
                               /*    are U^k + Q~ d, the increment Q~ d read from the  */
                               /*    packed BF16/FP8 tiles and U^k a compensated       */
                               /*    float32 product re-formed (anchored) by the       */
-                              /*    precision check every 64 accepted iterations; a   */
-                              /*    stall there switches to the float32 tiles        */
+                              /*    precision check every 64 accepted iterations; it  */
+                              /*    switches to the float32 tiles when the level's    */
+                              /*    own residual reaches tol while the true one does  */
+                              /*    not, or when the true residual did not fall at    */
+                              /*    two checks in a row                               */
   double stall_ratio;         /* stall: the true rel KKT fell by less than this factor */
                               /*    since the previous precision check               */
   int32_t max_iter, max_trials, kkt_every;

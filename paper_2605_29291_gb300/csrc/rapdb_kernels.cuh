@@ -887,11 +887,22 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
           dec = 2;
         } else {
           const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
+          S.stall_count = (S.kkt_ref > 0.0 && rel >= S.kkt_ref) ? S.stall_count + 1 : 0;
           S.kkt_ref = rel;
-          // switch when the true residual stalls, when the stored matrices'
-          // problem is solved, or when the storage error already dominates
-          // (the true residual is more than twice the stored level's)
-          if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) dec = 1;
+          if (S.precision == 3) {
+            // the quantised-increment level: every check re-anchors U, so the
+            // storage error cannot build up beyond ANCHOR_EVERY iterations and
+            // shrinks with the steps. Checks come every ANCHOR_EVERY
+            // iterations, too often for the halving test: switch when the
+            // true residual did not fall at all, twice in a row, or when the
+            // drifted products claim convergence that the check denies
+            if (S.stall_count >= 2 || S.rel_q <= P.tol) dec = 1;
+          } else if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) {
+            // switch when the true residual stalls, when the stored matrices'
+            // problem is solved, or when the storage error already dominates
+            // (the true residual is more than twice the stored level's)
+            dec = 1;
+          }
         }
         s_dec = dec;
       }
