@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "librapdb.so")
 # (RAPDB_CHECKED) and report a failed check instead of touching memory
 LIB_CHECKED = os.path.join(HERE, "librapdb_checked.so")
 SOURCES = ["rapdb.cu", "kern_f32.cu", "kern_bf16.cu", "kern_fp8.cu", "rapdb_noalloc.cu", "rapdb_selftest.cu"]
-DEPS = SOURCES + ["rapdb_device.cuh", "rapdb_kernels.cuh", "rapdb_sym.cuh", "rapdb_util.cuh", "rapdb_launch.h",
+DEPS = SOURCES + ["rapdb_device.cuh", "rapdb_kernels.cuh", "rapdb_sym.cuh", "rapdb_tc.cuh", "rapdb_util.cuh", "rapdb_launch.h",
                   "kern_impl.cuh"]
 BUILD_DIR = os.path.join(HERE, "_build")
 BUILD_DIR_CHECKED = os.path.join(HERE, "_build_checked")

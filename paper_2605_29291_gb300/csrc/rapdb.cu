@@ -142,6 +142,11 @@ void launch_sym_finish(int storage, dim3 g, cudaStream_t s, const Inst* I, State
   else if (storage == RAPDB_FP8) k_sym_finish<RAPDB_FP8><<<g, NT, 0, s>>>(I, S, C);
   else k_sym_finish<RAPDB_F32><<<g, NT, 0, s>>>(I, S, C);
 }
+// The pieces of v for the quantised tiles (before launch_sym_plain with quant).
+void launch_sym_pieces(int storage, cudaStream_t s, const Inst* I, const float* v) {
+  if (storage == RAPDB_BF16) k_sym_pieces<RAPDB_BF16><<<128, NT, 0, s>>>(I, v);
+  else if (storage == RAPDB_FP8) k_sym_pieces<RAPDB_FP8><<<128, NT, 0, s>>>(I, v);
+}
 void launch_sym_plain(int storage, dim3 g, cudaStream_t s, const Inst* I, const float* v, int quant, int* err) {
   if (storage == RAPDB_BF16) k_sym_plain<RAPDB_BF16><<<g, NTS, sym_smem_bytes(), s>>>(I, v, quant, err);
   else if (storage == RAPDB_FP8) k_sym_plain<RAPDB_FP8><<<g, NTS, sym_smem_bytes(), s>>>(I, v, quant, err);
@@ -521,6 +526,11 @@ rapdb_status build_instance(rapdb_ctx* ctx, InstHost& H, int64_t n64, int64_t m6
       CK(cudaGetLastError());
       I.Qpq = qq;
       H.qpq_bytes = (int64_t)M * ntile * STB * STB * EB + (EB == 1 ? (int64_t)M * n * 4 : 0);
+      // the pieces of the trial right-hand side, one 2 KB (BF16) / 1 KB (FP8)
+      // block per 128 entries; the rows past the pieces stay zero
+      const size_t pqb = (size_t)(EB == 1 ? M : 1) * T * sym_piece_bytes(EB);
+      AL(I.Pq, pqb);
+      CK(cudaMemsetAsync(I.Pq, 0, pqb, st));
     }
   }
   I.P = make_devparams(p, ctx);
@@ -1338,6 +1348,7 @@ rapdb_status rapdb_packed_pass(rapdb_ctx* ctx, const float* x, const float* v, c
   if (fp8)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, xpad, vpad, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS,
                                       ctx->tvpart, 0);
+  if (quant) launch_sym_pieces(ctx->storage, st, ctx->d_inst, fp8 ? ctx->VS : vpad);
   launch_sym_plain(ctx->storage, dim3(ctx->sym_tile_grid), st, ctx->d_inst, fp8 ? ctx->VS : vpad, quant,
                    &ctx->d_ctrl->err);
   k_sym_rows_plain<0><<<I.M * I.tsym, NT, 0, st>>>(ctx->d_inst, xpad, nullptr, vpad, ctx->tUo, nullptr, ctx->tU,
@@ -1420,9 +1431,13 @@ rapdb_status rapdb_time_pass(rapdb_ctx* ctx, int32_t reps, int32_t level, double
   if (fp8s)
     k_vec_plain<<<I.ncb, NT, 0, st>>>(ctx->d_inst, x, v, nullptr, ctx->tU, ctx->tW, ctx->XS, ctx->VS, ctx->tvpart, 0);
   const int grid = I.M * I.nrb;
+  // level 6 times the quantised tile kernel alone (its right-hand-side pieces
+  // formed once, here); level 7 the whole pass, pieces included
+  if (lv == 6) launch_sym_pieces(ctx->storage, st, ctx->d_inst, fp8s ? ctx->VS : v);
   auto launch = [&]() {
     if (lv >= 4) {
       const int quant = lv >= 6 ? 1 : 0;
+      if (lv == 7) launch_sym_pieces(ctx->storage, st, ctx->d_inst, fp8s ? ctx->VS : v);
       launch_sym_plain(ctx->storage, dim3(ctx->sym_tile_grid), st, ctx->d_inst, (quant && fp8s) ? ctx->VS : v,
                        quant, &ctx->d_ctrl->err);
       if (lv == 4 || lv == 7)

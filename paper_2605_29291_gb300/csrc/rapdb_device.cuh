@@ -136,7 +136,10 @@ struct Inst {
   float* sp;            // (2, M, T, T * STB) tile products: slot J of the rows of block I,
                         // one set per right-hand side
   const void* Qpq;      // (M, ntile, STB, STB) BF16 / FP8 codes of the stored matrices in the same
-                        // tiles (quantised contexts with packing), read by the quantised level's trials
+                        // tiles (quantised contexts with packing, core-matrix layout), read by the
+                        // quantised level's trials on the tensor cores
+  uint8_t* Pq;          // (1 or M, T) blocks of the right-hand side's pieces, the B operands of those
+                        // tile products (BF16: one set for d; FP8: one per stored matrix, s_s .* d)
   float2* spart;        // (M, NDOT, T) row-block dot partials of the packed pass (double-float pairs)
   int tsym, ntile;      // T = ceil(n / STB) (0: no packing), T (T + 1) / 2
   double* vpart;        // (ncb, NVP) vector partials
@@ -858,6 +861,9 @@ __device__ __forceinline__ void bulk_g2s_evict_first(void* dst, const void* src,
           "r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

@@ -25,6 +25,8 @@
 // over quantised matrices keep the row-streaming tile.
 #pragma once
 
+#include "rapdb_tc.cuh"
+
 namespace rapdb_dev {
 
 constexpr int STB = 128;             // tile edge (rows of a row block)
@@ -204,20 +206,28 @@ static __device__ void sym_rows2(const Inst& I, const float* __restrict__ Px, co
 // global fences: the row-block reduction runs in the next kernel.  Every wait
 // is bounded; on a timeout the CTA sets *err, waits (bounded) for its copies
 // in flight and returns.
-// `dsm` = [stage mbarriers (128 B) | 2 x NWS x STB floats | 192 KB of stages].
+// `dsm` = [stage mbarriers (128 B) | 2 x NWS x STB floats | 192 KB of stages]
+// (within sym_smem_bytes(), which the tensor-core path lays out its own way).
 constexpr int NTS = 512;
 constexpr int NWS = NTS / 32;
 constexpr int SRW8 = STB / NWS;      // tile rows per warp (8)
 static_assert(SRW8 == 8, "warp_rows8 reduces 8 rows per warp");
 constexpr int SNST = 3;                          // float32 stages of 64 KB
 constexpr uint32_t STILE = (uint32_t)STB * STB * 4;
+// (the tensor-core tile path lays out the same bytes as [barriers 256 B |
+// pieces ring 24 KB | stages | zero block 2 KB | metadata 256 B])
 __host__ __device__ constexpr size_t sym_smem_bytes() {
-  return (size_t)128 + (size_t)2 * NWS * STB * 4 + (size_t)SNST * STILE;
+  return (size_t)256 + 24576 + (size_t)SNST * STILE + 2048 + 256;
 }
+static_assert(2 * NWS * STB * 4 <= 24576, "the float32 path's column sums fit before the stages");
+// Bytes of one block of right-hand-side pieces (128 entries, eb-byte type).
+__host__ __device__ constexpr uint32_t sym_piece_bytes(int eb) { return (uint32_t)(STB * eb / 16) * 128; }
 
-// Stored tile elements: a thread reads 4 consecutive entries of each of its
-// 8 rows (16, 8 or 4 bytes) and decodes them to float32.  The quantised
-// tiles use the same 192 KB of stages: more, smaller stages in flight.
+// Stored tile elements.  Float32 tiles are row-major; a thread of the
+// CUDA-core tile loop reads 4 consecutive entries of each of its 8 rows (16
+// bytes) and decodes them to float32.  The quantised tiles (BF16 / FP8 codes,
+// read by the tensor cores) are in the core-matrix layout of rapdb_tc.cuh and
+// use the same 192 KB of stages: more, smaller stages in flight.
 template <int ST> struct TileElt;
 template <> struct TileElt<RAPDB_F32> {
   using raw = uint4;
@@ -227,25 +237,8 @@ template <> struct TileElt<RAPDB_F32> {
     o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
   }
 };
-template <> struct TileElt<RAPDB_BF16> {
-  using raw = uint2;
-  static constexpr int B = 2;
-  __device__ __forceinline__ static void dec(const raw& r, float (&o)[4]) {
-    o[0] = __uint_as_float(r.x << 16); o[1] = __uint_as_float(r.x & 0xffff0000u);
-    o[2] = __uint_as_float(r.y << 16); o[3] = __uint_as_float(r.y & 0xffff0000u);
-  }
-};
-template <> struct TileElt<RAPDB_FP8> {
-  using raw = uint32_t;
-  static constexpr int B = 1;
-  __device__ __forceinline__ static void dec(const raw& r, float (&o)[4]) {
-    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r & 0xffffu), __NV_E4M3);
-    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r >> 16), __NV_E4M3);
-    const float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
-    const float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-  }
-};
+template <> struct TileElt<RAPDB_BF16> { static constexpr int B = 2; };
+template <> struct TileElt<RAPDB_FP8> { static constexpr int B = 1; };
 template <int ST>
 __host__ __device__ constexpr uint32_t sym_tile_bytes() { return (uint32_t)STB * STB * TileElt<ST>::B; }
 template <int ST>
@@ -460,163 +453,379 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
   }
 }
 
-// The quantised tiles (BF16 / FP8, one right-hand side) two at a time: a
-// 16- or 32-KB tile takes as much arithmetic as a 64-KB float32 one, and one
-// tile per loop iteration leaves the CTA waiting on its own barriers and
-// shuffle chains (latency-bound at about half the copy bandwidth).  Each
-// warp takes its 8 rows of tiles k and k + 1 together (independent
-// instruction streams), with one pair of barriers per two tiles; the column
-// partials of the two tiles go to the two halves of sred and are summed by
-// the two halves of the CTA.  Same arithmetic per tile as sym_tiles<1, ST>.
+// The quantised tiles (BF16 / FP8 codes, one right-hand side) on the
+// tensor cores.  On the CUDA cores a quantised tile costs as much
+// arithmetic as a float32 one (decode, then two FMAs per entry, plus the
+// shuffle and shared-memory reductions) in a half or a quarter of the bytes:
+// measured, that kernel was issue-bound at about 4 TB/s of BF16 and 2 TB/s of
+// FP8 tiles.  Here each tile is two small MMAs of the fifth-generation tensor
+// cores, operands in shared memory, accumulators in tensor memory (TMEM):
+//   row product    D_r (128 x 16) = B  P_J   (B = the tile, read K-major),
+//   column product D_c (128 x 16) = B' P_I   (the same tile, read MN-major),
+// the quantised tiles being stored in the core-matrix layout (8 rows x 16
+// bytes per 128-byte core, cores row-major over the tile), which both
+// readings accept.  P_J holds the right-hand side's slice d_J split into
+// pieces of the tile's own type, one piece per column of the N = 16 operand,
+// so that the products of the pieces are exact and only the float32
+// accumulation rounds:
+//   BF16: d = h + m + l, three bf16 pieces (exact: 3 x 8 significant bits);
+//   FP8:  sigma d = sum_j q_j 16^-j, six e4m3 pieces, sigma a power of two per
+//         128-entry slice (|sigma d| < 256), each residual scaled by 16 before
+//         it is rounded (no e4m3 underflow); the pieces hold sigma d to about
+//         2^-24 of itself.
+// The pieces are formed once per pass (sym_pieces, in the kernel that runs
+// before the tile kernel) into blocks of one 128-entry slice each; each
+// tile's stage receives its tile and the blocks of slices J and I by bulk
+// copy on one mbarrier.  Operand rows 8-15 are an all-zero block in shared
+// memory (the descriptors' SBO points there).  The epilogue adds the pieces'
+// columns (Horner in 1/16, then 1/sigma, for FP8) and writes the tile's row
+// and column partials to their slots, as the float32 tile kernel does.
+//
+// Warp roles (NTS = 512 threads), linked by mbarriers, no CTA barrier per
+// tile:
+//   producer (warp 9; its elected lane issues): waits until the MMAs of the
+//     stage's previous tile are done (empty), then copies tile k and its
+//     pieces blocks (full);
+//   MMA issuer (warp 8; its elected lane issues): waits for the stage (full)
+//     and for the accumulator pair of tile k - TC_NACC to be read out
+//     (accempty), issues the row and column MMAs, then commits them to empty
+//     (the stage is free) and to accfull;
+//   epilogue (warps 0-7): waits for accfull, reads its accumulators (warps
+//     0-3 the row products, TMEM lanes 32 w ..; warps 4-7 the column
+//     products), arrives on accempty, adds the pieces' columns and stores.
+// Each role derives the tile coordinates it needs from k (the issuer reads
+// the producer's, published by the full barrier's arrival); the epilogue
+// reads FP8's 1 / sigma from the pieces blocks in global memory.
+// TMEM: 128 columns, four tiles of [row 16 | column 16] in flight between
+// the issuer and the epilogue.  Every wait is bounded and also gives up when
+// another role has failed; on a failure the CTA sets *err, drains its copies
+// and MMAs in flight (bounded), frees its TMEM and returns.
+constexpr int TC_MMA = 8 * 32;              // warp 8 (lane 0 issues)
+constexpr int TC_PROD = 9 * 32;             // warp 9
+constexpr int TC_NACC = 4;                  // accumulator pairs
+constexpr int TC_NCOL = 32 * TC_NACC;
+struct TcMeta {
+  uint32_t tmem;
+  int fail;                    // a role's wait gave up
+  int issued;                  // tiles whose copies the producer issued
+  int ti[16], tj[16];          // tile k's coordinates in slot k % 16 (written before its copies)
+};
+// tensor-core layout: [barriers 256 B | pieces ring | stages | zero block | metadata]
+constexpr size_t TC_BARS = 256;
+constexpr size_t TC_PRING = 24576;
+constexpr size_t TC_ZERO = 2048;
+static_assert(sizeof(TcMeta) <= 256, "tile metadata fits the tail of the shared-memory layout");
+static_assert(TC_BARS + TC_PRING + (size_t)SNST * STILE + TC_ZERO + 256 == sym_smem_bytes(), "shared layout");
+
+// A bounded wait that also gives up once *fail is set.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err, const int* fail) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*reinterpret_cast<const volatile int*>(fail)) return false;
+      if (globaltimer() - t0 > 2000000000ull) {
+        if (err) atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+// Pieces of one 128-entry slice e (lane l holds entries 4l .. 4l+3) into the
+// block P: core kc (128 bytes) holds entries kc CE .. kc CE + CE - 1, row j
+// of the core their piece j.  FP8 also stores 1 / sigma in row 7 of core 0
+// (operand row 7 meets D column 7, which nothing reads).
 template <int ST>
-__device__ __forceinline__ void sym_tiles_q(const Inst& I, const float* __restrict__ r0, size_t rstride,
-                                            uint8_t* dsm, int* err) {
-  using TE = TileElt<ST>;
+__device__ __forceinline__ void sym_piece_block(float4 e, uint8_t* __restrict__ P) {
+  const int lane = threadIdx.x & 31;
+  float a0 = e.x, a1 = e.y, a2 = e.z, a3 = e.w;
+  if constexpr (ST == RAPDB_BF16) {
+    uint8_t* p = P + (lane >> 1) * 128 + (lane & 1) * 8;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(a0, a1);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(a2, a3);
+      *reinterpret_cast<uint2*>(p + j * 16) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+      // exact: the residual of a rounding to 8 significant bits
+      a0 -= __low2float(lo);
+      a1 -= __high2float(lo);
+      a2 -= __low2float(hi);
+      a3 -= __high2float(hi);
+    }
+  } else {
+    float mx = fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(a3)));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int ex = 0;
+    (void)frexpf(mx, &ex);                                    // mx < 2^ex
+    ex = max(-100, min(ex, 100));
+    const float sig = __int_as_float((127 + 8 - ex) << 23);  // 2^(8 - ex): |sigma e| < 256
+    a0 *= sig;
+    a1 *= sig;
+    a2 *= sig;
+    a3 *= sig;
+    uint8_t* p = P + (lane >> 2) * 128 + (lane & 3) * 4;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a0, a1), __NV_SATFINITE, __NV_E4M3);
+      const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(a2, a3), __NV_SATFINITE, __NV_E4M3);
+      *reinterpret_cast<uint32_t*>(p + j * 16) = (uint32_t)lo | ((uint32_t)hi << 16);
+      __half2_raw hl = __nv_cvt_fp8x2_to_halfraw2(lo, __NV_E4M3);
+      __half2_raw hh = __nv_cvt_fp8x2_to_halfraw2(hi, __NV_E4M3);
+      const float2 ql = __half22float2(*reinterpret_cast<__half2*>(&hl));
+      const float2 qh = __half22float2(*reinterpret_cast<__half2*>(&hh));
+      // exact: the e4m3 value is a multiple of the residual's float32 ulp
+      a0 = (a0 - ql.x) * 16.0f;
+      a1 = (a1 - ql.y) * 16.0f;
+      a2 = (a2 - qh.x) * 16.0f;
+      a3 = (a3 - qh.y) * 16.0f;
+    }
+    if (lane == 0) *reinterpret_cast<float*>(P + 7 * 16) = __int_as_float((127 - 8 + ex) << 23);   // 1 / sigma
+  }
+}
+
+// All piece blocks of a pass's right-hand side, one warp per block: BF16 the
+// T slices of r, FP8 the M x T slices of r + s rstride (s_s .* d).
+template <int ST>
+__device__ __forceinline__ void sym_pieces(const Inst& I, const float* __restrict__ r, size_t rstride) {
+  constexpr uint32_t PB = sym_piece_bytes(TileElt<ST>::B);
+  const int T = I.tsym, n = I.n;
+  const int nb = (ST == RAPDB_FP8 ? I.M : 1) * T;
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int q = blockIdx.x * nw + (threadIdx.x >> 5); q < nb; q += gridDim.x * nw) {
+    const int s = q / T, b = q - s * T;
+    const float* v = r + (size_t)s * rstride;
+    const int c0 = b * STB + lane * 4;
+    float4 e;
+    if (c0 + 4 <= n) {
+      e = __ldg(reinterpret_cast<const float4*>(v + c0));
+    } else {
+      e.x = (c0 < n) ? __ldg(v + c0) : 0.f;
+      e.y = (c0 + 1 < n) ? __ldg(v + c0 + 1) : 0.f;
+      e.z = (c0 + 2 < n) ? __ldg(v + c0 + 2) : 0.f;
+      e.w = (c0 + 3 < n) ? __ldg(v + c0 + 3) : 0.f;
+    }
+    sym_piece_block<ST>(e, I.Pq + (size_t)q * PB);
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* err) {
+  constexpr bool F8 = (ST == RAPDB_FP8);
   constexpr uint32_t TB = sym_tile_bytes<ST>();
+  constexpr uint32_t PB = sym_piece_bytes(TileElt<ST>::B);
   constexpr int NSG = sym_stages<ST>();
-  static_assert(NSG % 2 == 0, "pairs of stages");
+  static_assert(NSG * 2 * PB <= TC_PRING && NSG <= 12 && PB <= TC_ZERO, "tensor-core stage layout");
+  constexpr uint32_t NC = STB * TileElt<ST>::B / 16;     // cores per core row of a tile
+  constexpr int KSTEPS = F8 ? 4 : 8;                     // MMAs per product (K = 32 / 16 each)
+  constexpr uint32_t IDR = umma_idesc(F8, false, STB, 16), IDC = umma_idesc(F8, true, STB, 16);
   const uint8_t* Qt = reinterpret_cast<const uint8_t*>(I.Qpq);
-  const int T = I.tsym, nt = I.ntile, M = I.M, n = I.n;
+  const uint8_t* Pq = I.Pq;
+  const int T = I.tsym, nt = I.ntile;
   float* const sp = I.sp;
   const size_t ldp = (size_t)T * STB;
-  const int total = M * nt;
+  const int total = I.M * nt;
   const int first = blockIdx.x, G = gridDim.x;
   if (first >= total) return;
   const int K = (total - first + G - 1) / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
-  float* sred = reinterpret_cast<float*>(dsm + 128);
-  uint8_t* stg = dsm + 128 + (size_t)2 * NWS * STB * 4;
-  if (tid == 0) {
-    for (int k = 0; k < NSG; ++k) mbar_init(&full[k], 1);
-    fence_proxy_async();
-  }
-  __syncthreads();
-  const uint64_t pol = l2_policy_evict_first();
-  auto issue = [&](int k) {
-    const int st = k % NSG;
-    const size_t it = (size_t)first + (size_t)k * G;
-    mbar_expect_tx(&full[st], TB);
-    bulk_g2s_evict_first(stg + (size_t)st * TB, Qt + it * TB, TB, &full[st], pol);
-  };
-  if (tid == 0)
-    for (int k = 0; k < NSG && k < K; ++k) issue(k);
-  auto coords = [&](int k, int& s, int& TI, int& TJ) {
-    const int it = first + k * G;
-    s = it / nt;
-    sym_tile_coords(it - s * nt, T, TI, TJ);
-  };
-  auto slices = [&](int k, int& s, int& TI, int& TJ, float (&dj)[4], float& dil) {
-    if (k < K) {
-      coords(k, s, TI, TJ);
-      sym_dslices(r0 + (size_t)s * rstride, n, TI, TJ, dj, dil);
-    } else {
-      s = 0; TI = 0; TJ = 0; dil = 0.f;
-      dj[0] = dj[1] = dj[2] = dj[3] = 0.f;
-    }
-  };
-  // slices of the current pair (a: k, b: k + 1) and the next (k + 2, k + 3)
-  int sa, ia, ja, sb, ib, jb, nsa, nia, nja, nsb, nib, njb;
-  float dja[4], dila, djb[4], dilb, nja4[4], nila, njb4[4], nilb;
-  slices(0, sa, ia, ja, dja, dila);
-  slices(1, sb, ib, jb, djb, dilb);
-  slices(2, nsa, nia, nja, nja4, nila);
-  slices(3, nsb, nib, njb, njb4, nilb);
-  for (int k = 0; k < K; k += 2) {
-    const bool hb = k + 1 < K;
-    const int sta = k % NSG, stb = (k + 1) % NSG;
-    bool got = mbar_wait_bounded(&full[sta], (uint32_t)((k / NSG) & 1), err);
-    if (hb) got = got && mbar_wait_bounded(&full[stb], (uint32_t)(((k + 1) / NSG) & 1), err);
-    if (!__syncthreads_and(got)) {
-      if (tid == 0)
-        for (int k2 = k; k2 < K && k2 < k + NSG; ++k2)
-          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
-      __syncthreads();
-      return;
-    }
 #ifdef RAPDB_CHECKED
-    if (!__syncthreads_and(ia >= 0 && ia <= ja && ja < T && (!hb || (ib >= 0 && ib <= jb && jb < T)))) {
-      if (tid == 0) {
-        if (err) atomicCAS(err, 0, CHK_SYM_RANGE);
-        for (int k2 = k + 2; k2 < K && k2 < k + NSG; ++k2)
-          mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
-      }
-      __syncthreads();
+  {
+    bool bad = false;
+    for (int k = 0; k < K && !bad; ++k) {
+      const int it = first + k * G, s = it / nt;
+      int TI, TJ;
+      sym_tile_coords(it - s * nt, T, TI, TJ);
+      bad = TI < 0 || TI > TJ || TJ >= T || s >= I.M;
+    }
+    if (bad) {
+      if (tid == 0 && err) atomicCAS(err, 0, CHK_SYM_RANGE);
       return;
     }
+  }
 #endif
-    float rpa[SRW8], rpb[SRW8], cpa[4] = {0.f, 0.f, 0.f, 0.f}, cpb[4] = {0.f, 0.f, 0.f, 0.f};
-    {
-      const size_t off = ((size_t)warp * SRW8 * STB + lane * 4) * TE::B;
-      const uint8_t* pa = stg + (size_t)sta * TB + off;
-      const uint8_t* pb = stg + (size_t)stb * TB + off;
-      typename TE::raw ra[SRW8], rb_[SRW8];
-#pragma unroll
-      for (int q = 0; q < SRW8; ++q) {
-        ra[q] = *reinterpret_cast<const typename TE::raw*>(pa + (size_t)q * STB * TE::B);
-        rb_[q] = hb ? *reinterpret_cast<const typename TE::raw*>(pb + (size_t)q * STB * TE::B) : ra[q];
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);     // [12]
+  uint64_t* empty = full + 12;                           // [12]
+  uint64_t* accfull = full + 24;                         // [TC_NACC]
+  uint64_t* accempty = full + 24 + TC_NACC;              // [TC_NACC]
+  static_assert((24 + 2 * TC_NACC) * 8 <= TC_BARS, "barriers fit their area");
+  uint8_t* pring = dsm + TC_BARS;                        // stage st: [P_J | P_I]
+  uint8_t* stg = pring + TC_PRING;
+  uint8_t* zero = stg + (size_t)SNST * STILE;
+  TcMeta* meta = reinterpret_cast<TcMeta*>(zero + TC_ZERO);
+  if (tid == 0) {
+    for (int k = 0; k < NSG; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int b = 0; b < TC_NACC; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 8);        // one arrival per epilogue warp
+    }
+    fence_proxy_async();
+    meta->fail = 0;
+    meta->issued = 0;
+  }
+  for (int i = tid; i < (int)(TC_ZERO / 16); i += NTS) reinterpret_cast<uint4*>(zero)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tmem_alloc(&meta->tmem, TC_NCOL);
+  fence_proxy_async();   // the zero block is read by the tensor cores
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = meta->tmem;
+  int* const fail = &meta->fail;
+  int consumed = 0, committed = -1;                      // (the MMA issuer's)
+  if (warp == TC_PROD / 32) {
+    const uint64_t pol = l2_policy_evict_first();
+    int k = 0;
+    for (; k < K; ++k) {
+      const int st = k % NSG;
+      const int it = first + k * G;
+      const int s = it / nt;
+      int TI, TJ;
+      sym_tile_coords(it - s * nt, T, TI, TJ);
+      if (k >= NSG &&
+          !__all_sync(0xffffffffu, tc_wait(&empty[st], (uint32_t)(((k / NSG) - 1) & 1), err, fail))) {
+        if (lane == 0) *fail = 1;
+        break;
       }
+      const uint8_t* pb = Pq + (size_t)(F8 ? s : 0) * T * PB;
+      const bool off = TI != TJ;
+      if (elect_one()) {
+        meta->ti[k & 15] = TI;
+        meta->tj[k & 15] = TJ;
+        mbar_expect_tx(&full[st], TB + PB * (off ? 2u : 1u));
+        bulk_g2s_evict_first(stg + (size_t)st * TB, Qt + (size_t)it * TB, TB, &full[st], pol);
+        bulk_g2s(pring + (size_t)st * 2 * PB, pb + (size_t)TJ * PB, PB, &full[st]);
+        if (off) bulk_g2s(pring + (size_t)st * 2 * PB + PB, pb + (size_t)TI * PB, PB, &full[st]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) meta->issued = k;
+  } else if (warp == TC_MMA / 32) {
+    const uint32_t zr = smem_u32(zero);
+    for (int k = 0; k < K; ++k) {
+      const int st = k % NSG, b = k % TC_NACC;
+      if (!__all_sync(0xffffffffu, tc_wait(&full[st], (uint32_t)((k / NSG) & 1), err, fail))) {
+        if (lane == 0) *fail = 1;
+        break;
+      }
+      consumed = k + 1;
+      if (k >= TC_NACC &&
+          !__all_sync(0xffffffffu, tc_wait(&accempty[b], (uint32_t)(((k / TC_NACC) - 1) & 1), err, fail))) {
+        if (lane == 0) *fail = 1;
+        break;
+      }
+      tc_fence_after();
+      // (the producer wrote tile k's coordinates before its copies completed)
+      const bool off = meta->ti[k & 15] != meta->tj[k & 15];
+      const uint32_t a = smem_u32(stg + (size_t)st * TB);
+      const uint32_t pj = smem_u32(pring + (size_t)st * 2 * PB), pi = pj + PB;
+      const uint64_t ar = umma_sdesc(a, 128u, NC * 128u), bj = umma_sdesc(pj, 128u, zr - pj);
+      const uint64_t ac = umma_sdesc(a, NC * 128u, 128u), bi = umma_sdesc(pi, 128u, zr - pi);
+      const uint32_t d = tmem + (uint32_t)b * 32;
+      // K steps: the tile's next two cores along the row (256 B) for the row
+      // product, its next 16 / 32 rows (4096 B) for the column product; the
+      // pieces' next two cores (256 B); addresses in 16-byte units
 #pragma unroll
-      for (int q = 0; q < SRW8; ++q) {
-        float ba[4], bb[4];
-        TE::dec(ra[q], ba);
-        TE::dec(rb_[q], bb);
-        rpa[q] = fmaf(ba[3], dja[3], fmaf(ba[2], dja[2], fmaf(ba[1], dja[1], ba[0] * dja[0])));
-        rpb[q] = fmaf(bb[3], djb[3], fmaf(bb[2], djb[2], fmaf(bb[1], djb[1], bb[0] * djb[0])));
-        const float da = __shfl_sync(0xffffffffu, dila, q);
-        const float db = __shfl_sync(0xffffffffu, dilb, q);
+      for (int kk = 0; kk < KSTEPS; ++kk) {
+        if (elect_one()) umma<F8>(d, ar + 16u * kk, bj + 16u * kk, IDR, kk > 0);
+        __syncwarp();
+      }
+      if (off) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          cpa[e] = fmaf(ba[e], da, cpa[e]);
-          cpb[e] = fmaf(bb[e], db, cpb[e]);
+        for (int kk = 0; kk < KSTEPS; ++kk) {
+          if (elect_one()) umma<F8>(d + 16, ac + 256u * kk, bi + 16u * kk, IDC, kk > 0);
+          __syncwarp();
         }
       }
+      // (the elected lane is the lowest active one: the lane that issued)
+      if (elect_one()) {
+        umma_commit(&empty[st]);
+        umma_commit(&accfull[b]);
+      }
+      __syncwarp();
+      committed = k;
     }
-    const bool offa = ia != ja, offb = hb && ib != jb;
-    if (offa)
-      *reinterpret_cast<float4*>(sred + warp * STB + lane * 4) = make_float4(cpa[0], cpa[1], cpa[2], cpa[3]);
-    if (offb)
-      *reinterpret_cast<float4*>(sred + (NWS + warp) * STB + lane * 4) = make_float4(cpb[0], cpb[1], cpb[2], cpb[3]);
-    __syncthreads();   // both stages consumed, both tiles' column partials in sred
-    if (tid == 0) {
-      fence_proxy_async();
-      if (k + NSG < K) issue(k + NSG);
-      if (k + 1 + NSG < K) issue(k + 1 + NSG);
-    }
-    const int csa = sa, cia = ia, cja = ja, csb = sb, cib = ib, cjb = jb;
-    sa = nsa; ia = nia; ja = nja; dila = nila;
-    sb = nsb; ib = nib; jb = njb; dilb = nilb;
+  } else if (warp < 8) {
+    const bool rowp = warp < 4;
+    const int t = 32 * (warp & 3) + lane;
+    // tile coordinates and FP8's 1 / sigma two tiles ahead (their latency
+    // stays off the accumulator read-out)
+    struct Ahead {
+      int s, ti, tj;
+      float sc;
+    };
+    auto look = [&](int k) {
+      Ahead a{0, 0, 0, 1.f};
+      if (k < K) {
+        const int it = first + k * G;
+        a.s = it / nt;
+        sym_tile_coords(it - a.s * nt, T, a.ti, a.tj);
+        if constexpr (F8)
+          if (rowp || a.ti != a.tj)
+            a.sc = __ldg(reinterpret_cast<const float*>(Pq + ((size_t)a.s * T + (rowp ? a.tj : a.ti)) * PB + 7 * 16));
+      }
+      return a;
+    };
+    Ahead a0 = look(0), a1 = look(1);
+    for (int k = 0; k < K; ++k) {
+      const int b = k % TC_NACC;
+      const Ahead cur = a0;
+      a0 = a1;
+      a1 = look(k + 2);
+      const int s = cur.s, TI = cur.ti, TJ = cur.tj;
+      const float sc = cur.sc;
+      const bool work = rowp || TI != TJ;
+      const bool ok =
+          __all_sync(0xffffffffu, tc_wait(&accfull[b], (uint32_t)((k / TC_NACC) & 1), err, fail));
+      if (!ok) {
+        if (lane == 0) *fail = 1;
+        break;
+      }
+      tc_fence_after();
+      float v[8];
+      if (work) tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)b * 32 + (rowp ? 0u : 16u), v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[b]);
+      if (work) {
+        float y;
+        if constexpr (F8) {
+          float acc = v[5];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      dja[e] = nja4[e];
-      djb[e] = njb4[e];
-    }
-    slices(k + 4, nsa, nia, nja, nja4, nila);
-    slices(k + 5, nsb, nib, njb, njb4, nilb);
-    {
-      const float rv = warp_rows8(rpa);
-      if (!(lane & 3))
-        sp[(size_t)csa * T * ldp + (size_t)cja * ldp + (size_t)cia * STB + warp * SRW8 + sym_row8(lane)] = rv;
-    }
-    if (hb) {
-      const float rv = warp_rows8(rpb);
-      if (!(lane & 3))
-        sp[(size_t)csb * T * ldp + (size_t)cjb * ldp + (size_t)cib * STB + warp * SRW8 + sym_row8(lane)] = rv;
-    }
-    // column sums: the low half of the CTA for tile k, the high half for k + 1
-    const int half = tid / STB, c0 = tid - half * STB;
-    if (half < 2 && (half == 0 ? offa : offb)) {
-      const float* sr = sred + half * NWS * STB + c0;
-      float v[NWS];
-#pragma unroll
-      for (int w = 0; w < NWS; ++w) v[w] = sr[w * STB];
-      float c = v[0];
-#pragma unroll
-      for (int w = 1; w < NWS; ++w) c += v[w];
-      const int cs = half ? csb : csa, cI = half ? cib : cia, cJ = half ? cjb : cja;
-      sp[((size_t)cs * T + cI) * ldp + (size_t)cJ * STB + c0] = c;
+          for (int q = 4; q >= 0; --q) acc = fmaf(acc, 0.0625f, v[q]);
+          y = acc * sc;
+        } else {
+          (void)sc;
+          y = (v[2] + v[1]) + v[0];
+        }
+        if (rowp)
+          sp[((size_t)s * T + TJ) * ldp + (size_t)TI * STB + t] = y;
+        else
+          sp[((size_t)s * T + TI) * ldp + (size_t)TJ * STB + t] = y;
+      }
     }
   }
+  // on a failure, drain this CTA's copies and MMAs in flight
+  __syncthreads();
+  if (tid == TC_MMA && *reinterpret_cast<volatile int*>(fail)) {
+    const int issued = meta->issued;
+    for (int k2 = consumed; k2 < issued; ++k2)
+      mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
+    if (committed >= 0) {
+      mbar_wait_bounded(&accfull[committed % TC_NACC], (uint32_t)((committed / TC_NACC) & 1), err);
+      mbar_wait_bounded(&empty[committed % NSG], (uint32_t)((committed / NSG) & 1), err);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TC_NCOL);
 }
 
 // The right-hand sides of a smoothed-gap pass (the row-streaming pass reads
@@ -660,10 +869,7 @@ __global__ void __launch_bounds__(NTS, 1) k_sym_tiles(const Inst* __restrict__ i
     gap_rhs(I, S.phase, x, v);
     sym_tiles<2, RAPDB_F32>(I, x, v, 0, dsm, &ctrl->err);
   } else if constexpr (ST != RAPDB_F32) {
-    if (ST == RAPDB_FP8)
-      sym_tiles_q<ST>(I, VS, (size_t)I.ldv, dsm, &ctrl->err);
-    else
-      sym_tiles_q<ST>(I, I.dv, 0, dsm, &ctrl->err);
+    sym_tiles_tc<ST>(I, dsm, &ctrl->err);   // the pieces of d were formed by k_pass_sym
   }
 }
 
@@ -693,7 +899,12 @@ __global__ void __launch_bounds__(NT, 2) k_pass_sym(const Inst* __restrict__ ins
   __shared__ double red[NWARP * NDOT];
   __shared__ int s_dec;
   const Inst& I = insts[0];
-  if (sym_kind(I, states[0])) return;
+  const int kind = sym_kind(I, states[0]);
+  if (kind == 3) {   // a trial of the quantised level: the pieces of d for the tile kernel
+    if constexpr (ST != RAPDB_F32) sym_pieces<ST>(I, ST == RAPDB_FP8 ? VS : I.dv, ST == RAPDB_FP8 ? (size_t)I.ldv : 0);
+    return;
+  }
+  if (kind) return;
   for (int bid = blockIdx.x; bid < I.M * I.nrb; bid += gridDim.x)
     pass_body<ST, SYM_ROW_RPW<ST>, SYM_ROW_UNR<ST>, 0, 0>(insts, states, ctrl, pmap, XS, VS, dsm, red, s_dec, bid);
 }
@@ -797,11 +1008,19 @@ __global__ void __launch_bounds__(NTS, 1) k_sym_plain(const Inst* __restrict__ i
 #endif
   if constexpr (ST != RAPDB_F32) {
     if (quant) {
-      sym_tiles_q<ST>(insts[0], v, ST == RAPDB_FP8 ? (size_t)insts[0].ldv : 0, dsm, err);
+      sym_tiles_tc<ST>(insts[0], dsm, err);   // the pieces of v: k_sym_pieces
       return;
     }
   }
   sym_tiles<1, RAPDB_F32>(insts[0], v, nullptr, 0, dsm, err);
+}
+
+// The pieces of a stand-alone pass's right-hand side v for the quantised
+// tiles (FP8: v is the pre-scaled (M, ldv) array s_s .* v).
+template <int ST>
+__global__ void __launch_bounds__(NT) k_sym_pieces(const Inst* __restrict__ insts, const float* __restrict__ v) {
+  if constexpr (ST != RAPDB_F32)
+    sym_pieces<ST>(insts[0], v, ST == RAPDB_FP8 ? (size_t)insts[0].ldv : 0);
 }
 
 template <int DUMMY>

@@ -100,10 +100,13 @@ __global__ void k_pack_sym(const float* __restrict__ Q, int ld, int n, int M, in
 
 // The same tiles of the quantised stored matrices (EB-byte codes, row
 // stride ld): Qp[s][t] = codes of Q~_s[I*STB .., J*STB ..], zero outside n x n
-// (a zero code is 0.0 in BF16 and in E4M3).
+// (a zero code is 0.0 in BF16 and in E4M3), in the tensor cores' core-matrix
+// layout: entry (r, c) of a tile at ((r / 8) NC + c / CE) 128 B + (r % 8) 16 B +
+// (c % CE) EB, CE = 16 / EB entries per 16-byte core row, NC = STB / CE.
 template <typename T_>
 __global__ void k_pack_sym_codes(const T_* __restrict__ Q, int ld, int n, int M, int ntile,
                                  const int* __restrict__ tij, T_* __restrict__ Qp) {
+  constexpr int CE = 16 / (int)sizeof(T_), NC = STB / CE, PER_CORE = 128 / (int)sizeof(T_);
   const int64_t total = (int64_t)M * ntile * STB * STB;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e % STB);
@@ -113,7 +116,8 @@ __global__ void k_pack_sym_codes(const T_* __restrict__ Q, int ld, int n, int M,
     const int s = (int)(st / ntile);
     const int ij = tij[t];
     const int row = (ij >> 16) * STB + r, col = (ij & 0xffff) * STB + c;
-    Qp[e] = (row < n && col < n) ? Q[(size_t)s * n * ld + (size_t)row * ld + col] : T_(0);
+    const int64_t dst = st * STB * STB + (int64_t)((r >> 3) * NC + c / CE) * PER_CORE + (r & 7) * CE + (c % CE);
+    Qp[dst] = (row < n && col < n) ? Q[(size_t)s * n * ld + (size_t)row * ld + col] : T_(0);
   }
 }
 
