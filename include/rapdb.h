@@ -99,11 +99,12 @@ typedef struct {
                               /*    are U^k + Q~ d, the increment Q~ d read from the  */
                               /*    packed BF16/FP8 tiles and U^k a compensated       */
                               /*    float32 product re-formed (anchored) by the       */
-                              /*    precision check every 64 accepted iterations; it  */
-                              /*    switches to the float32 tiles when the level's    */
-                              /*    own residual reaches tol while the true one does  */
-                              /*    not, or when the true residual did not fall at    */
-                              /*    two checks in a row                               */
+                              /*    precision check every 64 accepted iterations (and */
+                              /*    whenever the level's own residual reaches tol);   */
+                              /*    it switches to the float32 tiles when four checks */
+                              /*    in a row find no true residual below the lowest   */
+                              /*    one so far while the level's own residual misses  */
+                              /*    the true one by more than half of it              */
   double stall_ratio;         /* stall: the true rel KKT fell by less than this factor */
                               /*    since the previous precision check               */
   int32_t max_iter, max_trials, kkt_every;

@@ -176,7 +176,7 @@ struct State {
                         // 3: compensated products whose trial increments Q~ d come from the
                         //    quantised packed tiles (anchored by float32 compensated products)
   int switch_it;        // iteration of the first precision switch (-1: none)
-  int stall_count;      // consecutive precision checks without a decrease of the true residual
+  int stall_count;      // quantised-increment level: consecutive checks without a new lowest true residual
   int hyp_ret;          // the phase a projection onto X serves (PH_TRIAL or PH_GAPF)
   double hyp_nu;        // the last projection's nu (warm start of the next)
   double hyp_t;         // the last normal-cone multiplier t of the KKT residual (warm start)

@@ -886,22 +886,34 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
         if (rel <= P.tol) {
           dec = 2;
         } else {
-          const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
-          S.stall_count = (S.kkt_ref > 0.0 && rel >= S.kkt_ref) ? S.stall_count + 1 : 0;
-          S.kkt_ref = rel;
           if (S.precision == 3) {
             // the quantised-increment level: every check re-anchors U, so the
             // storage error cannot build up beyond ANCHOR_EVERY iterations and
-            // shrinks with the steps. Checks come every ANCHOR_EVERY
-            // iterations, too often for the halving test: switch when the
-            // true residual did not fall at all, twice in a row, or when the
-            // drifted products claim convergence that the check denies
-            if (S.stall_count >= 2 || S.rel_q <= P.tol) dec = 1;
-          } else if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) {
+            // shrinks with the steps.  Checks come every ANCHOR_EVERY
+            // iterations, too often for the halving test (the residual of the
+            // method is not monotone, and it can sit on a plateau for
+            // thousands of iterations at float32 as well): kkt_ref is the
+            // lowest true residual so far, and the level switches when four
+            // checks in a row find none lower while the level's own residual
+            // at the same point (rel_q) misses the true one by more than half
+            // of it, i.e. when the stall is the storage's and not the
+            // method's.  A check that the drifted products' residual triggered
+            // (rel_q <= tol) and that finds the true one above tol re-anchors
+            // and the level carries on
+            if (S.kkt_ref > 0.0 && rel >= S.kkt_ref) {
+              S.stall_count += 1;
+            } else {
+              S.stall_count = 0;
+              S.kkt_ref = rel;
+            }
+            if (S.stall_count >= 4 && fabs(S.rel_q - rel) > 0.5 * rel) dec = 1;
+          } else {
+            const bool stalled = (S.kkt_ref > 0.0 && rel > P.stall_ratio * S.kkt_ref);
+            S.kkt_ref = rel;
             // switch when the true residual stalls, when the stored matrices'
             // problem is solved, or when the storage error already dominates
             // (the true residual is more than twice the stored level's)
-            dec = 1;
+            if (stalled || S.rel_q <= P.tol || rel > 2.0 * S.rel_q) dec = 1;
           }
         }
         s_dec = dec;

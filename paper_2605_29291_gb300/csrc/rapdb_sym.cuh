@@ -488,14 +488,15 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
 //     pieces blocks (full);
 //   MMA issuer (warp 8; its elected lane issues): waits for the stage (full)
 //     and for the accumulator pair of tile k - TC_NACC to be read out
-//     (accempty), issues the row and column MMAs, then commits them to empty
-//     (the stage is free) and to accfull;
-//   epilogue (warps 0-7): waits for accfull, reads its accumulators (warps
-//     0-3 the row products, TMEM lanes 32 w ..; warps 4-7 the column
-//     products), arrives on accempty, adds the pieces' columns and stores.
+//     (accempty), issues the row and column MMAs, then commits them to
+//     accfull;
+//   epilogue (warps 0-7): waits for accfull, takes FP8's 1 / sigma from the
+//     stage's pieces and frees the stage (empty, one arrival per warp), reads
+//     its accumulators (warps 0-3 the row products, TMEM lanes 32 w ..;
+//     warps 4-7 the column products), arrives on accempty, adds the pieces'
+//     columns and stores.
 // Each role derives the tile coordinates it needs from k (the issuer reads
-// the producer's, published by the full barrier's arrival); the epilogue
-// reads FP8's 1 / sigma from the pieces blocks in global memory.
+// the producer's, published by the full barrier's arrival).
 // TMEM: 128 columns, four tiles of [row 16 | column 16] in flight between
 // the issuer and the epilogue.  Every wait is bounded and also gives up when
 // another role has failed; on a failure the CTA sets *err, drains its copies
@@ -660,7 +661,7 @@ __device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* e
   if (tid == 0) {
     for (int k = 0; k < NSG; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], 1);
+      mbar_init(&empty[k], 8);           // one arrival per epilogue warp
     }
     for (int b = 0; b < TC_NACC; ++b) {
       mbar_init(&accfull[b], 1);
@@ -744,31 +745,23 @@ __device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* e
         }
       }
       // (the elected lane is the lowest active one: the lane that issued)
-      if (elect_one()) {
-        umma_commit(&empty[st]);
-        umma_commit(&accfull[b]);
-      }
+      if (elect_one()) umma_commit(&accfull[b]);
       __syncwarp();
       committed = k;
     }
   } else if (warp < 8) {
     const bool rowp = warp < 4;
     const int t = 32 * (warp & 3) + lane;
-    // tile coordinates and FP8's 1 / sigma two tiles ahead (their latency
-    // stays off the accumulator read-out)
+    // tile coordinates two tiles ahead (off the accumulator read-out)
     struct Ahead {
       int s, ti, tj;
-      float sc;
     };
     auto look = [&](int k) {
-      Ahead a{0, 0, 0, 1.f};
+      Ahead a{0, 0, 0};
       if (k < K) {
         const int it = first + k * G;
         a.s = it / nt;
         sym_tile_coords(it - a.s * nt, T, a.ti, a.tj);
-        if constexpr (F8)
-          if (rowp || a.ti != a.tj)
-            a.sc = __ldg(reinterpret_cast<const float*>(Pq + ((size_t)a.s * T + (rowp ? a.tj : a.ti)) * PB + 7 * 16));
       }
       return a;
     };
@@ -779,7 +772,6 @@ __device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* e
       a0 = a1;
       a1 = look(k + 2);
       const int s = cur.s, TI = cur.ti, TJ = cur.tj;
-      const float sc = cur.sc;
       const bool work = rowp || TI != TJ;
       const bool ok =
           __all_sync(0xffffffffu, tc_wait(&accfull[b], (uint32_t)((k / TC_NACC) & 1), err, fail));
@@ -787,6 +779,17 @@ __device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* e
         if (lane == 0) *fail = 1;
         break;
       }
+      // tile k's MMAs are done; FP8's 1 / sigma comes from the stage's pieces
+      // (its copies completed before the MMAs ran: the full wait returns at
+      // once), then this warp releases the stage to the producer
+      float sc = 1.0f;
+      if constexpr (F8) {
+        const int st = k % NSG;
+        if (work && __all_sync(0xffffffffu, tc_wait(&full[st], (uint32_t)((k / NSG) & 1), err, fail)))
+          sc = *reinterpret_cast<const float*>(pring + (size_t)st * 2 * PB + (rowp ? 0 : PB) + 7 * 16);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[k % NSG]);
       tc_fence_after();
       float v[8];
       if (work) tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)b * 32 + (rowp ? 0u : 16u), v);
@@ -817,10 +820,8 @@ __device__ __forceinline__ void sym_tiles_tc(const Inst& I, uint8_t* dsm, int* e
     const int issued = meta->issued;
     for (int k2 = consumed; k2 < issued; ++k2)
       mbar_wait_bounded(&full[k2 % NSG], (uint32_t)((k2 / NSG) & 1), err);
-    if (committed >= 0) {
+    if (committed >= 0)
       mbar_wait_bounded(&accfull[committed % TC_NACC], (uint32_t)((committed / TC_NACC) & 1), err);
-      mbar_wait_bounded(&empty[committed % NSG], (uint32_t)((committed / NSG) & 1), err);
-    }
   }
   tc_fence_before();
   __syncthreads();

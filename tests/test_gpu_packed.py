@@ -291,7 +291,8 @@ def test_quantised_level_solve_meets_tolerance(R, cuda, storage, case):
     """BF16 / FP8 storage with refinement and packing: the trials add the
     increments Q~ d of the quantised tiles to float32 compensated products,
     re-anchored at the check every 64 accepted iterations; a stall there
-    switches to the float32 tiles.  The solve ends at rel KKT 1e-6 of the
+    that the storage explains switches to the float32 tiles.  The solve ends
+    at rel KKT 1e-6 of the
     float32 problem by the oracle's float64 residual, whether or not it
     switched (switch_iter says when it did)."""
     data = W.kml_qcqp(200, 6, 8, seed=4 + storage) if case == "kml" else W.random_qcqp(300, 8, seed=7)
