@@ -708,6 +708,13 @@ def run_ours(args):
         summary.update(batched_instances_per_s=bt["instances_per_s"], batched_seconds=bt["seconds"],
                        batched_speedup_vs_sequential=bt["speedup_vs_sequential"],
                        batched_converged=bt["converged"], batched_instances=bt["instances"])
+    if "mixed" in extras:
+        # the quantised trial tiles (tensor-core kernel) against the copy peak
+        pk_ = peaks()[0]["hbm_gbs"]
+        for name in ("bf16", "fp8"):
+            g_ = extras["mixed"][name]["trial_tile_gbs"]
+            summary[f"mixed_{name}_trial_tile_gbs"] = g_
+            summary[f"mixed_{name}_trial_tile_frac"] = g_ / pk_
     if "mixed_over_seeds" in extras:
         mo = extras["mixed_over_seeds"]
         for name in ("bf16", "fp8"):
