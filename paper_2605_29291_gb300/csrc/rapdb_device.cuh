@@ -293,19 +293,17 @@ __device__ __forceinline__ void df_acc_mulf(dflt& acc, dflt a, float f) {
 // Sum of len >= 1 pairs src[0..len-1] in index order (L2 loads issued eight
 // at a time, so the adds do not wait on one load after another).
 __device__ __forceinline__ dflt df_sum_pairs(const float2* __restrict__ src, int len) {
+  // the loads of a batch of 32 are all issued before its sums (entries past
+  // len read as (0, 0), which TwoSum adds exactly): one memory round trip
+  // per 32 pairs instead of one per pair in a ragged tail
   float2 p0 = __ldcg(src);
   dflt t = {p0.x, p0.y};
-  int r = 1;
-  for (; r + 8 <= len; r += 8) {
-    float2 b[8];
+  for (int r = 1; r < len; r += 32) {
+    float2 b[32];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) b[u] = __ldcg(src + r + u);
+    for (int u = 0; u < 32; ++u) b[u] = (r + u < len) ? __ldcg(src + r + u) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) t = df_add(t, dflt{b[u].x, b[u].y});
-  }
-  for (; r < len; ++r) {
-    const float2 p = __ldcg(src + r);
-    t = df_add(t, dflt{p.x, p.y});
+    for (int u = 0; u < 32; ++u) t = df_add(t, dflt{b[u].x, b[u].y});
   }
   return t;
 }

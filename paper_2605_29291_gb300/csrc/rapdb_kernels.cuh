@@ -261,11 +261,18 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   __shared__ float sx[VCOL], sd[VCOL];
   __shared__ int s_dec;
   __shared__ __align__(16) State Sc;        // the control step's copy of the state
+  __shared__ __align__(16) Inst sI;         // the instance descriptor (one parallel copy)
   const int b = vmap[blockIdx.x];
-  const Inst& I = insts[b];
   State& S = states[b];
   const int phase = S.phase;
   if (!vec_phase(phase)) return;
+  {
+    const uint32_t* isrc = reinterpret_cast<const uint32_t*>(&insts[b]);
+    uint32_t* idst = reinterpret_cast<uint32_t*>(&sI);
+    for (int w = threadIdx.x; w < (int)(sizeof(Inst) / 4); w += NT) idst[w] = isrc[w];
+  }
+  __syncthreads();
+  const Inst& I = sI;
   const DevParams& P = I.P;
   const int m = I.m, n = I.n, ldv = I.ldv;
   const int cb = blockIdx.x - I.vblk0;
@@ -1038,7 +1045,7 @@ __device__ __forceinline__ void pass_tile(const uint8_t* Qm, int ld, int row0, i
 static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, int i, const double* part, int nb,
                                    int phase, bool comp, const float* x, const float* v, double* red, int& s_dec);
 static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int phase, bool comp, const float* x,
-                                    const float* v, double* red, int& s_dec);
+                                    const float* v, double* red, int& s_dec, double* Dsh = nullptr);
 
 template <int ST, int RPW, int UNR, int NST, int CWB>
 __device__ __forceinline__ void pass_body(const Inst* __restrict__ insts, State* __restrict__ states,
@@ -1158,11 +1165,17 @@ static __device__ void pass_finish(const Inst& I, State& S, Ctrl* ctrl, int s, i
 // I.dots: the equality dots, g at the pass point, and the phase's decision
 // (the yx backtracking test and step rule, the xy dual step, or the set-up,
 // restart, check and anchor bookkeeping).
+// Dsh: the reduced dots in shared memory (the packed pass's control kernel
+// formed them there), else they are read from I.dots, bypassing L1.
 static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int phase, bool comp, const float* x,
-                                    const float* v, double* red, int& s_dec) {
+                                    const float* v, double* red, int& s_dec, double* Dsh) {
   const int tid = threadIdx.x;
+  auto dl = [Dsh](const double* p) { return Dsh ? *p : __ldcg(p); };
   const int ldv = I.ldv;
-  if (I.s_off && tid < NDOT) I.dots[tid] = S.dots0[tid];
+  if (I.s_off && tid < NDOT) {
+    I.dots[tid] = S.dots0[tid];
+    if (Dsh) Dsh[tid] = S.dots0[tid];
+  }
   if (I.m > I.m_ineq && !gap_phase(phase)) {
     // linear equalities (no stored matrix): u = w = 0, c'x and c'v here
     const float* xlo_e =
@@ -1177,12 +1190,14 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
       }
       block_allsum<2>(sv, red);
       if (tid == 0) {
-        double* Di = I.dots + (size_t)ie * NDOT;
-        Di[D_XU] = 0.0;
-        Di[D_VW] = 0.0;
-        Di[D_VUO] = 0.0;
-        Di[D_CX] = sv[0];
-        Di[D_CV] = sv[1];
+        for (int c2 = 0; c2 < (Dsh ? 2 : 1); ++c2) {
+          double* Di = (c2 ? Dsh : I.dots) + (size_t)ie * NDOT;
+          Di[D_XU] = 0.0;
+          Di[D_VW] = 0.0;
+          Di[D_VUO] = 0.0;
+          Di[D_CX] = sv[0];
+          Di[D_CV] = sv[1];
+        }
       }
     }
   }
@@ -1190,7 +1205,7 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
 
   const DevParams& P = I.P;
   const int m = I.m;
-  const double* D = I.dots;
+  const double* D = Dsh ? Dsh : I.dots;
   const int k0 = S.k, gcur0 = S.gcur, ycur0 = S.ycur;
   if (gap_phase(phase)) {          // smoothed-gap passes: the vector kernel consumes the products
     if (tid == 0) S.passes += 1;
@@ -1208,10 +1223,10 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
     double acc[3] = {0.0, 0.0, 0.0};   // sum y~_i d'Q_i d, |dg|^2, |dy|^2
     for (int ii = tid; ii < m; ii += NT) {
       const double* Di = D + (size_t)(ii + 1) * NDOT;
-      const double vw = __ldcg(&Di[D_VW]);
-      I.gnew[ii] = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+      const double vw = dl(&Di[D_VW]);
+      I.gnew[ii] = 0.5 * dl(&Di[D_XU]) + dl(&Di[D_CX]) + I.dcon[ii];
       acc[0] += yt[ii] * vw;
-      const double dgi = __ldcg(&Di[D_VUO]) + __ldcg(&Di[D_CV]) + 0.5 * vw;
+      const double dgi = dl(&Di[D_VUO]) + dl(&Di[D_CV]) + 0.5 * vw;
       acc[1] += dgi * dgi;
       const double t = yt[ii] - y[ii];
       acc[2] += t * t;
@@ -1220,7 +1235,7 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
     const double an = P.c_alpha / sig;
     const double t_acc = sig / (k0 == 0 ? sig : S.sigma0);
     if (tid == 0) {
-      const double dQd = __ldcg(&D[D_VW]) + acc[0];
+      const double dQd = dl(&D[D_VW]) + acc[0];
       const double E = 0.5 * dQd - S.dd / (2.0 * tau) + acc[1] / (2.0 * an) - (1.0 / sig - th * S.alpha_k) * 0.5 * acc[2];
       const bool ok = E <= -P.delta * S.dd / (2.0 * tau) - P.delta * acc[2] / (2.0 * sig);
       S.trials_total += 1;
@@ -1246,7 +1261,7 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
     double* yt = I.yb[ycur0 ^ 1];
     for (int ii = tid; ii < m; ii += NT) {
       const double* Di = D + (size_t)(ii + 1) * NDOT;
-      const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+      const double g = 0.5 * dl(&Di[D_XU]) + dl(&Di[D_CX]) + I.dcon[ii];
       I.gnew[ii] = g;
       yt[ii] = (P.dual_simplex || ii >= I.m_ineq) ? y[ii] + sig * g : fmax(0.0, y[ii] + sig * g);
     }
@@ -1263,7 +1278,7 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
   const double T0 = S.T;
   for (int ii = tid; ii < m; ii += NT) {
     const double* Di = D + (size_t)(ii + 1) * NDOT;
-    const double g = 0.5 * __ldcg(&Di[D_XU]) + __ldcg(&Di[D_CX]) + I.dcon[ii];
+    const double g = 0.5 * dl(&Di[D_XU]) + dl(&Di[D_CX]) + I.dcon[ii];
     I.gnew[ii] = g;
     if (phase != PH_KKT32) gd[ii] = g;
     if (phase == PH_AVGP) I.yb[ycur0][ii] = I.ycum[ii] / T0;
@@ -1295,7 +1310,7 @@ static __device__ void pass_control(const Inst& I, State& S, Ctrl* ctrl, int pha
   S.xcur ^= 1;
   S.ucur ^= 1;
   S.anchor_age = 0;         // INIT / AVGP form U directly
-  S.obj = 0.5 * __ldcg(&D[D_XU]) + __ldcg(&D[D_CX]);
+  S.obj = 0.5 * dl(&D[D_XU]) + dl(&D[D_CX]);
   if (phase == PH_INIT) {
     S.fresh = 1;
     S.phase = PH_TRIAL;

@@ -954,34 +954,47 @@ __global__ void __launch_bounds__(NT) k_sym_finish(const Inst* __restrict__ inst
 // into I.dots, then the pass's control step.
 // The control step works on a shared-memory copy of the state (written back
 // at the end): its serial scalar updates then cost no global round trips.
+constexpr int SYM_CTRL_ROWS = 256;
 template <int DUMMY>
 __global__ void __launch_bounds__(NT) k_sym_ctrl(const Inst* __restrict__ insts, State* __restrict__ states,
                                                  Ctrl* __restrict__ ctrl) {
   __shared__ double red[NWARP * NDOT];
   __shared__ int s_dec;
   __shared__ __align__(16) State S;
-  const Inst& I = insts[0];
+  __shared__ __align__(16) Inst sI;
+  __shared__ double sdots[SYM_CTRL_ROWS * NDOT];
   {
-    static_assert(sizeof(State) % 4 == 0, "state copy in words");
+    // the state and the instance descriptor in shared memory: one parallel
+    // copy instead of a global round trip per field in the serial steps
+    static_assert(sizeof(State) % 4 == 0 && sizeof(Inst) % 4 == 0, "copies in words");
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&states[0]);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&S);
     for (int w = threadIdx.x; w < (int)(sizeof(State) / 4); w += NT) dst[w] = src[w];
+    const uint32_t* isrc = reinterpret_cast<const uint32_t*>(&insts[0]);
+    uint32_t* idst = reinterpret_cast<uint32_t*>(&sI);
+    for (int w = threadIdx.x; w < (int)(sizeof(Inst) / 4); w += NT) idst[w] = isrc[w];
   }
   __syncthreads();
+  const Inst& I = sI;
   const int kind = sym_kind(I, S);
   if (kind == 0) return;
   const int T = I.tsym, phase = S.phase;
+  // the dots also stay in shared memory for the control step (up to
+  // SYM_CTRL_ROWS constraint rows), which then reads them without a round trip
+  double* Dsh = (I.m + 1 <= SYM_CTRL_ROWS) ? sdots : nullptr;
   for (int pq = threadIdx.x; pq < I.M * NDOT; pq += NT) {
     const int s = pq / NDOT, q = pq - s * NDOT;
-    I.dots[(size_t)(s + I.s_off) * NDOT + q] = df_to_double(df_sum_pairs(I.spart + ((size_t)s * NDOT + q) * T, T));
+    const double d = df_to_double(df_sum_pairs(I.spart + ((size_t)s * NDOT + q) * T, T));
+    I.dots[(size_t)(s + I.s_off) * NDOT + q] = d;
+    if (Dsh) Dsh[(s + I.s_off) * NDOT + q] = d;
   }
   __syncthreads();
   if (kind == 2) {
     const float *x, *v;
     gap_rhs(I, phase, x, v);
-    pass_control(I, S, ctrl, phase, false, x, v, red, s_dec);
+    pass_control(I, S, ctrl, phase, false, x, v, red, s_dec, Dsh);
   } else {
-    pass_control(I, S, ctrl, phase, true, I.xf[S.xcur ^ 1], I.dv, red, s_dec);
+    pass_control(I, S, ctrl, phase, true, I.xf[S.xcur ^ 1], I.dv, red, s_dec, Dsh);
   }
   __syncthreads();
   {

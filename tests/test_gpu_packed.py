@@ -70,7 +70,7 @@ def stored_rows(data, si, rows, storage):
     return QZ.fp8_dequantize(codes, sc)[rows]
 
 
-def check_packed_pass(R, data, seed, rows=None, storage=0):
+def check_packed_pass(R, data, seed, rows=None, storage=0, vscale=None):
     """rapdb_packed_pass against float64 products on every (or the sampled)
     row of every stored matrix, under the gamma_23 bound; the dots against
     float64 sums of the same quantities; a second call bit-identical.  With
@@ -85,6 +85,9 @@ def check_packed_pass(R, data, seed, rows=None, storage=0):
     g.manual_seed(seed)
     x = (data.lb + (data.ub - data.lb) * torch.rand(n, generator=g, device=dev)).contiguous()
     v = (1e-2 * torch.randn(n, generator=g, device=dev)).contiguous()
+    if vscale is not None:   # one factor per 128-entry slice (the slices the tile kernels split)
+        for b, f in enumerate(vscale):
+            v[128 * b:128 * (b + 1)] *= f
     uold = torch.randn((M, n), generator=g, device=dev).contiguous()
     U, Wt, dots = s.packed_pass(x, v, uold)
     U2, W2, d2 = s.packed_pass(x, v, uold)
@@ -140,6 +143,16 @@ def test_quantised_packed_pass_matches_float64(R, cuda, storage, n, m):
     """The BF16 / FP8 tiles: products of the stored (quantised) matrices."""
     data = W.random_qcqp(n, m, seed=n + 3 * m).to(cuda)
     check_packed_pass(R, data, seed=n + 1, storage=storage)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_quantised_packed_pass_slice_magnitudes(R, cuda, storage):
+    """Right-hand-side slices of very different magnitudes, one of them all
+    zero: the tensor-core path splits each 128-entry slice into pieces (FP8
+    with a power-of-two scale per slice); the products still meet the
+    float32 bound of the stored matrices."""
+    data = W.random_qcqp(700, 4, seed=11).to(cuda)
+    check_packed_pass(R, data, seed=6, storage=storage, vscale=[0.0, 1e-18, 1.0, 1e15, 3.0e-5, 7.0])
 
 
 @pytest.mark.parametrize("storage", [1, 2])
