@@ -263,15 +263,21 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
   __shared__ __align__(16) State Sc;        // the control step's copy of the state
   __shared__ __align__(16) Inst sI;         // the instance descriptor (one parallel copy)
   const int b = vmap[blockIdx.x];
-  State& S = states[b];
-  const int phase = S.phase;
-  if (!vec_phase(phase)) return;
   {
+    // the instance descriptor and the state in shared memory, in one round
+    // trip: the column work below only reads the state (the last CTA copies
+    // it again for the control step, and the arrival counter is global)
     const uint32_t* isrc = reinterpret_cast<const uint32_t*>(&insts[b]);
     uint32_t* idst = reinterpret_cast<uint32_t*>(&sI);
     for (int w = threadIdx.x; w < (int)(sizeof(Inst) / 4); w += NT) idst[w] = isrc[w];
+    const uint32_t* ssrc = reinterpret_cast<const uint32_t*>(&states[b]);
+    uint32_t* sdst = reinterpret_cast<uint32_t*>(&Sc);
+    for (int w = threadIdx.x; w < (int)(sizeof(State) / 4); w += NT) sdst[w] = ssrc[w];
   }
   __syncthreads();
+  const State& S = Sc;
+  const int phase = S.phase;
+  if (!vec_phase(phase)) return;
   const Inst& I = sI;
   const DevParams& P = I.P;
   const int m = I.m, n = I.n, ldv = I.ldv;
@@ -613,11 +619,12 @@ __global__ void __launch_bounds__(NT) k_vec(const Inst* __restrict__ insts, Stat
       for (int q = 0; q < NVP; ++q) I.vpart[(size_t)cb * NVP + q] = acc[q];
     }
   }
-  if (!arrive_last(&S.arrive_vec, (unsigned)I.ncb)) return;
+  if (!arrive_last(&states[b].arrive_vec, (unsigned)I.ncb)) return;
 
   // ---- last CTA of this instance: the control step, on a shared-memory copy
   // of the state (its serial scalar updates then cost no global round trips;
   // written back at the end) ----
+  __syncthreads();   // (every thread has read its copy of the state above)
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&states[b]);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&Sc);
