@@ -132,7 +132,11 @@ typedef struct {
                               /*    bytes of a row-streaming pass.  BF16/FP8 storage  */
                               /*    also keeps its codes in the same tiles (a half /  */
                               /*    a quarter of the float32 tiles' bytes), read by   */
-                              /*    the trials of the quantised-increment level.      */
+                              /*    the trials of the quantised-increment level on    */
+                              /*    the tcgen05 tensor cores (the right-hand side     */
+                              /*    split into exact pieces of the codes' type; the   */
+                              /*    products meet the float32 error bound of the      */
+                              /*    stored matrices).                                 */
                               /*    Needs refine = 1, exactly symmetric Q_i (checked  */
                               /*    at create: RAPDB_ERR_INVALID) and a single-       */
                               /*    instance context; rows_per_block and              */
@@ -321,10 +325,12 @@ rapdb_status rapdb_packed_pass(rapdb_ctx *ctx, const float *x, const float *v, c
  * products at x^k), 4 = level 3 through the packed upper block triangle
  * (contexts created with pack_sym = 1; the form their trials use: the tile
  * kernel, then the row-block kernel), 5 = the tile kernel of level 4 alone,
- * 6 = the tile kernel over the packed BF16 / FP8 tiles of a quantised
- * pack_sym context (the quantised-increment level's trials), 7 = level 6 with
- * its row-block kernel; -1 in a context whose last solve ended at the
- * quantised-increment level times level 7.
+ * 6 = the tensor-core tile kernel over the packed BF16 / FP8 tiles of a
+ * quantised pack_sym context (the quantised-increment level's trials; the
+ * right-hand side's pieces are formed once, before the timed launches),
+ * 7 = level 6 with the pieces formed in every pass and the row-block kernel;
+ * -1 in a context whose last solve ended at the quantised-increment level
+ * times level 7.
  * *ms_per_pass (host) receives the average duration of one launch,
  * *bytes_per_pass (host) the algorithmic bytes of one pass: the Q entries
  * read, M * n * n * (4 | 2 | 1) (+ M * n * 4 scale bytes for FP8); at
