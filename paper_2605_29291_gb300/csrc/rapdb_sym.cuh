@@ -468,11 +468,12 @@ __device__ __forceinline__ void sym_tiles(const Inst& I, const float* __restrict
 // pieces of the tile's own type, one piece per column of the N = 16 operand,
 // so that the products of the pieces are exact and only the float32
 // accumulation rounds:
-//   BF16: d = h + m + l, three bf16 pieces (exact: 3 x 8 significant bits);
+//   BF16: d = h + m + l, three bf16 pieces (exact: 3 x 8 significant bits,
+//         for |d| >= 2^-100);
 //   FP8:  sigma d = sum_j q_j 16^-j, six e4m3 pieces, sigma a power of two per
 //         128-entry slice (|sigma d| < 256), each residual scaled by 16 before
-//         it is rounded (no e4m3 underflow); the pieces hold sigma d to about
-//         2^-24 of itself.
+//         it is rounded; the pieces hold sigma d to 2^-23 of each entry or
+//         2^-37 of the slice's largest entry, whichever is larger.
 // The pieces are formed once per pass (sym_pieces, in the kernel that runs
 // before the tile kernel) into blocks of one 128-entry slice each; each
 // tile's stage receives its tile and the blocks of slices J and I by bulk
